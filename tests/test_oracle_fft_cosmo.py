@@ -1,0 +1,149 @@
+"""Pins of the oracle's FFT and cosmology against things other than the oracle itself:
+brute-force DFT sums, Parseval, spherical Bessel functions, closed forms for power-law
+spectra, the Einstein-de Sitter growth law, and the halo masses the paper prints."""
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dft_matrix(n, sign):
+    j = np.arange(n)
+    return np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 16, 64, 12, 7])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft1d_matches_direct_sum(n, sign):
+    rng = np.random.default_rng(n)
+    a = rng.normal(size=n) + 1j * rng.normal(size=n)
+    ref = dft_matrix(n, sign) @ a
+    np.testing.assert_allclose(oracle.fft1d(a, sign), ref, rtol=0, atol=1e-12 * max(1, n))
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_fft3d_matches_direct_sum(n):
+    rng = np.random.default_rng(100 + n)
+    a = rng.normal(size=(n, n, n)) + 1j * rng.normal(size=(n, n, n))
+    f = dft_matrix(n, -1)
+    ref = np.einsum("ia,jb,kc,abc->ijk", f, f, f, a)
+    np.testing.assert_allclose(oracle.fft3d(a, -1), ref, rtol=0, atol=1e-11)
+
+
+def test_fft3d_parseval_and_round_trip():
+    n = 16
+    rng = np.random.default_rng(7)
+    a = rng.normal(size=(n, n, n))
+    spec = oracle.fft3d(a, -1)
+    assert np.isclose(np.sum(np.abs(spec) ** 2) / n ** 3, np.sum(a ** 2), rtol=1e-12)
+    back = oracle.fft3d(spec, +1) / n ** 3
+    np.testing.assert_allclose(back.real, a, atol=1e-12)
+    np.testing.assert_allclose(back.imag, 0.0, atol=1e-12)
+
+
+def test_fft3d_is_numpy_fftn():
+    n = 32
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(n, n, n))
+    np.testing.assert_allclose(oracle.fft3d(a, -1), np.fft.fftn(a), atol=1e-9)
+
+
+@pytest.mark.parametrize("x", [0.0, 1e-6, 1e-3, 0.0499, 0.05, 0.03, 0.5, 1.0, 4.4934, 10.0, 57.3, 300.0])
+def test_tophat_window_is_spherical_bessel(x):
+    ref = 1.0 if x == 0 else 3.0 * special.spherical_jn(1, x) / x
+    assert abs(oracle.tophat_w(x) - ref) < 1e-12
+
+
+def test_bbks_small_q_limit():
+    assert oracle.bbks_transfer(0.0) == 1.0
+    assert abs(oracle.bbks_transfer(1e-8) - 1.0) < 1e-6
+    q = np.logspace(-4, 2, 50)
+    t = np.array([oracle.bbks_transfer(v) for v in q])
+    assert np.all(np.diff(t) < 0) and np.all(t > 0)
+
+
+def test_sigma2_white_spectrum_closed_form():
+    # P(k) = A (n_s = 0, no transfer): the top-hat smoothed variance is A / V_R. The
+    # integrand falls only as 1/k, so the quadrature's cut at k = 1e4/Mpc leaves a
+    # relative tail of about 1/(R k_max): use large radii.
+    o = oracle.Oracle(oracle.Cosmology(n_s=0.0, use_transfer=False))
+    for r in [8.0 / 0.68, 20.0, 50.0]:
+        assert np.isclose(o.sigma2(r), o.amp / (4.0 / 3.0 * np.pi * r ** 3), rtol=2e-5)
+
+
+def test_sigma2_inverse_k_spectrum_closed_form():
+    # P(k) = A / k (n_s = -1, no transfer): sigma^2 = A/(2 pi^2 R^2) Int_0^inf x W(x)^2 dx
+    # and Int x W^2 dx = 9 Int j1(x)^2 / x dx = 9/4, so sigma^2 = 9 A / (8 pi^2 R^2).
+    # The cut at k_max = 1e4/Mpc leaves a relative tail of 1/(R k_max)^2.
+    o = oracle.Oracle(oracle.Cosmology(n_s=-1.0, use_transfer=False))
+    for r in [0.1, 1.0, 5.0, 30.0]:
+        assert np.isclose(o.sigma2(r), 9.0 * o.amp / (8.0 * np.pi ** 2 * r ** 2), rtol=2e-6)
+
+
+def test_sigma8_normalisation_and_monotone():
+    o = oracle.Oracle()
+    assert np.isclose(np.sqrt(o.sigma2(8.0 / 0.68)), 0.82, rtol=1e-9)
+    rs = np.logspace(-2, 2, 40)
+    s = np.array([o.sigma2(r) for r in rs])
+    assert np.all(np.diff(s) < 0)
+
+
+def test_growth_einstein_de_sitter():
+    o = oracle.Oracle(oracle.Cosmology(omega_m=1.0, omega_l=0.0))
+    for z in [0.0, 1.0, 8.0, 9.0, 10.0]:
+        assert np.isclose(o.growth(z), 1.0 / (1.0 + z), rtol=1e-9)
+
+
+def test_growth_lcdm_carroll_press_turner():
+    # Carroll, Press & Turner (1992) fit of the growth suppression, accurate to ~1 %.
+    om = 0.31
+    o = oracle.Oracle(oracle.Cosmology(omega_m=om))
+    ol = 1.0 - om
+    g0 = 2.5 * om / (om ** (4.0 / 7.0) - ol + (1.0 + om / 2.0) * (1.0 + ol / 70.0))
+    # at z = 9 matter dominates (g ~ 1), so D(9) ~ (1/10) / g0
+    assert abs(o.growth(9.0) * 10.0 * g0 - 1.0) < 0.01
+
+
+def _golden_mmin():
+    rows = []
+    with open(os.path.join(GOLDEN, "mmin_paper.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                t, m = line.split()[:2]
+                rows.append((float(t), float(m)))
+    return rows
+
+
+@pytest.mark.parametrize("tvir,log_m", _golden_mmin())
+def test_mmin_matches_paper_printed_masses(tvir, log_m):
+    o = oracle.Oracle(oracle.PAPER_COSMOLOGY)
+    assert abs(np.log10(o.mmin(tvir, 8.0)) - log_m) <= 0.005
+
+
+def test_mmin_mu_is_pinned():
+    # mu = 0.59 or 1.22 moves the first printed mass beyond the 0.005 dex rounding
+    o = oracle.Oracle(oracle.PAPER_COSMOLOGY)
+    assert abs(np.log10(o.mmin(1e4, 8.0, mu=0.59)) - 8.06) > 0.005
+    assert abs(np.log10(o.mmin(1e4, 8.0, mu=1.22)) - 8.06) > 0.1
+
+
+def test_t0_reduces_to_27mk():
+    # (1+z)/10 = 1, Omega_m h^2 = 0.15, Omega_b h^2 = 0.023 make every factor of Sec. 2.2 unity
+    h = 0.7
+    o = oracle.Oracle(oracle.Cosmology(h=h, omega_m=0.15 / h ** 2, omega_b=0.023 / h ** 2))
+    assert np.isclose(o.t0_mk(9.0), 27.0, rtol=1e-14)
+    assert np.isclose(o.t0_mk(19.0), 27.0 * np.sqrt(2.0), rtol=1e-14)
+
+
+def test_mass_radius_round_trip():
+    o = oracle.Oracle()
+    rho = o.rho_mean()
+    assert np.isclose(rho, 0.31 * 2.775e11 * 0.68 ** 2, rtol=1e-14)
+    for m in [1e8, 1e10, 1e12]:
+        r = o.mass_to_radius(m)
+        assert np.isclose(4.0 / 3.0 * np.pi * r ** 3 * rho, m, rtol=1e-12)
