@@ -1,0 +1,355 @@
+"""Benchmark: 21-cm likelihood evaluations per second on 128^3 x 3-redshift boxes.
+
+One step = one batched likelihood call (eor_likelihood) for W walkers: per walker and
+redshift the whole excursion-set path (tables, filter + inverse FFT per radius, flag,
+partial ionization, delta T_b, power spectrum) and the chi^2, summed over redshifts. One
+evaluation = one walker's three-redshift chi^2. Inputs are seeded synthetic boxes (a BBKS
+Gaussian random field grown to z and clipped at delta > -1) and walker parameters drawn
+uniformly from zeta in [5, 100], R_mfp in [5, 20] Mpc, log10 T_vir in [4, 6].
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--walkers 128] [--impl reference]
+
+Under torchrun (N > 1) each rank evaluates its own walkers on its own GPU (weak scaling);
+ranks share no data, only a barrier and the max of the timings. Rank 0 prints one JSON
+line. `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "21cm likelihood evals/s at 128³×3z, batched vs plain; HBM roofline %"
+N, BOX, ZS = 128, 250.0, (8.0, 9.0, 10.0)
+FIDUCIAL = (30.0, 15.0, 4.7)
+WORKLOAD = "128^3 boxes, L=250 Mpc, z=8,9,10; batched walkers (zeta, R_mfp, log10 T_vir) uniform in [5,100]x[5,20]x[4,6]"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--walkers", type=int, default=128)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-walkers", type=int, default=16, help="walkers timed one call each (plain path)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-trace", action="store_true", help="time without the per-kernel event brackets")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+
+def oracle_sample(seconds: float, walkers_params, delta, mock, sigma):
+    """Time the FP64 oracle on (walker, redshift) realizations of the workload until the
+    budget is spent (at least one). Returns (evals/s, realizations, seconds, threads)."""
+    import oracle
+    orc = oracle.Oracle()
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        w, j = divmod(done, len(ZS))
+        w %= len(walkers_params)
+        ion = orc.ionize(delta[j], BOX, ZS[j], *walkers_params[w])
+        d2, _, cnt = oracle.power_spectrum(ion["dtb"], BOX, 14, 0.1, 1.5)
+        oracle.chi2(d2, cnt, mock[j], sigma[j])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    per_eval = el / done * len(ZS)
+    return 1.0 / per_eval, done, el, orc.threads
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1501_06576_gb300 import synth
+    import oracle
+    delta = synth.density_boxes(N, BOX, ZS, seed=1)
+    params = synth.walker_params(max(args.walkers, 1), seed=3)
+    mock = np.full((len(ZS), 14), 10.0)
+    sigma = 0.2 * mock
+    per_step = []
+    orc = oracle.Oracle()
+    for s in range(args.warmup + args.steps):
+        w = s % len(params)
+        j = s % len(ZS)
+        t0 = time.perf_counter()
+        ion = orc.ionize(delta[j], BOX, ZS[j], *params[w])
+        d2, _, cnt = oracle.power_spectrum(ion["dtb"], BOX, 14, 0.1, 1.5)
+        oracle.chi2(d2, cnt, mock[j], sigma[j])
+        if s >= args.warmup:
+            per_step.append(time.perf_counter() - t0)
+    mean = statistics.mean(per_step)
+    value = 1.0 / (mean * len(ZS))
+    sample = "each step: one walker at one redshift of the workload (128^3 ionization over its radius ladder, delta T_b, Delta^2, chi^2), FP64; evals/s = 1 / (3 x seconds per realization)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "box_mpc": BOX, "z": list(ZS), "walkers": args.walkers},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": orc.threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm helpers
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "fft_core.cuh", "eor_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str):
+    """DRAM bytes per task of a kernel class from the committed ncu summary, or None if the
+    kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        return d["bytes_per_task"].get(kernel_class)
+    except Exception:
+        return None
+
+
+def algorithmic_bytes(n: int):
+    """Bytes each kernel class must move per unit (one (walker, redshift, radius) task for the
+    filter-plane and pencil passes): complex64 half spectrum nh*n*n*8, real box n^3*4."""
+    nspec = (n // 2 + 1) * n * n * 8
+    return {"filter_plane": 2 * nspec,       # read the density spectrum, write the plane-transformed task
+            "pencil_ionize": nspec}          # read it back (flags, delta and delta T_b extra per pair)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    from paper_1501_06576_gb300 import eor21, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    W = args.walkers
+
+    delta = synth.density_boxes(N, BOX, ZS, seed=1)
+    mock_delta = synth.density_boxes(N, BOX, ZS, seed=2)
+    params = synth.walker_params(W, seed=3 + rank)
+
+    with torch.cuda.stream(stream):
+        ctx = eor21.Context(n=N, box_mpc=BOX, z=ZS, max_walkers=W, stream=stream.cuda_stream)
+        # the mock: the fiducial model on the independent seed + 1 boxes (set-up, untimed)
+        ctx.init_boxes(torch.from_numpy(mock_delta).cuda())
+        ctx.set_params(np.array([FIDUCIAL]))
+        ctx.run_ionization()
+        mock = ctx.power_spectrum()[0][0]
+        sigma = 0.2 * mock
+        ctx.init_boxes(torch.from_numpy(delta).cuda())
+        d_params = torch.from_numpy(params).cuda()
+        d_mock = torch.from_numpy(np.ascontiguousarray(mock)).cuda()
+        d_sigma = torch.from_numpy(np.ascontiguousarray(sigma)).cuda()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        ctx.trace(not args.no_trace)
+        for _ in range(args.warmup):
+            ctx.likelihood(d_params, d_mock, d_sigma)
+        stream.synchronize()
+
+        # ---------------- timed region: device-resident inputs
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.3)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        class_ms, class_launches = {}, {}
+        launches = 0
+        for s in range(args.steps):
+            flush.zero_()
+            starts[s].record(stream)
+            ctx.likelihood(d_params, d_mock, d_sigma)
+            ends[s].record(stream)
+            launches += ctx.launch_count()
+            if not args.no_trace:
+                for k, (ms, cnt) in ctx.trace_read().items():
+                    class_ms[k] = class_ms.get(k, 0.0) + ms
+                    class_launches[k] = class_launches.get(k, 0) + cnt
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        clk = clocks.stop()
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+        value = W * world * args.steps / (total_ms / 1e3)
+
+        # units processed by the filter-plane and pencil passes: one per (walker, z, radius)
+        ctx.set_params(params)
+        tasks_per_step = sum(len(ctx.walker_ladder(w)) for w in range(W)) * len(ZS)
+
+        # ---------------- end to end through host buffers (pinned), D2H of chi^2 every step
+        h_params = torch.from_numpy(params).pin_memory().numpy()
+        h_mock = torch.from_numpy(np.ascontiguousarray(mock)).pin_memory().numpy()
+        h_sigma = torch.from_numpy(np.ascontiguousarray(sigma)).pin_memory().numpy()
+        ctx.trace(False)
+        ctx.likelihood(h_params, h_mock, h_sigma)        # capture outside the timed loop
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            chi2 = ctx.likelihood(h_params, h_mock, h_sigma)
+            e2e_s += time.perf_counter() - t0
+        assert np.all(np.isfinite(chi2))
+        e2e = W * world * args.steps / e2e_s
+        h2d = h_params.nbytes + h_mock.nbytes + h_sigma.nbytes
+        d2h = chi2.nbytes
+
+        # ---------------- plain path: one walker per call
+        pw = min(args.plain_walkers, W)
+        for w in range(2):
+            ctx.likelihood(d_params[w:w + 1], d_mock, d_sigma)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for w in range(pw):
+            ctx.likelihood(d_params[w:w + 1], d_mock, d_sigma)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain = pw / (p0.elapsed_time(p1) / 1e3)
+
+    if rank != 0:
+        return 0
+
+    # ---------------- roofline of the dominant kernel class
+    peak, peak_kind = measured_peak()
+    roof = None
+    per_unit = algorithmic_bytes(N)
+    if class_ms:
+        dom = max(per_unit, key=lambda k: class_ms.get(k, 0.0))
+        avg_launch_ms = class_ms[dom] / max(class_launches[dom], 1)
+        units_per_launch = tasks_per_step * args.steps / max(class_launches[dom], 1)
+        bytes_per_launch = per_unit[dom] * units_per_launch
+        achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+        traffic = ncu_traffic(dom)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if traffic is None else traffic * units_per_launch, "kernel": dom,
+                "peak_kind": peak_kind, "bytes_per_unit": per_unit[dom], "units_per_launch": units_per_launch,
+                "avg_launch_ms": avg_launch_ms,
+                "share": {k: class_ms[k] / sum(class_ms.values()) for k in class_ms if class_ms[k] > 0}}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        flat = np.full((len(ZS), 14), 10.0)     # the oracle takes no input from the GPU path
+        cv, nrel, secs, cores = oracle_sample(args.cpu_seconds, params, delta, flat, 0.2 * flat)
+        cpu = {"value": cv, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"{nrel} (walker, redshift) realizations of the workload in {secs:.1f} s (FP64, "
+                         f"128^3, full radius ladder, delta T_b, Delta^2, chi^2); evals/s = 1/(3 x s per realization)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "box_mpc": BOX, "z": list(ZS), "walkers_per_gpu": W,
+                       "radius_tasks_per_step": tasks_per_step, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"walkers sharded over {world} GPU(s)", "traced": not args.no_trace},
+            "plain": {"value": plain, "unit": "evals/s", "walkers_timed": pw,
+                      "note": "same kernels, one walker per eor_likelihood call"},
+            "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

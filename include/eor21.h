@@ -1,0 +1,173 @@
+/*
+ * eor21.h — C ABI of libeor21, the GB300 (sm_103a) implementation of the data-parallel
+ * hot path inside every likelihood call of 21CMMC (Greig & Mesinger 2015,
+ * arXiv:1501.06576): the seminumerical excursion-set reionization step on fixed
+ * density boxes, the 21-cm brightness temperature, its spherically averaged power
+ * spectrum and the chi^2 against a mock.
+ *
+ * Call order (EOR_ESTATE otherwise):
+ *   eor_create -> eor_init_boxes -> eor_set_params -> eor_run_ionization
+ *              -> eor_power_spectrum -> eor_chi2
+ * eor_likelihood runs set_params .. chi2 as one call (one CUDA-graph replay).
+ *
+ * Memory: the caller owns every pointer it passes; the library copies inputs and
+ * never keeps a caller pointer past the call. The library owns its device memory
+ * (cudaMalloc, or the allocator given in eor_config). A `mem` argument says where a
+ * caller buffer lives: EOR_HOST (the call returns when the data is copied and the
+ * outputs are ready) or EOR_DEVICE (a device pointer on the context's device; the
+ * work is ordered on the context's stream and the call returns without waiting).
+ *
+ * Errors: every int-returning call gives EOR_OK (0) or a code below, and
+ * eor_last_error() gives the message. No exception crosses the ABI, nothing aborts,
+ * and no kernel traps: device-side checks set an error word that the host reads.
+ *
+ * Layouts (row-major, last index fastest):
+ *   density boxes   float [n_z][n][n][n]      (x, y, z), box j at redshift cfg.z[j]
+ *   walker params   double [n_walkers][3]     (zeta, R_mfp [Mpc], log10 T_vir [K])
+ *   x_HI boxes      float [n_walkers][n_z][n][n][n]
+ *   x_HI means      double [n_walkers][n_z]
+ *   spectra         double [n_walkers][n_z][n_bins]  (Delta^2 in mK^2, mean |k| in 1/Mpc)
+ *   mode counts     long long [n_walkers][n_z][n_bins]
+ *   mock, sigma     double [n_z][n_bins]
+ *   chi^2           double [n_walkers]
+ */
+#ifndef EOR21_H
+#define EOR21_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EOR21_MAX_Z 8
+#define EOR21_MAX_BINS 64
+#define EOR21_MAX_RADII 64
+
+enum {
+    EOR_OK = 0,
+    EOR_EINVAL = 1,    /* bad size, NaN or out-of-range value, NULL where one is required */
+    EOR_ENOMEM = 2,    /* device or host allocation failed */
+    EOR_ECUDA = 3,     /* a CUDA call failed (message holds cudaGetErrorString) */
+    EOR_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    EOR_ESTATE = 5,    /* call out of order */
+    EOR_ENOTSUP = 6    /* grid size or option this build does not provide */
+};
+
+enum { EOR_HOST = 0, EOR_DEVICE = 1 };
+
+typedef struct eor_ctx eor_ctx;   /* opaque, library-owned */
+
+/* Problem description. eor_default_config fills the 128^3, 250 Mpc, z = 8, 9, 10
+ * workload with the readings the library takes where the paper is silent. */
+typedef struct {
+    int n;                       /* grid side: 16, 32, 64 or 128 */
+    double box_mpc;              /* comoving box side L [Mpc] */
+    int n_z;                     /* redshifts, 1..EOR21_MAX_Z */
+    double z[EOR21_MAX_Z];
+    double h, omega_m, omega_b, n_s, sigma8;   /* flat LCDM, Omega_Lambda = 1 - Omega_m */
+    double r_factor;             /* ratio between successive filter radii (1.1) */
+    int r_cell_rule;             /* 0: R_cell = radius of a sphere of one cell's volume; 1: cell side */
+    double delta_c;              /* linear collapse threshold (1.686) */
+    double mu;                   /* mean molecular weight in the T_vir -> M relation (0.6) */
+    int n_bins;                  /* logarithmic k bins (14) */
+    double k_lo, k_hi;           /* bin range [k_lo, k_hi) [1/Mpc] (0.1, 1.5) */
+    double chi2_k_lo, chi2_k_hi; /* bins whose geometric centre lies here enter chi^2 (0.15, 1.0) */
+    int max_walkers;             /* largest n_walkers passed to eor_set_params */
+    double r_mfp_max;            /* largest R_mfp passed to eor_set_params [Mpc] (sizes tables) */
+    /* Optional device allocator (both or neither); NULL: cudaMalloc / cudaFree. */
+    void* (*dev_alloc)(size_t bytes, void* user);
+    void (*dev_free)(void* ptr, void* user);
+    void* alloc_user;
+} eor_config;
+
+/* Defaults: n = 128, L = 250 Mpc, z = {8, 9, 10}, (h, Omega_m, Omega_b, n_s, sigma_8) =
+ * (0.68, 0.31, 0.02254/0.68^2, 0.96, 0.82), r_factor 1.1, r_cell_rule 0, delta_c 1.686,
+ * mu 0.6 (the value that reproduces the halo masses printed in Sec. 3.1 and 4.1),
+ * 14 bins on [0.1, 1.5), chi^2 bins 0.15..1.0 (Sec. 2.5), max_walkers 1, r_mfp_max 20. */
+void eor_default_config(eor_config* cfg);
+
+/* Create a context on the current CUDA device, ordered on `cuda_stream` (a cudaStream_t;
+ * NULL: a stream the context creates). Builds the FP64 cosmology tables on the GPU:
+ * growth D(z), the top-hat mass variance sigma^2(R) (Sec. 2.1 via the collapsed fraction),
+ * and the k-bin tables. *out is NULL on failure. */
+int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out);
+
+/* Load the fixed density boxes (Sec. 2.5: the likelihood samples one fixed realization)
+ * and Fourier transform each once (R2C, FP32). delta: float [n_z][n][n][n], used as
+ * given (delta T_b is proportional to 1 + delta). */
+int eor_init_boxes(eor_ctx* ctx, const float* delta, int mem);
+
+/* Set the walkers for the next run: params double [n_walkers][3] = (zeta, R_mfp [Mpc],
+ * log10 T_vir [K]) with zeta > 0, 0 < R_mfp <= r_mfp_max, n_walkers <= max_walkers.
+ * Builds per walker and redshift, in FP64 on the GPU: M_min(T_vir, z) (Sec. 2.1.3),
+ * the radius ladder from R_mfp down to R_cell (Sec. 2.1), sigma^2 of every radius and
+ * the overdensity at which zeta f_coll = 1 (Eq. 1); and per radius the FP32 top-hat
+ * window W(kR) on the grid. */
+int eor_set_params(eor_ctx* ctx, const double* params, int n_walkers, int mem);
+
+/* Excursion-set ionization (Eq. 1 and the partial ionization at R_cell of Sec. 2.1) of
+ * every (walker, redshift): for each radius, filter the density spectrum with W(kR),
+ * inverse-FFT and flag cells where zeta f_coll >= 1; cells never flagged get
+ * x_HII = zeta f_coll(R_cell). Then delta T_b = T0(z) x_HI (1 + delta) (Sec. 2.2, with
+ * T_S >> T_gamma and no velocity term). xhi (optional, float [n_walkers][n_z][n^3]) and
+ * xhi_mean (optional, double [n_walkers][n_z]) receive the neutral fraction. The Fourier
+ * transform and shell sums of delta T_b run here too, fused behind the last radius, so
+ * delta T_b never goes to memory; eor_power_spectrum then only normalises the sums. */
+int eor_run_ionization(eor_ctx* ctx, float* xhi, double* xhi_mean, int mem);
+
+/* Spherically averaged 21-cm power spectrum Delta^2(k) = k^3 P(k) / (2 pi^2) of delta T_b
+ * (Sec. 2.2): FFT (FP32), then per bin the mean over its modes (k != 0) of
+ * k^3 |dx^3 DFT|^2 / (2 pi^2 V), accumulated in FP64. Bins with no mode give NaN.
+ * d2 and kmean double [n_walkers][n_z][n_bins]; nmodes long long, same shape; each
+ * pointer optional. */
+int eor_power_spectrum(eor_ctx* ctx, double* d2, double* kmean, long long* nmodes, int mem);
+
+/* chi^2 = sum over redshifts (Sec. 3.4) and over bins with geometric centre in
+ * [chi2_k_lo, chi2_k_hi] (Sec. 2.5) of ((Delta^2 - mock) / sigma)^2, FP64. mock_d2 and
+ * sigma double [n_z][n_bins] (sigma > 0 on the used bins); chi2 double [n_walkers]. */
+int eor_chi2(eor_ctx* ctx, const double* mock_d2, const double* sigma, double* chi2, int mem);
+
+/* set_params + run_ionization + power_spectrum + chi2 for a batch of walkers, replayed
+ * as one captured CUDA graph per batch size. Same argument rules as those calls; d2
+ * (optional) receives the spectra. */
+int eor_likelihood(eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2,
+                   const double* sigma, double* chi2, double* d2, int mem);
+
+/* Diagnostics through the same kernels. eor_filtered_density: the density of box
+ * z_index smoothed by the top-hat of radius r_mpc, float [n][n][n].
+ * eor_density_spectrum: the box's R2C half spectrum as float pairs (re, im) in the
+ * layout [kz][kx][ky] with kz = 0..n/2. eor_walker_ladder: walker w's radii (double,
+ * up to EOR21_MAX_RADII) and their count, after eor_set_params. */
+int eor_filtered_density(eor_ctx* ctx, int z_index, double r_mpc, float* out, int mem);
+int eor_density_spectrum(eor_ctx* ctx, int z_index, float* out, int mem);
+int eor_walker_ladder(eor_ctx* ctx, int walker, double* radii, int* n_radii);
+
+/* Power spectrum of any real box on the context's grid (Sec. 2.2 definition, the same
+ * kernels as eor_power_spectrum): box float [n][n][n]; d2, kmean double [n_bins] and
+ * nmodes long long [n_bins], each optional. Needs only eor_create. */
+int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* kmean, long long* nmodes,
+                           int mem);
+
+/* Tracing (not part of the method). With tracing on, every kernel launch of the
+ * following calls is bracketed by CUDA events on the context's stream, also inside the
+ * captured graph of eor_likelihood (switching tracing re-captures it). eor_trace_read
+ * waits for the stream and sums, per kernel class, the event-timed milliseconds and the
+ * launches of the last call: classes 0..EOR21_KERNEL_CLASSES-1 are named by
+ * eor_kernel_class_name. eor_launch_count: kernels the last call launched (for
+ * eor_likelihood, the kernels of one graph replay), traced or not. */
+#define EOR21_KERNEL_CLASSES 7
+int eor_trace(eor_ctx* ctx, int enable);
+int eor_trace_read(eor_ctx* ctx, double* total_ms, long long* launches, int n_classes);
+const char* eor_kernel_class_name(int cls);
+long long eor_launch_count(const eor_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
+const char* eor_last_error(const eor_ctx* ctx);
+const char* eor_version(void);
+void eor_destroy(eor_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

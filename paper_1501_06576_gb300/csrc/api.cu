@@ -1,0 +1,516 @@
+// api.cu — the extern "C" boundary of libeor21: context lifetime, argument checks,
+// host <-> device copies and the order of kernel launches. No step of the method runs
+// on the host; the host only sizes buffers and sequences launches.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "eor_internal.cuh"
+
+using eor::kPi;
+
+namespace {
+
+const char* kVersion = "libeor21 0.1 (sm_103a)";
+thread_local std::string g_create_error;
+
+int fail(eor_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(eor_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, EOR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+void* dev_alloc(eor_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->cfg.dev_alloc) return c->cfg.dev_alloc(bytes, c->cfg.alloc_user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(eor_ctx* c, void* p) {
+    if (!p) return;
+    if (c->cfg.dev_free) c->cfg.dev_free(p, c->cfg.alloc_user);
+    else cudaFree(p);
+}
+
+template <class T>
+bool alloc_n(eor_ctx* c, T** out, size_t count) {
+    *out = static_cast<T*>(dev_alloc(c, sizeof(T) * count));
+    return *out != nullptr;
+}
+
+// Number of radii of the ladder that starts at r_mfp: used only to size tables and the
+// launch schedule (the ladders themselves are built on the device).
+int ladder_bound(const eor_config& g, double r_mfp) {
+    double dx = g.box_mpc / g.n;
+    double r_cell = g.r_cell_rule == 1 ? dx : cbrt(3.0 / (4.0 * kPi)) * dx;
+    int count = 0;
+    double r = r_mfp;
+    while (r > r_cell && count <= EOR21_MAX_RADII) {
+        count++;
+        r = r / g.r_factor;
+    }
+    return count + 1;
+}
+
+int copy_in(eor_ctx* c, void* dst, const void* src, size_t bytes, int mem) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, mem == EOR_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy in");
+    return EOR_OK;
+}
+
+int copy_out(eor_ctx* c, void* dst, const void* src, size_t bytes, int mem) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, mem == EOR_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy out");
+    return EOR_OK;
+}
+
+int finish(eor_ctx* c, int mem) {
+    if (mem == EOR_HOST) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return EOR_OK;
+}
+
+int check_device_error(eor_ctx* c) {
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error word");
+    if (err & eor::kErrParam) return fail(c, EOR_EINVAL, "walker parameter non-finite or out of range "
+                                                         "(zeta > 0, 0 < R_mfp <= r_mfp_max, 0 < log10 T_vir < 12)");
+    if (err & eor::kErrLadder) return fail(c, EOR_EINVAL, "radius ladder longer than the tables (raise r_mfp_max)");
+    if (err & eor::kErrSigmaRange) return fail(c, EOR_EINVAL, "radius or halo mass outside the sigma^2 table range");
+    return EOR_OK;
+}
+
+bool valid_mem(int mem) { return mem == EOR_HOST || mem == EOR_DEVICE; }
+
+int run_params_to_chi2(eor_ctx* c) {
+    cudaError_t e;
+    if ((e = eor::build_walker_tables(c, c->n_walkers)) != cudaSuccess) return cuda_fail(c, e, "walker tables");
+    if ((e = eor::launch_ionization(c, nullptr)) != cudaSuccess) return cuda_fail(c, e, "ionization");
+    if ((e = eor::launch_xhi_mean(c)) != cudaSuccess) return cuda_fail(c, e, "x_HI mean");
+    if ((e = eor::launch_power_spectrum(c)) != cudaSuccess) return cuda_fail(c, e, "power spectrum");
+    if ((e = eor::launch_chi2(c)) != cudaSuccess) return cuda_fail(c, e, "chi2");
+    return EOR_OK;
+}
+
+void trace_reset(eor_ctx* c) {
+    c->trace_used = 0;
+    c->trace_class.clear();
+    c->launches = 0;
+}
+
+cudaError_t trace_reserve(eor_ctx* c, size_t pairs) {
+    if (!c->trace_on) return cudaSuccess;
+    while (c->trace_events.size() < 2 * pairs) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        c->trace_events.push_back(e);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace eor {
+
+void trace_begin(eor_ctx* c, int cls) {
+    if (!c->trace_on) return;
+    const size_t i = 2 * (size_t)c->trace_used;
+    if (i + 1 >= c->trace_events.size()) return;   // pool sized beforehand; beyond it, untraced
+    cudaEventRecord(c->trace_events[i], c->stream);
+    c->trace_class.push_back(cls);
+}
+
+void trace_end(eor_ctx* c) {
+    c->launches++;
+    if (!c->trace_on) return;
+    const size_t i = 2 * (size_t)c->trace_used;
+    if (i + 1 >= c->trace_events.size() || c->trace_class.size() != (size_t)c->trace_used + 1) return;
+    cudaEventRecord(c->trace_events[i + 1], c->stream);
+    c->trace_used++;
+}
+
+}  // namespace eor
+
+extern "C" {
+
+void eor_default_config(eor_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->n = 128;
+    cfg->box_mpc = 250.0;
+    cfg->n_z = 3;
+    cfg->z[0] = 8.0; cfg->z[1] = 9.0; cfg->z[2] = 10.0;
+    cfg->h = 0.68; cfg->omega_m = 0.31; cfg->omega_b = 0.02254 / (0.68 * 0.68);
+    cfg->n_s = 0.96; cfg->sigma8 = 0.82;
+    cfg->r_factor = 1.1;
+    cfg->r_cell_rule = 0;
+    cfg->delta_c = 1.686;
+    cfg->mu = 0.6;
+    cfg->n_bins = 14; cfg->k_lo = 0.1; cfg->k_hi = 1.5;
+    cfg->chi2_k_lo = 0.15; cfg->chi2_k_hi = 1.0;
+    cfg->max_walkers = 1;
+    cfg->r_mfp_max = 20.0;
+}
+
+const char* eor_version(void) { return kVersion; }
+
+const char* eor_last_error(const eor_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void eor_destroy(eor_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaEvent_t e : c->trace_events) cudaEventDestroy(e);
+    void* bufs[] = {c->d_delta, c->d_spec, c->d_lnsig, c->d_growth, c->d_cosmo_amp, c->d_bin_of_m2,
+                    c->d_nmodes, c->d_ksum, c->d_params, c->d_walkers, c->d_pairs, c->d_wtab, c->d_inter,
+                    c->d_flags, c->d_psinter, c->d_ps_sum, c->d_xhi_sum, c->d_chi2, c->d_mock, c->d_d2,
+                    c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
+                    c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_err};
+    for (void* p : bufs) dev_free(c, p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
+    if (!out) return fail(nullptr, EOR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, EOR_EINVAL, "cfg is NULL");
+    const eor_config& g = *cfg;
+    if (!eor::grid_supported(g.n)) return fail(nullptr, EOR_ENOTSUP, "n must be 16, 32, 64 or 128");
+    if (!(g.box_mpc > 0.0) || !isfinite(g.box_mpc)) return fail(nullptr, EOR_EINVAL, "box_mpc must be > 0");
+    if (g.n_z < 1 || g.n_z > EOR21_MAX_Z) return fail(nullptr, EOR_EINVAL, "n_z out of range");
+    for (int j = 0; j < g.n_z; j++)
+        if (!(g.z[j] >= 0.0) || !isfinite(g.z[j])) return fail(nullptr, EOR_EINVAL, "redshift must be >= 0");
+    if (!(g.h > 0.0) || !(g.omega_m > 0.0 && g.omega_m <= 1.0) || !(g.omega_b > 0.0) || !(g.sigma8 > 0.0) ||
+        !isfinite(g.n_s))
+        return fail(nullptr, EOR_EINVAL, "cosmology out of range");
+    if (!(g.r_factor > 1.0) || !(g.delta_c > 0.0) || !(g.mu > 0.0) || (g.r_cell_rule != 0 && g.r_cell_rule != 1))
+        return fail(nullptr, EOR_EINVAL, "ionization settings out of range");
+    if (g.n_bins < 1 || g.n_bins > EOR21_MAX_BINS || !(g.k_lo > 0.0) || !(g.k_hi > g.k_lo))
+        return fail(nullptr, EOR_EINVAL, "bin settings out of range");
+    if (g.max_walkers < 1 || !(g.r_mfp_max > 0.0)) return fail(nullptr, EOR_EINVAL, "max_walkers/r_mfp_max");
+    if ((g.dev_alloc == nullptr) != (g.dev_free == nullptr))
+        return fail(nullptr, EOR_EINVAL, "dev_alloc and dev_free come together");
+
+    eor_ctx* c = new (std::nothrow) eor_ctx();
+    if (!c) return fail(nullptr, EOR_ENOMEM, "host allocation");
+    c->cfg = g;
+    cudaGetDevice(&c->device);
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("stream create: ") + cudaGetErrorString(e);
+            delete c;
+            return EOR_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->n = g.n;
+    c->nh = g.n / 2 + 1;
+    c->n3 = (size_t)g.n * g.n * g.n;
+    c->nspec = (size_t)c->nh * g.n * g.n;
+    c->n_m2 = 3 * (g.n / 2) * (g.n / 2) + 1;
+    c->max_radii = ladder_bound(g, g.r_mfp_max);
+    if (c->max_radii > EOR21_MAX_RADII) {
+        eor_destroy(c);
+        return fail(nullptr, EOR_EINVAL, "r_mfp_max gives more radii than EOR21_MAX_RADII");
+    }
+    const int P = c->tune.pairs, G = c->tune.group, W = g.max_walkers, Z = g.n_z, B = g.n_bins;
+    const size_t pairs = (size_t)W * Z;
+    c->flag_words = eor::flag_words_per_pair(g.n);
+    bool ok = alloc_n(c, &c->d_delta, (size_t)Z * c->n3) && alloc_n(c, &c->d_spec, (size_t)Z * c->nspec) &&
+              alloc_n(c, &c->d_lnsig, eor::kSigmaTable + 1) && alloc_n(c, &c->d_growth, Z) &&
+              alloc_n(c, &c->d_cosmo_amp, 1) && alloc_n(c, &c->d_bin_of_m2, c->n_m2) &&
+              alloc_n(c, &c->d_nmodes, B) && alloc_n(c, &c->d_ksum, B) && alloc_n(c, &c->d_params, 3 * W) &&
+              alloc_n(c, &c->d_walkers, W) && alloc_n(c, &c->d_pairs, pairs) &&
+              alloc_n(c, &c->d_wtab, (size_t)W * c->max_radii * c->n_m2) &&
+              alloc_n(c, &c->d_inter, (size_t)P * G * c->nspec) &&
+              alloc_n(c, &c->d_flags, (size_t)P * c->flag_words) && alloc_n(c, &c->d_psinter, (size_t)P * c->nspec) &&
+              alloc_n(c, &c->d_ps_sum, pairs * B) && alloc_n(c, &c->d_xhi_sum, pairs) &&
+              alloc_n(c, &c->d_xhi_mean, pairs) && alloc_n(c, &c->d_chi2, W) && alloc_n(c, &c->d_mock, 2 * Z * B) &&
+              alloc_n(c, &c->d_d2, pairs * B) && alloc_n(c, &c->d_kmean, pairs * B) &&
+              alloc_n(c, &c->d_nmodes_pair, pairs * B) && alloc_n(c, &c->d_scratch_box, c->n3) &&
+              alloc_n(c, &c->d_diag_pair, 1) && alloc_n(c, &c->d_diag_wtab, c->n_m2) &&
+              alloc_n(c, &c->d_diag_ps, 4 * B) && alloc_n(c, &c->d_diag_cnt, B) && alloc_n(c, &c->d_err, 1);
+    if (!ok) {
+        eor_destroy(c);
+        return fail(nullptr, EOR_ENOMEM, "device allocation failed");
+    }
+    cudaError_t e = eor::prepare_kernels(c->n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = eor::build_cosmology_tables(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cosmology tables: ") + cudaGetErrorString(e);
+        eor_destroy(c);
+        return EOR_ECUDA;
+    }
+    *out = c;
+    return EOR_OK;
+}
+
+int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (!delta || !valid_mem(mem)) return fail(c, EOR_EINVAL, "delta is NULL or bad mem");
+    int r = copy_in(c, c->d_delta, delta, sizeof(float) * c->cfg.n_z * c->n3, mem);
+    if (r) return r;
+    for (int zi = 0; zi < c->cfg.n_z; zi++) {
+        cudaError_t e = eor::launch_forward_spectrum(c, zi);
+        if (e != cudaSuccess) return cuda_fail(c, e, "forward spectrum");
+    }
+    r = finish(c, EOR_HOST);
+    if (r) return r;
+    c->stage = 1;
+    return EOR_OK;
+}
+
+int eor_set_params(eor_ctx* c, const double* params, int n_walkers, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (!params || !valid_mem(mem) || n_walkers < 1 || n_walkers > c->cfg.max_walkers)
+        return fail(c, EOR_EINVAL, "params NULL, bad mem or n_walkers outside 1..max_walkers");
+    int r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem);
+    if (r) return r;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    c->n_walkers = n_walkers;
+    CK(eor::build_walker_tables(c, n_walkers), "walker tables");
+    CK(cudaStreamSynchronize(c->stream), "walker tables");
+    r = check_device_error(c);
+    if (r) { c->stage = 1; return r; }
+    c->stage = 2;
+    return EOR_OK;
+}
+
+int eor_run_ionization(eor_ctx* c, float* xhi, double* xhi_mean, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (c->stage < 2) return fail(c, EOR_ESTATE, "eor_set_params first");
+    if (!valid_mem(mem)) return fail(c, EOR_EINVAL, "bad mem");
+    const size_t pairs = (size_t)c->n_walkers * c->cfg.n_z;
+    float* xhi_dev = nullptr;
+    if (xhi) {
+        if (mem == EOR_DEVICE) {
+            xhi_dev = xhi;
+        } else {
+            if (!c->d_xhi_out && !alloc_n(c, &c->d_xhi_out, (size_t)c->cfg.max_walkers * c->cfg.n_z * c->n3))
+                return fail(c, EOR_ENOMEM, "x_HI output buffer");
+            xhi_dev = c->d_xhi_out;
+        }
+    }
+    CK(eor::launch_ionization(c, xhi_dev), "ionization");
+    CK(eor::launch_xhi_mean(c), "x_HI mean");
+    int r;
+    if (xhi && mem == EOR_HOST && (r = copy_out(c, xhi, xhi_dev, sizeof(float) * pairs * c->n3, mem))) return r;
+    if (xhi_mean && (r = copy_out(c, xhi_mean, c->d_xhi_mean, sizeof(double) * pairs, mem))) return r;
+    r = finish(c, mem);
+    if (r) return r;
+    c->stage = 3;
+    return EOR_OK;
+}
+
+int eor_power_spectrum(eor_ctx* c, double* d2, double* kmean, long long* nmodes, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (c->stage < 3) return fail(c, EOR_ESTATE, "eor_run_ionization first");
+    if (!valid_mem(mem)) return fail(c, EOR_EINVAL, "bad mem");
+    CK(eor::launch_power_spectrum(c), "power spectrum");
+    const size_t cnt = (size_t)c->n_walkers * c->cfg.n_z * c->cfg.n_bins;
+    int r;
+    if (d2 && (r = copy_out(c, d2, c->d_d2, sizeof(double) * cnt, mem))) return r;
+    if (kmean && (r = copy_out(c, kmean, c->d_kmean, sizeof(double) * cnt, mem))) return r;
+    if (nmodes && (r = copy_out(c, nmodes, c->d_nmodes_pair, sizeof(long long) * cnt, mem))) return r;
+    r = finish(c, mem);
+    if (r) return r;
+    c->stage = 4;
+    return EOR_OK;
+}
+
+int eor_chi2(eor_ctx* c, const double* mock_d2, const double* sigma, double* chi2, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (c->stage < 4) return fail(c, EOR_ESTATE, "eor_power_spectrum first");
+    if (!mock_d2 || !sigma || !chi2 || !valid_mem(mem)) return fail(c, EOR_EINVAL, "NULL argument or bad mem");
+    const size_t zb = (size_t)c->cfg.n_z * c->cfg.n_bins;
+    int r;
+    if ((r = copy_in(c, c->d_mock, mock_d2, sizeof(double) * zb, mem))) return r;
+    if ((r = copy_in(c, c->d_mock + zb, sigma, sizeof(double) * zb, mem))) return r;
+    CK(eor::launch_chi2(c), "chi2");
+    if ((r = copy_out(c, chi2, c->d_chi2, sizeof(double) * c->n_walkers, mem))) return r;
+    return finish(c, mem);
+}
+
+int eor_likelihood(eor_ctx* c, const double* params, int n_walkers, const double* mock_d2, const double* sigma,
+                   double* chi2, double* d2, int mem) {
+    if (!c) return EOR_EINVAL;
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (!params || !mock_d2 || !sigma || !chi2 || !valid_mem(mem) || n_walkers < 1 ||
+        n_walkers > c->cfg.max_walkers)
+        return fail(c, EOR_EINVAL, "NULL argument, bad mem or n_walkers outside 1..max_walkers");
+    const size_t zb = (size_t)c->cfg.n_z * c->cfg.n_bins;
+    int r;
+    if ((r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem))) return r;
+    if ((r = copy_in(c, c->d_mock, mock_d2, sizeof(double) * zb, mem))) return r;
+    if ((r = copy_in(c, c->d_mock + zb, sigma, sizeof(double) * zb, mem))) return r;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    c->n_walkers = n_walkers;
+    if (c->graph_walkers != n_walkers || c->graph_traced != c->trace_on) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+            c->graph_walkers = -1;
+        }
+        cudaGraph_t graph = nullptr;
+        trace_reset(c);
+        CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rr = run_params_to_chi2(c);
+        cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+        if (rr) {
+            if (graph) cudaGraphDestroy(graph);
+            return rr;
+        }
+        if (ec != cudaSuccess) return cuda_fail(c, ec, "end capture");
+        ec = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) return cuda_fail(c, ec, "graph instantiate");
+        c->graph_walkers = n_walkers;
+        c->graph_traced = c->trace_on;
+        c->graph_launches = c->launches;
+    }
+    c->launches = c->graph_launches;
+    CK(cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+    if ((r = copy_out(c, chi2, c->d_chi2, sizeof(double) * n_walkers, mem))) return r;
+    if (d2 && (r = copy_out(c, d2, c->d_d2, sizeof(double) * n_walkers * zb, mem))) return r;
+    r = finish(c, mem);
+    if (r) return r;
+    if (mem == EOR_HOST && (r = check_device_error(c))) return r;
+    c->stage = 4;
+    return EOR_OK;
+}
+
+int eor_filtered_density(eor_ctx* c, int z_index, double r_mpc, float* out, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (!out || !valid_mem(mem) || z_index < 0 || z_index >= c->cfg.n_z || !(r_mpc >= 0.0) || !isfinite(r_mpc))
+        return fail(c, EOR_EINVAL, "bad argument");
+    CK(eor::launch_window_table(c, r_mpc, c->d_diag_wtab), "window table");
+    float* dst = mem == EOR_DEVICE ? out : c->d_scratch_box;
+    CK(eor::launch_filtered_density(c, z_index, dst, c->d_diag_wtab), "filtered density");
+    int r;
+    if (mem == EOR_HOST && (r = copy_out(c, out, dst, sizeof(float) * c->n3, mem))) return r;
+    return finish(c, mem);
+}
+
+int eor_density_spectrum(eor_ctx* c, int z_index, float* out, int mem) {
+    if (!c) return EOR_EINVAL;
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (!out || !valid_mem(mem) || z_index < 0 || z_index >= c->cfg.n_z) return fail(c, EOR_EINVAL, "bad argument");
+    int r = copy_out(c, out, c->d_spec + (size_t)z_index * c->nspec, sizeof(float2) * c->nspec, mem);
+    if (r) return r;
+    return finish(c, mem);
+}
+
+int eor_walker_ladder(eor_ctx* c, int walker, double* radii, int* n_radii) {
+    if (!c) return EOR_EINVAL;
+    if (c->stage < 2) return fail(c, EOR_ESTATE, "eor_set_params first");
+    if (walker < 0 || walker >= c->n_walkers || !radii || !n_radii) return fail(c, EOR_EINVAL, "bad argument");
+    eor::WalkerInfo wi;
+    CK(cudaMemcpyAsync(&wi, c->d_walkers + walker, sizeof(wi), cudaMemcpyDeviceToHost, c->stream), "copy ladder");
+    CK(cudaStreamSynchronize(c->stream), "copy ladder");
+    *n_radii = wi.n_r;
+    for (int j = 0; j < wi.n_r && j < EOR21_MAX_RADII; j++) radii[j] = wi.radii[j];
+    return EOR_OK;
+}
+
+int eor_box_power_spectrum(eor_ctx* c, const float* box, double* d2, double* kmean, long long* nmodes, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (!box || !valid_mem(mem)) return fail(c, EOR_EINVAL, "box is NULL or bad mem");
+    const float* src = box;
+    int r;
+    if (mem == EOR_HOST) {
+        if ((r = copy_in(c, c->d_scratch_box, box, sizeof(float) * c->n3, mem))) return r;
+        src = c->d_scratch_box;
+    }
+    CK(eor::launch_box_power_spectrum(c, src), "box power spectrum");
+    const int nb = c->cfg.n_bins;
+    if (d2 && (r = copy_out(c, d2, c->d_diag_ps + nb, sizeof(double) * nb, mem))) return r;
+    if (kmean && (r = copy_out(c, kmean, c->d_diag_ps + 2 * nb, sizeof(double) * nb, mem))) return r;
+    if (nmodes && (r = copy_out(c, nmodes, c->d_diag_cnt, sizeof(long long) * nb, mem))) return r;
+    return finish(c, mem);
+}
+
+int eor_trace(eor_ctx* c, int enable) {
+    if (!c) return EOR_EINVAL;
+    c->trace_on = enable != 0;
+    return EOR_OK;
+}
+
+int eor_trace_read(eor_ctx* c, double* total_ms, long long* launches, int n_classes) {
+    if (!c) return EOR_EINVAL;
+    if (n_classes < 0 || (n_classes > 0 && (!total_ms || !launches))) return fail(c, EOR_EINVAL, "bad argument");
+    CK(cudaStreamSynchronize(c->stream), "trace read");
+    for (int k = 0; k < n_classes; k++) { total_ms[k] = 0.0; launches[k] = 0; }
+    for (int i = 0; i < c->trace_used; i++) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, c->trace_events[2 * i], c->trace_events[2 * i + 1]), "event time");
+        int k = c->trace_class[i];
+        if (k < n_classes) {
+            total_ms[k] += ms;
+            launches[k] += 1;
+        }
+    }
+    return EOR_OK;
+}
+
+const char* eor_kernel_class_name(int cls) {
+    static const char* names[] = {"tables", "filter_plane", "pencil_ionize", "ps_plane", "finish", "forward_fft",
+                                  "other"};
+    return (cls >= 0 && cls < eor::kKClasses) ? names[cls] : "";
+}
+
+long long eor_launch_count(const eor_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

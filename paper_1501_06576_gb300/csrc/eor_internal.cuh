@@ -1,0 +1,156 @@
+// eor_internal.cuh — data shared by the translation units of libeor21 (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/eor21.h"
+
+namespace eor {
+
+constexpr int kMaxRadii = EOR21_MAX_RADII;
+constexpr int kSigmaTable = 1024;          // ln R grid of the sigma^2(R) table
+constexpr double kSigmaRlo = 0.005;        // [Mpc]
+constexpr double kSigmaRhi = 1000.0;       // [Mpc]
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kRhoCritH2 = 2.775e11;    // 3 H0^2 / (8 pi G) in h^2 Msun / Mpc^3
+
+// Device error word bits (set by kernels, read by the host).
+enum : int {
+    kErrLadder = 1,       // a walker's ladder exceeds the table size
+    kErrSigmaRange = 2,   // a radius outside the sigma^2 table
+    kErrParam = 4,        // non-finite or out-of-range walker parameter
+};
+
+// Per (walker, redshift): everything the fused kernels need.
+struct PairInfo {
+    int w, zi, n_r, pad;
+    float zeta;              // ionizing efficiency
+    float t0;                // brightness prefactor T0(z) [mK]
+    float inv_sqrt2s2_cell;  // 1 / sqrt(2 (sigma^2_min - sigma^2(R_cell))) or 0 when <= 0
+    float cell_ok;           // 1 when R_cell's mass exceeds M_min, else 0
+    float delta_crit[kMaxRadii];   // delta_R >= delta_crit  <=>  zeta f_coll >= 1 (+inf: never)
+};
+
+// Per walker (FP64 ladder, kept for diagnostics).
+struct WalkerInfo {
+    int n_r, pad[3];
+    double radii[kMaxRadii];
+};
+
+// Cosmology constants the table kernels need.
+struct CosmoParams {
+    double h, omega_m, omega_l, omega_b, n_s, sigma8;
+    double amp;          // P(k) amplitude (set after the sigma_8 integral)
+    double rho_mean;     // Msun / Mpc^3
+};
+
+// Kernel classes of the tracing facility (eor_trace).
+enum KernelClass : int {
+    kKTables = 0,      // per-walker tables and window tables
+    kKFilterPlane = 1, // pass 1: filter + inverse plane FFT
+    kKPencil = 2,      // pass 2: C2R pencils + flag (+ x_HI, delta T_b, R2C)
+    kKPsPlane = 3,     // forward plane FFT + shell sums
+    kKFinish = 4,      // x_HI means, spectra, chi^2
+    kKForward = 5,     // density spectrum (once per box)
+    kKOther = 6,       // cosmology tables and diagnostics
+    kKClasses = 7
+};
+
+struct Tuning {
+    int group;        // radii per pencil launch (G)
+    int pairs;        // (walker, redshift) pairs in flight (P)
+};
+
+}  // namespace eor
+
+struct eor_ctx {
+    eor_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
+    size_t n3 = 0, nspec = 0;
+    eor::CosmoParams cosmo{};
+    eor::Tuning tune{4, 2};
+
+    // device buffers
+    float* d_delta = nullptr;        // [n_z][n^3]
+    float2* d_spec = nullptr;        // [n_z][nh][n][n]
+    double* d_lnsig = nullptr;       // ln sigma^2(R) at z = 0 on the ln R grid
+    double* d_growth = nullptr;      // [n_z]
+    double* d_cosmo_amp = nullptr;   // [1] P(k) amplitude
+    signed char* d_bin_of_m2 = nullptr;   // [n_m2] bin of |m|^2 or -1
+    long long* d_nmodes = nullptr;   // [n_bins]
+    double* d_ksum = nullptr;        // [n_bins]
+    double* d_params = nullptr;      // [max_walkers][3]
+    eor::WalkerInfo* d_walkers = nullptr;
+    eor::PairInfo* d_pairs = nullptr;
+    float* d_wtab = nullptr;         // [max_walkers][max_radii][n_m2]
+    float2* d_inter = nullptr;       // [G*P][nspec]
+    uint32_t* d_flags = nullptr;     // [P][flag words per pair]
+    float2* d_psinter = nullptr;     // [P][nspec]
+    double* d_ps_sum = nullptr;      // [max_walkers][n_z][n_bins]
+    double* d_xhi_sum = nullptr;     // [max_walkers][n_z]
+    double* d_chi2 = nullptr;        // [max_walkers]
+    double* d_mock = nullptr;        // [n_z][n_bins] x 2 (mock, sigma)
+    double* d_d2 = nullptr;          // [max_walkers][n_z][n_bins]
+    double* d_kmean = nullptr;       // [max_walkers][n_z][n_bins]
+    long long* d_nmodes_pair = nullptr;   // [max_walkers][n_z][n_bins]
+    double* d_xhi_mean = nullptr;    // [max_walkers][n_z]
+    float* d_xhi_out = nullptr;      // optional [max_walkers][n_z][n^3]
+    float* d_scratch_box = nullptr;  // [n^3] diagnostics
+    eor::PairInfo* d_diag_pair = nullptr;   // one-task table for diagnostics
+    float* d_diag_wtab = nullptr;    // [n_m2] window of one radius
+    double* d_diag_ps = nullptr;     // [4][n_bins] sums, d2, kmean, (counts as double)
+    long long* d_diag_cnt = nullptr; // [n_bins]
+    int* d_err = nullptr;
+    size_t flag_words = 0;
+    int n_ready_tables = 0;
+
+    // state
+    int stage = 0;                   // 0 created, 1 boxes, 2 params, 3 ionized, 4 spectra
+    int n_walkers = 0;
+    std::string err;
+
+    // tracing: event pairs around each launch of the last call (or captured graph)
+    bool trace_on = false;
+    std::vector<cudaEvent_t> trace_events;
+    std::vector<int> trace_class;
+    int trace_used = 0;
+    long long launches = 0;          // kernels launched by the last call
+    long long graph_launches = 0;    // kernels in the captured graph
+
+    // captured likelihood graphs, keyed by walker count
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_walkers = -1;
+    bool graph_traced = false;
+};
+
+namespace eor {
+
+// api.cu (tracing)
+void trace_begin(eor_ctx* c, int cls);
+void trace_end(eor_ctx* c);
+size_t estimate_launches(const eor_ctx* c);
+
+// tables.cu
+cudaError_t build_cosmology_tables(eor_ctx* c);
+cudaError_t build_walker_tables(eor_ctx* c, int n_walkers);
+
+// kernels.cu
+cudaError_t prepare_kernels(int n);
+size_t flag_words_per_pair(int n);
+cudaError_t launch_forward_spectrum(eor_ctx* c, int zi);
+cudaError_t launch_ionization(eor_ctx* c, float* xhi_out);
+cudaError_t launch_xhi_mean(eor_ctx* c);
+cudaError_t launch_power_spectrum(eor_ctx* c);
+cudaError_t launch_chi2(eor_ctx* c);
+cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab);
+cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab);
+cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box);
+bool grid_supported(int n);
+
+}  // namespace eor

@@ -1,0 +1,795 @@
+// kernels.cu — the per-cell hot path of the excursion-set likelihood on sm_103a.
+//
+// A 3D real transform of an n^3 box is done in two kinds of pass:
+//   plane pass  — one CTA per kz plane (n x n complex, shared-memory resident):
+//                 2D complex FFT over (kx, ky), transform along kx first so both
+//                 global sides of the CTA are coalesced;
+//   pencil pass — one CTA per 32 (x, y) pencils: the real <-> half-complex transform
+//                 along z, done as an n/2-point complex FFT plus a pre/post twist.
+// Fused work:
+//   pass 1 (plane, inverse)  multiplies the shared density spectrum by W(kR) on load;
+//   pass 2 (pencil, C2R)     compares delta_R with the walker's threshold (Eq. 1) and
+//                            ORs the ionization flag over a group of radii; at the last
+//                            radius (R_cell) it adds the partial ionization, forms
+//                            delta T_b = T0 x_HI (1 + delta) (Sec. 2.2) and runs the
+//                            forward R2C along z of delta T_b;
+//   PS pass (plane, forward) bins k^3 |X|^2 into the log-k shells in FP64 (Sec. 2.2).
+// delta_R and delta T_b never touch global memory.
+#include <math.h>
+
+#include "eor_internal.cuh"
+#include "fft_core.cuh"
+
+namespace eor {
+
+namespace {
+
+__device__ __forceinline__ int signed_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// ------------------------------------------------------------------ plane pass
+
+template <int N>
+struct Plane {
+    static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
+    static constexpr int S = N + 1;                        // padded row stride (float2)
+    static constexpr int UNITS = N * R2;                   // (line, team member) pairs per pass
+    static constexpr int THREADS = UNITS < 512 ? UNITS : 512;
+    static constexpr int LPT = UNITS / THREADS;            // lines per thread per pass
+    static constexpr int NB = R1 / R2;                     // stage-B DFTs per unit
+    static constexpr size_t SMEM = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 64 * sizeof(double);
+};
+
+// 2D FFT of an n x n complex plane. load(r, c) gives the natural-order input; on return
+// hold[l][q][k2] is the output at row rowOf(l) and column colOf(l, q, k2).
+template <int N, int DIR, class Load>
+__device__ __forceinline__ void plane_fft(float2* buf, const float2* tw, Load load,
+                                          float2 (&hold)[Plane<N>::LPT][Plane<N>::NB][Plane<N>::R2]) {
+    using P = Plane<N>;
+    const int t = threadIdx.x;
+    // transform along the row index r, one line per column c
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int u = t + P::THREADS * l, i = u / N, c = u % N;
+        float2 a[P::R1];
+#pragma unroll
+        for (int j = 0; j < P::R1; j++) a[j] = load(j * P::R2 + i, c);
+        dft_reg<P::R1, DIR>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < P::R1; k1++) a[k1] = cmul(a[k1], tw_get<N, DIR>(tw, i * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < P::R1; k1++) buf[(k1 * P::R2 + i) * P::S + c] = a[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int u = t + P::THREADS * l, i = u / N, c = u % N;
+#pragma unroll
+        for (int q = 0; q < P::NB; q++) {
+            const int k1 = i + P::R2 * q;
+#pragma unroll
+            for (int i2 = 0; i2 < P::R2; i2++) hold[l][q][i2] = buf[(k1 * P::R2 + i2) * P::S + c];
+            dft_reg<P::R2, DIR>(hold[l][q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int u = t + P::THREADS * l, i = u / N, c = u % N;
+#pragma unroll
+        for (int q = 0; q < P::NB; q++)
+#pragma unroll
+            for (int k2 = 0; k2 < P::R2; k2++) buf[(i + P::R2 * q + P::R1 * k2) * P::S + c] = hold[l][q][k2];
+    }
+    __syncthreads();
+    // transform along the column index, one line per row r
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int u = t + P::THREADS * l, i = u / N, r = u % N;
+        float2 a[P::R1];
+#pragma unroll
+        for (int j = 0; j < P::R1; j++) a[j] = buf[r * P::S + j * P::R2 + i];
+        dft_reg<P::R1, DIR>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < P::R1; k1++) a[k1] = cmul(a[k1], tw_get<N, DIR>(tw, i * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < P::R1; k1++) buf[r * P::S + k1 * P::R2 + i] = a[k1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int u = t + P::THREADS * l, i = u / N, r = u % N;
+#pragma unroll
+        for (int q = 0; q < P::NB; q++) {
+            const int k1 = i + P::R2 * q;
+#pragma unroll
+            for (int i2 = 0; i2 < P::R2; i2++) hold[l][q][i2] = buf[r * P::S + k1 * P::R2 + i2];
+            dft_reg<P::R2, DIR>(hold[l][q]);
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ int plane_row(int l) { return (threadIdx.x + Plane<N>::THREADS * l) % N; }
+template <int N>
+__device__ __forceinline__ int plane_col(int l, int q, int k2) {
+    using P = Plane<N>;
+    const int i = (threadIdx.x + P::THREADS * l) / N;
+    return i + P::R2 * q + P::R1 * k2;
+}
+
+// After plane_fft: write hold to dst[r][c] (n x n, natural order) through shared memory.
+template <int N>
+__device__ __forceinline__ void plane_store(float2* buf,
+                                            const float2 (&hold)[Plane<N>::LPT][Plane<N>::NB][Plane<N>::R2],
+                                            float2* dst) {
+    using P = Plane<N>;
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++)
+#pragma unroll
+        for (int q = 0; q < P::NB; q++)
+#pragma unroll
+            for (int k2 = 0; k2 < P::R2; k2++) buf[plane_row<N>(l) * P::S + plane_col<N>(l, q, k2)] = hold[l][q][k2];
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += P::THREADS) dst[e] = buf[(e / N) * P::S + (e % N)];
+}
+
+struct Pass1Args {
+    const float2* spec;        // [n_z][nh][n][n]
+    float2* inter;             // [P slots][G][nh][n][n]
+    const PairInfo* pairs;
+    const float* wtab;         // [walker][max_radii][n_m2]
+    int max_radii, n_m2;
+    int pair0, n_pairs, j0, G;
+};
+
+// Pass 1: delta_hat(k) W(|k| R) -> inverse 2D FFT over (kx, ky) for one kz plane of one
+// (walker, redshift, radius) task.
+template <int N>
+__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_filter_inverse(Pass1Args a) {
+    using P = Plane<N>;
+    constexpr int NH = N / 2 + 1;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = smem + N * P::S;
+    const int kz = blockIdx.x, tg = blockIdx.y, slot = blockIdx.z;
+    const int pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    const int n_r = a.pairs[pair].n_r, w = a.pairs[pair].w, zi = a.pairs[pair].zi;
+    const int j = a.j0 + tg;
+    if (j >= n_r) return;
+    fill_twiddles<N>(tw);
+    __syncthreads();
+    const float2* src = a.spec + ((size_t)zi * NH + kz) * N * N;
+    const float* wt = a.wtab + ((size_t)w * a.max_radii + j) * a.n_m2;
+    const int mz2 = kz * kz;
+    auto load = [&](int r, int c) {
+        const int mx = signed_index(r, N), my = signed_index(c, N);
+        const float wv = __ldg(wt + mx * mx + my * my + mz2);
+        const float2 v = __ldg(src + r * N + c);
+        return make_float2(v.x * wv, v.y * wv);
+    };
+    float2 hold[P::LPT][P::NB][P::R2];
+    plane_fft<N, +1>(buf, tw, load, hold);
+    float2* dst = a.inter + (((size_t)slot * a.G + tg) * NH + kz) * N * N;
+    plane_store<N>(buf, hold, dst);
+}
+
+// Forward 2D FFT of plane kz of src ([nh][n][n], [x][y]) into dst ([nh][n][n], [kx][ky]).
+template <int N>
+__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_forward(const float2* src, float2* dst) {
+    using P = Plane<N>;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = smem + N * P::S;
+    const int kz = blockIdx.x;
+    fill_twiddles<N>(tw);
+    __syncthreads();
+    const float2* s = src + (size_t)kz * N * N;
+    auto load = [&](int r, int c) { return __ldg(s + r * N + c); };
+    float2 hold[P::LPT][P::NB][P::R2];
+    plane_fft<N, -1>(buf, tw, load, hold);
+    plane_store<N>(buf, hold, dst + (size_t)kz * N * N);
+}
+
+struct PSArgs {
+    const float2* ps_inter;    // [P slots][nh][n][n]  (z already transformed)
+    const PairInfo* pairs;
+    const signed char* bin_of_m2;
+    double* ps_sum;            // [pair][n_bins]
+    int pair0, n_pairs, n_bins;
+    float kf3;                 // (2 pi / L)^3
+};
+
+// Forward 2D FFT of one kz plane of delta T_b's z-transformed box, then the shell sums
+// S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2: the conjugate half).
+template <int N>
+__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_ps(PSArgs a) {
+    using P = Plane<N>;
+    constexpr int NH = N / 2 + 1;
+    constexpr int WARPS = P::THREADS / 32 > 0 ? P::THREADS / 32 : 1;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = smem + N * P::S;
+    __shared__ double s_bins[WARPS][EOR21_MAX_BINS];
+    const int kz = blockIdx.x, slot = blockIdx.y;
+    const int pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    fill_twiddles<N>(tw);
+    for (int e = threadIdx.x; e < WARPS * EOR21_MAX_BINS; e += P::THREADS) (&s_bins[0][0])[e] = 0.0;
+    __syncthreads();
+    const float2* s = a.ps_inter + ((size_t)slot * NH + kz) * N * N;
+    auto load = [&](int r, int c) { return __ldg(s + r * N + c); };
+    float2 hold[P::LPT][P::NB][P::R2];
+    plane_fft<N, -1>(buf, tw, load, hold);
+    const float weight = (kz == 0 || kz == N / 2) ? 1.0f : 2.0f;
+    const int warp = threadIdx.x / 32;
+    const int mz2 = kz * kz;
+#pragma unroll
+    for (int l = 0; l < P::LPT; l++) {
+        const int mx = signed_index(plane_row<N>(l), N);
+#pragma unroll
+        for (int q = 0; q < P::NB; q++)
+#pragma unroll
+            for (int k2 = 0; k2 < P::R2; k2++) {
+                const int my = signed_index(plane_col<N>(l, q, k2), N);
+                const int m2 = mx * mx + my * my + mz2;
+                const int b = a.bin_of_m2[m2];
+                if (b >= 0) {
+                    const float2 v = hold[l][q][k2];
+                    const float fm2 = (float)m2;
+                    const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (v.x * v.x + v.y * v.y);
+                    atomicAdd(&s_bins[warp][b], (double)val);
+                }
+            }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < a.n_bins; b += P::THREADS) {
+        double sum = 0.0;
+        for (int wi = 0; wi < WARPS; wi++) sum += s_bins[wi][b];
+        if (sum != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], sum);
+    }
+}
+
+// ------------------------------------------------------------------ pencil pass
+
+template <int N>
+struct Pencil {
+    static constexpr int M = N / 2;                      // complex length of the z transform
+    static constexpr int P1 = Split<M>::R1, P2 = Split<M>::R2;
+    static constexpr int TY = N < 32 ? N : 32;           // pencils per CTA (consecutive y)
+    static constexpr int THREADS = TY * P2;
+    static constexpr int NBp = P1 / P2;
+    static constexpr int DS = N + 2;                     // density tile row stride (floats)
+    static constexpr int TILES = N * N / TY;
+    static constexpr size_t SMEM = (size_t)(M + 1) * TY * sizeof(float2) + (size_t)M * TY * sizeof(float2) +
+                                   (size_t)TY * DS * sizeof(float) + N * sizeof(float2);
+};
+
+template <int N>
+struct PencilSmem {
+    float2* xs;   // [(M+1)][TY] half spectrum of the tile's pencils, or Z after a forward core
+    float2* zs;   // [M][TY] exchange
+    float* ds;    // [TY][DS] density / x_HI tile
+    float2* tw;   // [N]
+    __device__ PencilSmem(void* base) {
+        using P = Pencil<N>;
+        char* p = (char*)base;
+        xs = (float2*)p; p += (size_t)(P::M + 1) * P::TY * sizeof(float2);
+        zs = (float2*)p; p += (size_t)P::M * P::TY * sizeof(float2);
+        tw = (float2*)p; p += N * sizeof(float2);
+        ds = (float*)p;
+    }
+};
+
+// Complex-to-real along z for the tile's pencils: xs holds X[k] (k = 0..M) per pencil.
+// On return z[q][k2] = x[2m] + i x[2m+1] with m = i + P2 q + P1 k2 (unnormalised).
+template <int N>
+__device__ __forceinline__ void pencil_c2r(const PencilSmem<N>& s, int p, int i,
+                                           float2 (&z)[Pencil<N>::NBp][Pencil<N>::P2]) {
+    using P = Pencil<N>;
+    float2 a[P::P1];
+#pragma unroll
+    for (int j = 0; j < P::P1; j++) {
+        const int k = j * P::P2 + i;
+        const float2 xk = s.xs[k * P::TY + p], xm = cconj(s.xs[(P::M - k) * P::TY + p]);
+        const float2 sum = cadd(xk, xm), dif = cmul(csub(xk, xm), tw_get<N, +1>(s.tw, k));
+        a[j] = make_float2(sum.x - dif.y, sum.y + dif.x);     // sum + i * dif
+    }
+    dft_reg<P::P1, +1>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < P::P1; k1++) a[k1] = cmul(a[k1], tw_get<N, +1>(s.tw, 2 * i * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < P::P1; k1++) s.zs[(k1 * P::P2 + i) * P::TY + p] = a[k1];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++) {
+        const int k1 = i + P::P2 * q;
+#pragma unroll
+        for (int i2 = 0; i2 < P::P2; i2++) z[q][i2] = s.zs[(k1 * P::P2 + i2) * P::TY + p];
+        dft_reg<P::P2, +1>(z[q]);
+    }
+}
+
+// Real-to-complex along z: z[q][k2] = x[2m] + i x[2m+1] with m = i + P2 q + P1 k2.
+// Writes X[k], k = 0..M, of every pencil to dst[k * kstride + p].
+template <int N>
+__device__ __forceinline__ void pencil_r2c(const PencilSmem<N>& s, int p, int i,
+                                           const float2 (&z)[Pencil<N>::NBp][Pencil<N>::P2], float2* dst,
+                                           size_t kstride) {
+    using P = Pencil<N>;
+    float2 a[P::P1];
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) a[q + P::NBp * k2] = z[q][k2];   // element m = i + P2 * j
+    dft_reg<P::P1, -1>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < P::P1; k1++) a[k1] = cmul(a[k1], tw_get<N, -1>(s.tw, 2 * i * k1));
+    __syncthreads();   // zs and xs may still be read by a previous step
+#pragma unroll
+    for (int k1 = 0; k1 < P::P1; k1++) s.zs[(k1 * P::P2 + i) * P::TY + p] = a[k1];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++) {
+        const int k1 = i + P::P2 * q;
+        float2 b[P::P2];
+#pragma unroll
+        for (int i2 = 0; i2 < P::P2; i2++) b[i2] = s.zs[(k1 * P::P2 + i2) * P::TY + p];
+        dft_reg<P::P2, -1>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) s.xs[(k1 + P::P1 * k2) * P::TY + p] = b[k2];   // Z natural
+    }
+    __syncthreads();
+    for (int k = i; k <= P::M; k += P::P2) {
+        const float2 zk = s.xs[(k % P::M) * P::TY + p];
+        const float2 zm = cconj(s.xs[((P::M - k) % P::M) * P::TY + p]);
+        const float2 e = cscale(cadd(zk, zm), 0.5f);
+        const float2 d = cmul(csub(zk, zm), tw_get<N, -1>(s.tw, k));
+        dst[(size_t)k * kstride + p] = make_float2(e.x + 0.5f * d.y, e.y - 0.5f * d.x);   // e - (i/2) d
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void pencil_load_spectrum(const PencilSmem<N>& s, const float2* src, size_t kstride) {
+    using P = Pencil<N>;
+    const int p = threadIdx.x % P::TY;
+    for (int row = threadIdx.x / P::TY; row <= P::M; row += P::THREADS / P::TY)
+        s.xs[row * P::TY + p] = __ldg(src + (size_t)row * kstride + p);
+}
+
+// Load the tile's TY pencils of a real box (contiguous TY * N floats) into ds.
+template <int N>
+__device__ __forceinline__ void pencil_load_real(const PencilSmem<N>& s, const float* src) {
+    using P = Pencil<N>;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int e = threadIdx.x; e < P::TY * N / 4; e += P::THREADS) {
+        const float4 v = __ldg(s4 + e);
+        const int pp = (4 * e) / N, zz = (4 * e) % N;
+        float2* d = reinterpret_cast<float2*>(s.ds + pp * P::DS + zz);
+        d[0] = make_float2(v.x, v.y);
+        d[1] = make_float2(v.z, v.w);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void pencil_store_real(const PencilSmem<N>& s, float* dst) {
+    using P = Pencil<N>;
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int e = threadIdx.x; e < P::TY * N / 4; e += P::THREADS) {
+        const int pp = (4 * e) / N, zz = (4 * e) % N;
+        const float2* sv = reinterpret_cast<const float2*>(s.ds + pp * P::DS + zz);
+        const float2 u = sv[0], v = sv[1];
+        d4[e] = make_float4(u.x, u.y, v.x, v.y);
+    }
+}
+
+struct Pass2Args {
+    const float2* inter;        // [P slots][G][nh][n][n]
+    const PairInfo* pairs;
+    uint32_t* flags;            // [P slots][TILES][THREADS]
+    const float* delta;         // [n_z][n^3]
+    float* xhi_out;             // optional [pair][n^3]
+    double* xhi_sum;            // [pair]
+    float2* ps_inter;           // [P slots][nh][n][n]
+    int pair0, n_pairs, j0, G;
+    float delta_c;
+};
+
+// Pass 2: for the group of radii j0 .. j0+G-1 of one (walker, redshift): C2R along z,
+// flag |= delta_R >= delta_crit(R). The group that holds R_cell then forms x_HI, delta T_b
+// and delta T_b's R2C along z.
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_ionize(Pass2Args a) {
+    using P = Pencil<N>;
+    constexpr int NH = N / 2 + 1;
+    extern __shared__ __align__(16) float2 smem[];
+    const PencilSmem<N> s(smem);
+    const int tile = blockIdx.x, slot = blockIdx.y;
+    const int pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    const PairInfo& pi = a.pairs[pair];
+    const int n_r = pi.n_r;
+    if (a.j0 >= n_r) return;
+    const int jend = min(a.j0 + a.G, n_r);
+    const bool last = (jend == n_r);
+    const int t = threadIdx.x, p = t % P::TY, i = t / P::TY;
+    const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
+    fill_twiddles<N>(s.tw);
+    const size_t fidx = ((size_t)slot * P::TILES + tile) * P::THREADS + t;
+    uint32_t flags = a.j0 == 0 ? 0u : a.flags[fidx];
+    const float scale = 1.0f / ((float)N * (float)N * (float)N);
+    float2 z[P::NBp][P::P2];
+    for (int j = a.j0; j < jend; j++) {
+        const float2* src = a.inter + (((size_t)slot * a.G + (j - a.j0)) * NH) * N * N + (size_t)x * N + y0;
+        pencil_load_spectrum<N>(s, src, (size_t)N * N);
+        __syncthreads();
+        pencil_c2r<N>(s, p, i, z);
+        const float dcrit = pi.delta_crit[j];
+#pragma unroll
+        for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+            for (int k2 = 0; k2 < P::P2; k2++) {
+                const int bit = 2 * (q * P::P2 + k2);
+                flags |= (uint32_t)(z[q][k2].x * scale >= dcrit) << bit;
+                flags |= (uint32_t)(z[q][k2].y * scale >= dcrit) << (bit + 1);
+            }
+    }
+    if (!last) {
+        a.flags[fidx] = flags;
+        return;
+    }
+    // ---- R_cell reached: partial ionization, x_HI, delta T_b (z holds delta at R_cell)
+    const size_t n3 = (size_t)N * N * N;
+    pencil_load_real<N>(s, a.delta + (size_t)pi.zi * n3 + ((size_t)x * N + y0) * N);
+    __syncthreads();
+    const float zeta = pi.zeta, t0 = pi.t0, inv = pi.inv_sqrt2s2_cell, dc = a.delta_c;
+    const bool cell_ok = pi.cell_ok > 0.5f;
+    float xsum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) {
+            const int m = i + P::P2 * q + P::P1 * k2;
+            const int bit = 2 * (q * P::P2 + k2);
+            float out[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float dr = (h ? z[q][k2].y : z[q][k2].x) * scale;
+                float f = 0.0f;
+                if (cell_ok) f = dr >= dc ? 1.0f : erfcf((dc - dr) * inv);
+                const float xhii = ((flags >> (bit + h)) & 1u) ? 1.0f : fminf(1.0f, zeta * f);
+                const float xhi = 1.0f - xhii;
+                float* cell = s.ds + p * P::DS + 2 * m + h;
+                out[h] = t0 * xhi * (1.0f + *cell);
+                *cell = xhi;
+                xsum += xhi;
+            }
+            z[q][k2] = make_float2(out[0], out[1]);
+        }
+    // neutral-fraction sum (FP64 across the block)
+    double v = (double)xsum;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((t & 31) == 0) atomicAdd(&a.xhi_sum[pair], v);
+    if (a.xhi_out) {
+        __syncthreads();
+        pencil_store_real<N>(s, a.xhi_out + (size_t)pair * n3 + ((size_t)x * N + y0) * N);
+    }
+    float2* dst = a.ps_inter + (size_t)slot * NH * N * N + (size_t)x * N + y0;
+    pencil_r2c<N>(s, p, i, z, dst, (size_t)N * N);
+}
+
+// Forward R2C along z of a real box: src [n^3] -> dst [nh][n][n] ([kz][x][y]).
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_forward(const float* src, float2* dst) {
+    using P = Pencil<N>;
+    extern __shared__ __align__(16) float2 smem[];
+    const PencilSmem<N> s(smem);
+    const int tile = blockIdx.x;
+    const int t = threadIdx.x, p = t % P::TY, i = t / P::TY;
+    const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
+    fill_twiddles<N>(s.tw);
+    pencil_load_real<N>(s, src + ((size_t)x * N + y0) * N);
+    __syncthreads();
+    float2 z[P::NBp][P::P2];
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) {
+            const int m = i + P::P2 * q + P::P1 * k2;
+            z[q][k2] = make_float2(s.ds[p * P::DS + 2 * m], s.ds[p * P::DS + 2 * m + 1]);
+        }
+    pencil_r2c<N>(s, p, i, z, dst + (size_t)x * N + y0, (size_t)N * N);
+}
+
+// Inverse C2R along z of one task's plane-pass output, writing delta_R (normalised).
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_density(const float2* src, float* out) {
+    using P = Pencil<N>;
+    extern __shared__ __align__(16) float2 smem[];
+    const PencilSmem<N> s(smem);
+    const int tile = blockIdx.x;
+    const int t = threadIdx.x, p = t % P::TY, i = t / P::TY;
+    const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
+    fill_twiddles<N>(s.tw);
+    pencil_load_spectrum<N>(s, src + (size_t)x * N + y0, (size_t)N * N);
+    __syncthreads();
+    float2 z[P::NBp][P::P2];
+    pencil_c2r<N>(s, p, i, z);
+    const float scale = 1.0f / ((float)N * (float)N * (float)N);
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) {
+            const int m = i + P::P2 * q + P::P1 * k2;
+            s.ds[p * P::DS + 2 * m] = z[q][k2].x * scale;
+            s.ds[p * P::DS + 2 * m + 1] = z[q][k2].y * scale;
+        }
+    __syncthreads();
+    pencil_store_real<N>(s, out + ((size_t)x * N + y0) * N);
+}
+
+// ------------------------------------------------------------------ spectra and chi^2
+
+// Delta^2 = S_b dx^6 / (2 pi^2 V) / n_b and mean |k| per (pair, bin).
+__global__ void k_finish_spectra(const double* ps_sum, const long long* nmodes, const double* ksum, int n_pairs,
+                                 int n_bins, double scale, double* d2, double* kmean, long long* nmodes_pair) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_pairs * n_bins) return;
+    int b = e % n_bins;
+    long long n = nmodes[b];
+    d2[e] = n > 0 ? ps_sum[e] * scale / (double)n : nan("");
+    kmean[e] = n > 0 ? ksum[b] / (double)n : nan("");
+    nmodes_pair[e] = n;
+}
+
+// Volume-weighted neutral fraction per (walker, redshift).
+__global__ void k_xhi_mean(const double* xhi_sum, int n_pairs, double inv_n3, double* out) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_pairs) out[e] = xhi_sum[e] * inv_n3;
+}
+
+struct Chi2Args {
+    const double* d2;          // [walker][n_z][n_bins]
+    const long long* nmodes;   // [n_bins]
+    const double* mock;        // [n_z][n_bins]
+    const double* sigma;       // [n_z][n_bins]
+    double* chi2;              // [walker]
+    int n_walkers, n_z, n_bins;
+    double k_lo, k_hi, chi_lo, chi_hi;
+};
+
+// chi^2 per walker, summed linearly over redshifts (Sec. 3.4), bins chosen by their
+// geometric centre in [chi_lo, chi_hi] (Sec. 2.5). FP64.
+__global__ void k_chi2(Chi2Args a) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= a.n_walkers) return;
+    double acc = 0.0;
+    for (int zi = 0; zi < a.n_z; zi++)
+        for (int b = 0; b < a.n_bins; b++) {
+            double centre = a.k_lo * pow(a.k_hi / a.k_lo, (b + 0.5) / a.n_bins);
+            if (centre < a.chi_lo || centre > a.chi_hi || a.nmodes[b] == 0) continue;
+            double r = (a.d2[((size_t)w * a.n_z + zi) * a.n_bins + b] - a.mock[zi * a.n_bins + b]) /
+                       a.sigma[zi * a.n_bins + b];
+            acc += r * r;
+        }
+    a.chi2[w] = acc;
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N>
+cudaError_t prepare_n() {
+    cudaError_t e;
+    if ((e = set_smem(k_pencil_forward<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_forward<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_filter_inverse<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_ps<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+template <int N>
+cudaError_t forward_spectrum_n(eor_ctx* c, int zi) {
+    constexpr int NH = N / 2 + 1;
+    float2* tmp = c->d_psinter;   // slot 0 of the PS scratch
+    trace_begin(c, kKForward);
+    k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
+        c->d_delta + (size_t)zi * c->n3, tmp);
+    trace_end(c);
+    trace_begin(c, kKForward);
+    k_plane_forward<N><<<NH, Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(tmp, c->d_spec + (size_t)zi * c->nspec);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
+    constexpr int NH = N / 2 + 1;
+    const int n_pairs = c->n_walkers * c->cfg.n_z;
+    const int G = c->tune.group, P = c->tune.pairs;
+    const int groups = (c->max_radii + G - 1) / G;
+    cudaMemsetAsync(c->d_xhi_sum, 0, sizeof(double) * n_pairs, c->stream);
+    cudaMemsetAsync(c->d_ps_sum, 0, sizeof(double) * n_pairs * c->cfg.n_bins, c->stream);
+    const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
+    for (int pair0 = 0; pair0 < n_pairs; pair0 += P) {
+        for (int g = 0; g < groups; g++) {
+            Pass1Args a1{c->d_spec, c->d_inter, c->d_pairs, c->d_wtab, c->max_radii, c->n_m2,
+                         pair0, n_pairs, g * G, G};
+            trace_begin(c, kKFilterPlane);
+            k_plane_filter_inverse<N><<<dim3(NH, G, P), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(a1);
+            trace_end(c);
+            Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, c->d_delta, xhi_out,
+                         c->d_xhi_sum, c->d_psinter, pair0, n_pairs, g * G, G, (float)c->cfg.delta_c};
+            trace_begin(c, kKPencil);
+            k_pencil_ionize<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(a2);
+            trace_end(c);
+        }
+        PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
+                  kf * kf * kf};
+        trace_begin(c, kKPsPlane);
+        k_plane_ps<N><<<dim3(NH, P), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(ap);
+        trace_end(c);
+    }
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab) {
+    constexpr int NH = N / 2 + 1;
+    cudaError_t e;
+    // one task: walker 0 of a one-radius table at wtab, box zi
+    PairInfo pi{};
+    pi.w = 0; pi.zi = zi; pi.n_r = 1;
+    if ((e = cudaMemcpyAsync(c->d_diag_pair, &pi, sizeof(PairInfo), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
+        return e;
+    Pass1Args a1{c->d_spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
+    trace_begin(c, kKFilterPlane);
+    k_plane_filter_inverse<N><<<dim3(NH, 1, 1), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(a1);
+    trace_end(c);
+    trace_begin(c, kKOther);
+    k_pencil_density<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(c->d_inter, out);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
+    constexpr int NH = N / 2 + 1;
+    const int nb = c->cfg.n_bins;
+    const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
+    cudaError_t e;
+    PairInfo pi{};
+    if ((e = cudaMemcpyAsync(c->d_diag_pair, &pi, sizeof(PairInfo), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(c->d_diag_ps, 0, sizeof(double) * nb, c->stream)) != cudaSuccess) return e;
+    trace_begin(c, kKForward);
+    k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(box, c->d_psinter);
+    trace_end(c);
+    PSArgs ap{c->d_psinter, c->d_diag_pair, c->d_bin_of_m2, c->d_diag_ps, 0, 1, nb, kf * kf * kf};
+    trace_begin(c, kKPsPlane);
+    k_plane_ps<N><<<dim3(NH, 1), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(ap);
+    trace_end(c);
+    const double dx = c->cfg.box_mpc / c->n;
+    const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
+    const double scale = dx * dx * dx * dx * dx * dx / (2.0 * kPi * kPi * vol);
+    trace_begin(c, kKFinish);
+    k_finish_spectra<<<(nb + 255) / 256, 256, 0, c->stream>>>(c->d_diag_ps, c->d_nmodes, c->d_ksum, 1, nb, scale,
+                                                              c->d_diag_ps + nb, c->d_diag_ps + 2 * nb,
+                                                              c->d_diag_cnt);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box) {
+    switch (c->n) {
+        case 16: return box_power_spectrum_n<16>(c, box);
+        case 32: return box_power_spectrum_n<32>(c, box);
+        case 64: return box_power_spectrum_n<64>(c, box);
+        case 128: return box_power_spectrum_n<128>(c, box);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t estimate_launches(const eor_ctx* c) {
+    const int n_pairs = (c->n_walkers > 0 ? c->n_walkers : 1) * c->cfg.n_z;
+    const int batches = (n_pairs + c->tune.pairs - 1) / c->tune.pairs;
+    const int groups = (c->max_radii + c->tune.group - 1) / c->tune.group;
+    return (size_t)batches * (2 * groups + 1) + 2 * (size_t)c->cfg.n_z + 32;
+}
+
+bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+
+cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) {
+    switch (c->n) {
+        case 16: return forward_spectrum_n<16>(c, zi);
+        case 32: return forward_spectrum_n<32>(c, zi);
+        case 64: return forward_spectrum_n<64>(c, zi);
+        case 128: return forward_spectrum_n<128>(c, zi);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
+    switch (c->n) {
+        case 16: return ionization_n<16>(c, xhi_out);
+        case 32: return ionization_n<32>(c, xhi_out);
+        case 64: return ionization_n<64>(c, xhi_out);
+        case 128: return ionization_n<128>(c, xhi_out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_kernels(int n) {
+    switch (n) {
+        case 16: return prepare_n<16>();
+        case 32: return prepare_n<32>();
+        case 64: return prepare_n<64>();
+        case 128: return prepare_n<128>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t flag_words_per_pair(int n) {
+    switch (n) {
+        case 16: return (size_t)Pencil<16>::TILES * Pencil<16>::THREADS;
+        case 32: return (size_t)Pencil<32>::TILES * Pencil<32>::THREADS;
+        case 64: return (size_t)Pencil<64>::TILES * Pencil<64>::THREADS;
+        case 128: return (size_t)Pencil<128>::TILES * Pencil<128>::THREADS;
+        default: return 0;
+    }
+}
+
+cudaError_t launch_xhi_mean(eor_ctx* c) {
+    const int n_pairs = c->n_walkers * c->cfg.n_z;
+    trace_begin(c, kKFinish);
+    k_xhi_mean<<<(n_pairs + 127) / 128, 128, 0, c->stream>>>(c->d_xhi_sum, n_pairs, 1.0 / (double)c->n3,
+                                                              c->d_xhi_mean);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab) {
+    switch (c->n) {
+        case 16: return filtered_density_n<16>(c, zi, out, wtab);
+        case 32: return filtered_density_n<32>(c, zi, out, wtab);
+        case 64: return filtered_density_n<64>(c, zi, out, wtab);
+        case 128: return filtered_density_n<128>(c, zi, out, wtab);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_power_spectrum(eor_ctx* c) {
+    const int n_pairs = c->n_walkers * c->cfg.n_z, nb = c->cfg.n_bins;
+    const double dx = c->cfg.box_mpc / c->n;
+    const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
+    const double scale = dx * dx * dx * dx * dx * dx / (2.0 * kPi * kPi * vol);
+    const int total = n_pairs * nb;
+    trace_begin(c, kKFinish);
+    k_finish_spectra<<<(total + 255) / 256, 256, 0, c->stream>>>(c->d_ps_sum, c->d_nmodes, c->d_ksum, n_pairs, nb,
+                                                                 scale, c->d_d2, c->d_kmean, c->d_nmodes_pair);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chi2(eor_ctx* c) {
+    const eor_config& g = c->cfg;
+    Chi2Args a{c->d_d2, c->d_nmodes, c->d_mock, c->d_mock + g.n_z * g.n_bins, c->d_chi2, c->n_walkers, g.n_z,
+               g.n_bins, g.k_lo, g.k_hi, g.chi2_k_lo, g.chi2_k_hi};
+    trace_begin(c, kKFinish);
+    k_chi2<<<(c->n_walkers + 127) / 128, 128, 0, c->stream>>>(a);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+}  // namespace eor

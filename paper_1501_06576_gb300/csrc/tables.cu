@@ -1,0 +1,387 @@
+// tables.cu — FP64 cosmology and per-walker tables of the excursion-set path, built on
+// the GPU (sm_103a). FP64 is kept to these small tables: the growth factor, the
+// top-hat mass variance sigma^2(R), the virial mass threshold, each walker's radius
+// ladder and the overdensity at which Eq. 1 switches; the per-cell work stays FP32.
+#include <math.h>
+
+#include "eor_internal.cuh"
+
+namespace eor {
+
+namespace {
+
+constexpr int kGL = 8;   // Gauss-Legendre points per panel
+
+// Nodes and weights of the kGL-point Gauss-Legendre rule on [-1, 1], by Newton's method
+// on the Legendre recurrence (one thread per node).
+__device__ void gauss_legendre(double* x, double* w) {
+    int i = threadIdx.x;
+    if (i < kGL) {
+        double z = cos(kPi * (i + 0.75) / (kGL + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 1; k < kGL; k++) {
+                double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+                p0 = p1; p1 = p2;
+            }
+            dp = kGL * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Bardeen et al. (1986) App. G transfer function, q = k / (Omega_m h^2 Mpc^-1).
+__device__ double transfer_bbks(double q) {
+    if (q <= 0.0) return 1.0;
+    double q2 = q * q;
+    double poly = 1.0 + 3.89 * q + 259.21 * q2 + 162.771336 * q2 * q + 2027.16958081 * q2 * q2;
+    return log1p(2.34 * q) / (2.34 * q) / sqrt(sqrt(poly));
+}
+
+__device__ double window_tophat(double x) {
+    if (x < 0.05) {
+        double x2 = x * x;
+        return 1.0 - x2 * (0.1 - x2 * (1.0 / 280.0 - x2 / 15120.0));
+    }
+    double s, c;
+    sincos(x, &s, &c);
+    return 3.0 * (s - x * c) / (x * x * x);
+}
+
+// k^3 T(k)^2 k^n_s W(kR)^2 / (2 pi^2): d sigma^2 / d ln k without the amplitude.
+__device__ double dsigma2_dlnk(double k, double r, double om_h2, double n_s) {
+    double t = transfer_bbks(k / om_h2);
+    double w = window_tophat(k * r);
+    return k * k * k * pow(k, n_s) * t * t * w * w / (2.0 * kPi * kPi);
+}
+
+__device__ double block_sum(double v, double* red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+// One block per radius: sigma^2 shape integral over ln k in [ln 1e-6, ln(1/R)] (panels
+// of width <= 0.1) and over x = kR in [1, min(400, 1e4 R)] (panels of pi/8, resolving
+// the window's oscillation). Beyond x = 400 the integrand is below 1e-10 of the total.
+__global__ void k_sigma2_shape(double lnr_lo, double dlnr, int n_table, double r8, double om_h2,
+                               double n_s, double* out) {
+    __shared__ double gx[kGL], gw[kGL], red[32];
+    gauss_legendre(gx, gw);
+    __syncthreads();
+    int idx = blockIdx.x;
+    double r = idx < n_table ? exp(lnr_lo + dlnr * idx) : r8;
+    double acc = 0.0;
+    // part A: ln k panels
+    double a = log(1e-6), b = log(fmin(1.0 / r, 1e4));
+    int na = (int)ceil((b - a) / 0.1);
+    double ha = (b - a) / na;
+    for (int p = threadIdx.x; p < na; p += blockDim.x) {
+        double lo = a + p * ha;
+        for (int g = 0; g < kGL; g++) {
+            double lnk = lo + 0.5 * ha * (gx[g] + 1.0);
+            acc += 0.5 * ha * gw[g] * dsigma2_dlnk(exp(lnk), r, om_h2, n_s);
+        }
+    }
+    // part B: x panels, integrand in k: (1/k) dsigma2_dlnk, dk = dx / r
+    double x0 = 1.0, x1 = fmin(400.0, 1e4 * r);
+    if (x1 > x0) {
+        int nb = (int)ceil((x1 - x0) / (kPi / 8.0));
+        double hb = (x1 - x0) / nb;
+        for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+            double lo = x0 + p * hb;
+            for (int g = 0; g < kGL; g++) {
+                double x = lo + 0.5 * hb * (gx[g] + 1.0);
+                double k = x / r;
+                acc += 0.5 * hb * gw[g] * dsigma2_dlnk(k, r, om_h2, n_s) / x;
+            }
+        }
+    }
+    double s = block_sum(acc, red);
+    if (threadIdx.x == 0) out[idx] = s;
+}
+
+// amp = sigma_8^2 / shape(8/h); table -> ln(amp * shape).
+__global__ void k_sigma2_normalise(double* shape, int n_table, double sigma8, double* amp_out) {
+    double amp = sigma8 * sigma8 / shape[n_table];
+    for (int i = threadIdx.x; i < n_table; i += blockDim.x) shape[i] = log(amp * shape[i]);
+    if (threadIdx.x == 0) amp_out[0] = amp;
+}
+
+// Linear growth D(z) = E(a) Int_0^a da'/(a' E(a'))^3 / (same at a = 1), flat LCDM;
+// substituting a' = u^2 makes the integrand smooth at 0. One block per redshift.
+__global__ void k_growth(const double* zs, int n_z, double om, double ol, double* out) {
+    __shared__ double gx[kGL], gw[kGL], red[32];
+    gauss_legendre(gx, gw);
+    __syncthreads();
+    const int panels = 256;
+    double res[2];
+    for (int which = 0; which < 2; which++) {
+        double a = which == 0 ? 1.0 / (1.0 + zs[blockIdx.x]) : 1.0;
+        double umax = sqrt(a), h = umax / panels, acc = 0.0;
+        for (int p = threadIdx.x; p < panels; p += blockDim.x) {
+            for (int g = 0; g < kGL; g++) {
+                double u = p * h + 0.5 * h * (gx[g] + 1.0);
+                double ap = u * u;
+                double e = sqrt(om / (ap * ap * ap) + ol);
+                double d = ap * e;
+                acc += 0.5 * h * gw[g] * 2.0 * u / (d * d * d);
+            }
+        }
+        double s = block_sum(acc, red);
+        res[which] = sqrt(om / (a * a * a) + ol) * s;
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = res[0] / res[1];
+}
+
+// Bin of every |m|^2 = mx^2 + my^2 + mz^2 (FP64 decision, -1 outside [k_lo, k_hi) or k = 0).
+__global__ void k_bin_table(int n_m2, double kf, double k_lo, double k_hi, int n_bins, signed char* bin) {
+    int m2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m2 >= n_m2) return;
+    int b = -1;
+    if (m2 > 0) {
+        double k = kf * sqrt((double)m2);
+        if (k >= k_lo && k < k_hi) {
+            b = (int)floor(n_bins * log(k / k_lo) / log(k_hi / k_lo));
+            if (b < 0 || b >= n_bins) b = -1;
+        }
+    }
+    bin[m2] = (signed char)b;
+}
+
+// Mode count and summed |k| per bin over the full n^3 grid (data independent).
+__global__ void k_mode_counts(int n, double kf, const signed char* bin, int n_bins, long long* cnt,
+                              double* ksum) {
+    __shared__ unsigned long long s_cnt[EOR21_MAX_BINS];
+    __shared__ double s_k[EOR21_MAX_BINS];
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) { s_cnt[b] = 0ull; s_k[b] = 0.0; }
+    __syncthreads();
+    long long n3 = (long long)n * n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n3;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int ix = (int)(idx / ((long long)n * n)), iy = (int)((idx / n) % n), iz = (int)(idx % n);
+        int mx = ix < n / 2 ? ix : ix - n, my = iy < n / 2 ? iy : iy - n, mz = iz < n / 2 ? iz : iz - n;
+        int m2 = mx * mx + my * my + mz * mz;
+        int b = bin[m2];
+        if (b >= 0) {
+            atomicAdd(&s_cnt[b], 1ull);
+            atomicAdd(&s_k[b], kf * sqrt((double)m2));
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+        atomicAdd((unsigned long long*)&cnt[b], s_cnt[b]);
+        atomicAdd(&ksum[b], s_k[b]);
+    }
+}
+
+__device__ double interp_lnsig(const double* lnsig, double lnr_lo, double dlnr, double r, int* err) {
+    double u = (log(r) - lnr_lo) / dlnr;
+    int i = (int)floor(u);
+    if (!(i >= 1 && i <= kSigmaTable - 3)) {
+        atomicOr(err, kErrSigmaRange);
+        i = i < 1 ? 1 : kSigmaTable - 3;
+    }
+    double t = u - i;
+    // 4-point Lagrange through i-1, i, i+1, i+2
+    double f0 = lnsig[i - 1], f1 = lnsig[i], f2 = lnsig[i + 1], f3 = lnsig[i + 2];
+    double l0 = -t * (t - 1.0) * (t - 2.0) / 6.0;
+    double l1 = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+    double l2 = -(t + 1.0) * t * (t - 2.0) / 2.0;
+    double l3 = (t + 1.0) * t * (t - 1.0) / 6.0;
+    return exp(l0 * f0 + l1 * f1 + l2 * f2 + l3 * f3);
+}
+
+struct WalkerTableArgs {
+    const double* params;
+    const double* growth;
+    const double* lnsig;
+    double lnr_lo, dlnr;
+    double z[EOR21_MAX_Z];
+    int n_z, n_walkers, max_radii;
+    double r_cell, r_factor, r_mfp_max, delta_c, mu;
+    double h, omega_m, omega_l, omega_b, rho_mean;
+    WalkerInfo* walkers;
+    PairInfo* pairs;
+    int* err;
+};
+
+// One thread per (walker, redshift): M_min (Sec. 2.1.3), ladder (Sec. 2.1), sigma^2 of
+// each radius, the threshold overdensity of Eq. 1 and the partial-ionization constants.
+__global__ void k_walker_tables(WalkerTableArgs a) {
+    int pid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pid >= a.n_walkers * a.n_z) return;
+    int w = pid / a.n_z, zi = pid % a.n_z;
+    double zeta = a.params[3 * w], r_mfp = a.params[3 * w + 1], logt = a.params[3 * w + 2];
+    PairInfo& P = a.pairs[pid];
+    P.w = w; P.zi = zi; P.pad = 0;
+    bool ok = isfinite(zeta) && isfinite(r_mfp) && isfinite(logt) && zeta > 0.0 && r_mfp > 0.0 &&
+              r_mfp <= a.r_mfp_max && logt > 0.0 && logt < 12.0;
+    if (!ok) {
+        atomicOr(a.err, kErrParam);
+        P.n_r = 0;
+        if (zi == 0) a.walkers[w].n_r = 0;
+        return;
+    }
+    // radius ladder: R_mfp, R_mfp / f, ... while above R_cell, then R_cell once
+    double radii[kMaxRadii];
+    int nr = 0;
+    double r = r_mfp;
+    while (r > a.r_cell) {
+        if (nr >= a.max_radii - 1) { atomicOr(a.err, kErrLadder); break; }
+        radii[nr++] = r;
+        r = r / a.r_factor;
+    }
+    radii[nr++] = a.r_cell;
+    P.n_r = nr;
+    if (zi == 0) {
+        a.walkers[w].n_r = nr;
+        for (int j = 0; j < nr; j++) a.walkers[w].radii[j] = radii[j];
+    }
+    // virial temperature -> minimum halo mass at z
+    double zp = 1.0 + a.z[zi];
+    double om_z = a.omega_m * zp * zp * zp / (a.omega_m * zp * zp * zp + a.omega_l);
+    double d = om_z - 1.0;
+    double dc = 18.0 * kPi * kPi + 82.0 * d - 39.0 * d * d;
+    double tvir = pow(10.0, logt);
+    double m_min = 1e8 / a.h * pow(a.mu / 0.6, -1.5) * pow(a.omega_m / om_z * dc / (18.0 * kPi * kPi), -0.5) *
+                   pow(tvir / 1.98e4, 1.5) * pow(zp / 10.0, -1.5);
+    double r_min = cbrt(3.0 * m_min / (4.0 * kPi * a.rho_mean));
+    double g2 = a.growth[zi] * a.growth[zi];
+    double s2_min = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, r_min, a.err);
+    // zeta erfc((delta_c - delta_R) / sqrt(2 s2)) >= 1  <=>  delta_R >= delta_c - sqrt(2 s2) erfcinv(1/zeta)
+    double u_star = zeta >= 1.0 ? erfcinv(1.0 / zeta) : 0.0;
+    double s2 = 0.0;
+    for (int j = 0; j < nr; j++) {
+        s2 = s2_min - g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, radii[j], a.err);
+        double dcrit = (s2 > 0.0 && zeta >= 1.0) ? a.delta_c - sqrt(2.0 * s2) * u_star : INFINITY;
+        P.delta_crit[j] = (float)dcrit;
+    }
+    for (int j = nr; j < kMaxRadii; j++) P.delta_crit[j] = INFINITY;
+    P.zeta = (float)zeta;
+    P.cell_ok = s2 > 0.0 ? 1.0f : 0.0f;
+    P.inv_sqrt2s2_cell = s2 > 0.0 ? (float)(1.0 / sqrt(2.0 * s2)) : 0.0f;
+    double h2 = a.h * a.h;
+    P.t0 = (float)(27.0 * sqrt(zp / 10.0 * 0.15 / (a.omega_m * h2)) * (a.omega_b * h2 / 0.023));
+}
+
+// W(kR) of each walker's radii on the grid's |m|^2 values, FP32: a 12-term series below
+// x = 2 (the closed form cancels there in single precision), the closed form above.
+__device__ __forceinline__ float tophat_f32(float x) {
+    if (x < 2.0f) {
+        float x2 = x * x, term = 1.0f, sum = 1.0f;
+#pragma unroll
+        for (int n = 0; n < 12; n++) {
+            term *= -x2 / (float)((2 * n + 2) * (2 * n + 5));
+            sum += term;
+        }
+        return sum;
+    }
+    float s, c;
+    sincosf(x, &s, &c);
+    return 3.0f * (s - x * c) / (x * x * x);
+}
+
+__global__ void k_window_tables(const WalkerInfo* walkers, int max_radii, int n_m2, float kf, float* wtab) {
+    int m2 = blockIdx.x * blockDim.x + threadIdx.x;
+    int wj = blockIdx.y;
+    int w = wj / max_radii, j = wj % max_radii;
+    if (m2 >= n_m2 || j >= walkers[w].n_r) return;
+    float r = (float)walkers[w].radii[j];
+    wtab[(size_t)wj * n_m2 + m2] = tophat_f32(kf * sqrtf((float)m2) * r);
+}
+
+__global__ void k_window_single(double r, int n_m2, float kf, float* wtab) {
+    int m2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m2 < n_m2) wtab[m2] = tophat_f32(kf * sqrtf((float)m2) * (float)r);
+}
+
+}  // namespace
+
+cudaError_t build_cosmology_tables(eor_ctx* c) {
+    const eor_config& g = c->cfg;
+    double om_h2 = g.omega_m * g.h * g.h;
+    double lnr_lo = log(kSigmaRlo), dlnr = (log(kSigmaRhi) - log(kSigmaRlo)) / (kSigmaTable - 1);
+    trace_begin(c, kKOther);
+    k_sigma2_shape<<<kSigmaTable + 1, 256, 0, c->stream>>>(lnr_lo, dlnr, kSigmaTable, 8.0 / g.h, om_h2,
+                                                           g.n_s, c->d_lnsig);
+    trace_end(c);
+    trace_begin(c, kKOther);
+    k_sigma2_normalise<<<1, 256, 0, c->stream>>>(c->d_lnsig, kSigmaTable, g.sigma8, c->d_cosmo_amp);
+    trace_end(c);
+    double* d_z = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_z, sizeof(double) * g.n_z, c->stream);
+    if (e != cudaSuccess) return e;
+    cudaMemcpyAsync(d_z, g.z, sizeof(double) * g.n_z, cudaMemcpyHostToDevice, c->stream);
+    trace_begin(c, kKOther);
+    k_growth<<<g.n_z, 128, 0, c->stream>>>(d_z, g.n_z, g.omega_m, 1.0 - g.omega_m, c->d_growth);
+    trace_end(c);
+    cudaFreeAsync(d_z, c->stream);
+    double kf = 2.0 * kPi / g.box_mpc;
+    trace_begin(c, kKOther);
+    k_bin_table<<<(c->n_m2 + 255) / 256, 256, 0, c->stream>>>(c->n_m2, kf, g.k_lo, g.k_hi, g.n_bins,
+                                                              c->d_bin_of_m2);
+    trace_end(c);
+    cudaMemsetAsync(c->d_nmodes, 0, sizeof(long long) * g.n_bins, c->stream);
+    cudaMemsetAsync(c->d_ksum, 0, sizeof(double) * g.n_bins, c->stream);
+    trace_begin(c, kKOther);
+    k_mode_counts<<<256, 256, 0, c->stream>>>(c->n, kf, c->d_bin_of_m2, g.n_bins, c->d_nmodes, c->d_ksum);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
+    const eor_config& g = c->cfg;
+    WalkerTableArgs a{};
+    a.params = c->d_params;
+    a.growth = c->d_growth;
+    a.lnsig = c->d_lnsig;
+    a.lnr_lo = log(kSigmaRlo);
+    a.dlnr = (log(kSigmaRhi) - log(kSigmaRlo)) / (kSigmaTable - 1);
+    for (int j = 0; j < g.n_z; j++) a.z[j] = g.z[j];
+    a.n_z = g.n_z;
+    a.n_walkers = n_walkers;
+    a.max_radii = c->max_radii;
+    double dx = g.box_mpc / g.n;
+    a.r_cell = g.r_cell_rule == 1 ? dx : cbrt(3.0 / (4.0 * kPi)) * dx;
+    a.r_factor = g.r_factor;
+    a.r_mfp_max = g.r_mfp_max;
+    a.delta_c = g.delta_c;
+    a.mu = g.mu;
+    a.h = g.h; a.omega_m = g.omega_m; a.omega_l = 1.0 - g.omega_m; a.omega_b = g.omega_b;
+    a.rho_mean = g.omega_m * kRhoCritH2 * g.h * g.h;
+    a.walkers = c->d_walkers;
+    a.pairs = c->d_pairs;
+    a.err = c->d_err;
+    int np = n_walkers * g.n_z;
+    trace_begin(c, kKTables);
+    k_walker_tables<<<(np + 127) / 128, 128, 0, c->stream>>>(a);
+    trace_end(c);
+    dim3 grid((c->n_m2 + 255) / 256, n_walkers * c->max_radii);
+    trace_begin(c, kKTables);
+    k_window_tables<<<grid, 256, 0, c->stream>>>(c->d_walkers, c->max_radii, c->n_m2,
+                                                  (float)(2.0 * kPi / g.box_mpc), c->d_wtab);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab) {
+    trace_begin(c, kKOther);
+    k_window_single<<<(c->n_m2 + 255) / 256, 256, 0, c->stream>>>(r, c->n_m2,
+                                                                  (float)(2.0 * kPi / c->cfg.box_mpc), wtab);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+}  // namespace eor

@@ -1,0 +1,305 @@
+"""Python binding of libeor21 (include/eor21.h): argument marshalling only.
+
+Every step of the likelihood path runs in the library's CUDA kernels; this module
+turns numpy arrays (host memory, EOR_HOST) and CUDA torch tensors (device memory,
+EOR_DEVICE) into pointers and calls the C ABI by the same names. If the shared
+library is missing it raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EOR_OK, EOR_EINVAL, EOR_ENOMEM, EOR_ECUDA, EOR_ETIMEOUT, EOR_ESTATE, EOR_ENOTSUP = range(7)
+EOR_HOST, EOR_DEVICE = 0, 1
+MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
+
+# names exported by include/eor21.h
+EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
+           "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
+           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_trace",
+           "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_last_error", "eor_version",
+           "eor_destroy")
+KERNEL_CLASSES = 7
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class EorConfig(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("box_mpc", ctypes.c_double), ("n_z", ctypes.c_int),
+                ("z", ctypes.c_double * MAX_Z),
+                ("h", ctypes.c_double), ("omega_m", ctypes.c_double), ("omega_b", ctypes.c_double),
+                ("n_s", ctypes.c_double), ("sigma8", ctypes.c_double),
+                ("r_factor", ctypes.c_double), ("r_cell_rule", ctypes.c_int), ("delta_c", ctypes.c_double),
+                ("mu", ctypes.c_double), ("n_bins", ctypes.c_int), ("k_lo", ctypes.c_double),
+                ("k_hi", ctypes.c_double), ("chi2_k_lo", ctypes.c_double), ("chi2_k_hi", ctypes.c_double),
+                ("max_walkers", ctypes.c_int), ("r_mfp_max", ctypes.c_double),
+                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p)]
+
+
+class EorError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libeor21 error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load (building first if allowed) the in-tree libeor21.so; raise if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if build_if_missing and _build.stale():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libeor21 is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "eor_default_config": (None, [ctypes.POINTER(EorConfig)]),
+        "eor_create": (I, [ctypes.POINTER(EorConfig), P, ctypes.POINTER(P)]),
+        "eor_init_boxes": (I, [P, P, I]),
+        "eor_set_params": (I, [P, P, I, I]),
+        "eor_run_ionization": (I, [P, P, P, I]),
+        "eor_power_spectrum": (I, [P, P, P, P, I]),
+        "eor_chi2": (I, [P, P, P, P, I]),
+        "eor_likelihood": (I, [P, P, I, P, P, P, P, I]),
+        "eor_filtered_density": (I, [P, I, D, P, I]),
+        "eor_density_spectrum": (I, [P, I, P, I]),
+        "eor_walker_ladder": (I, [P, I, P, ctypes.POINTER(I)]),
+        "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
+        "eor_trace": (I, [P, I]),
+        "eor_trace_read": (I, [P, P, P, I]),
+        "eor_kernel_class_name": (ctypes.c_char_p, [I]),
+        "eor_launch_count": (ctypes.c_longlong, [P]),
+        "eor_last_error": (ctypes.c_char_p, [P]),
+        "eor_version": (ctypes.c_char_p, []),
+        "eor_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def default_config(**overrides) -> EorConfig:
+    cfg = EorConfig()
+    load_library().eor_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "z":
+            cfg.n_z = len(v)
+            for j, zv in enumerate(v):
+                cfg.z[j] = float(zv)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _arg(x, dtype):
+    """(pointer, mem, keepalive) for a numpy array or a CUDA torch tensor."""
+    if x is None:
+        return None, EOR_HOST, None
+    if _is_torch_cuda(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), EOR_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), EOR_HOST, a
+
+
+class Context:
+    """One libeor21 context (eor_create ... eor_destroy)."""
+
+    def __init__(self, cfg: EorConfig | None = None, stream=None, torch_allocator: bool = False, **overrides):
+        self.lib = load_library()
+        self.cfg = cfg if cfg is not None else default_config(**overrides)
+        self._cb = None
+        if torch_allocator:
+            import torch
+            blocks = {}
+
+            def _alloc(nbytes, _user):
+                try:
+                    ptr = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                             torch.cuda.current_stream().cuda_stream)
+                except Exception:
+                    return None
+                blocks[ptr] = True
+                return ptr
+
+            def _free(ptr, _user):
+                if ptr in blocks:
+                    del blocks[ptr]
+                    torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (_ALLOC(_alloc), _FREE(_free))
+            self.cfg.dev_alloc, self.cfg.dev_free = self._cb
+        handle = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        rc = self.lib.eor_create(ctypes.byref(self.cfg), st, ctypes.byref(handle))
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_last_error(None).decode())
+        self.handle = handle
+        self.n, self.n_z, self.n_bins = self.cfg.n, self.cfg.n_z, self.cfg.n_bins
+        self.n_walkers = 0
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, rc: int):
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _out(self, like_device: bool, shape, dtype):
+        if like_device:
+            import torch
+            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int64: torch.int64}[dtype]
+            return torch.empty(shape, dtype=tdt, device="cuda")
+        return np.empty(shape, dtype=dtype)
+
+    # ---------------------------------------------------------------- C ABI
+    def eor_init_boxes(self, delta):
+        p, mem, keep = _arg(delta, np.float32)
+        self._check(self.lib.eor_init_boxes(self.handle, p, mem))
+
+    def eor_set_params(self, params):
+        p, mem, keep = _arg(params, np.float64)
+        nw = int(keep.shape[0])
+        self._check(self.lib.eor_set_params(self.handle, p, nw, mem))
+        self.n_walkers = nw
+
+    def eor_run_ionization(self, want_xhi: bool = False, device: bool = False):
+        pairs = (self.n_walkers, self.n_z)
+        xhi = self._out(device, pairs + (self.n,) * 3, np.float32) if want_xhi else None
+        mean = self._out(device, pairs, np.float64)
+        px = None if xhi is None else _arg(xhi, np.float32)[0]
+        self._check(self.lib.eor_run_ionization(self.handle, px, _arg(mean, np.float64)[0],
+                                                EOR_DEVICE if device else EOR_HOST))
+        return xhi, mean
+
+    def eor_power_spectrum(self, device: bool = False):
+        shape = (self.n_walkers, self.n_z, self.n_bins)
+        d2 = self._out(device, shape, np.float64)
+        km = self._out(device, shape, np.float64)
+        cnt = self._out(device, shape, np.int64)
+        self._check(self.lib.eor_power_spectrum(self.handle, _arg(d2, np.float64)[0], _arg(km, np.float64)[0],
+                                                _arg(cnt, np.int64)[0], EOR_DEVICE if device else EOR_HOST))
+        return d2, km, cnt
+
+    def eor_chi2(self, mock_d2, sigma):
+        pm, mem, km = _arg(mock_d2, np.float64)
+        ps, mem2, ks = _arg(sigma, np.float64)
+        if mem != mem2:
+            raise ValueError("mock and sigma must both be host or both device")
+        out = self._out(mem == EOR_DEVICE, (self.n_walkers,), np.float64)
+        self._check(self.lib.eor_chi2(self.handle, pm, ps, _arg(out, np.float64)[0], mem))
+        return out
+
+    def eor_likelihood(self, params, mock_d2, sigma, want_d2: bool = False):
+        pp, mem, kp = _arg(params, np.float64)
+        pm, _, km = _arg(mock_d2, np.float64)
+        ps, _, ks = _arg(sigma, np.float64)
+        nw = int(kp.shape[0])
+        dev = mem == EOR_DEVICE
+        chi2 = self._out(dev, (nw,), np.float64)
+        d2 = self._out(dev, (nw, self.n_z, self.n_bins), np.float64) if want_d2 else None
+        self._check(self.lib.eor_likelihood(self.handle, pp, nw, pm, ps, _arg(chi2, np.float64)[0],
+                                            None if d2 is None else _arg(d2, np.float64)[0], mem))
+        self.n_walkers = nw
+        return (chi2, d2) if want_d2 else chi2
+
+    def eor_filtered_density(self, z_index: int, r_mpc: float, device: bool = False):
+        out = self._out(device, (self.n,) * 3, np.float32)
+        self._check(self.lib.eor_filtered_density(self.handle, int(z_index), float(r_mpc),
+                                                  _arg(out, np.float32)[0], EOR_DEVICE if device else EOR_HOST))
+        return out
+
+    def eor_density_spectrum(self, z_index: int) -> np.ndarray:
+        """Half spectrum as complex64 [kz][kx][ky], kz = 0..n/2."""
+        out = np.empty((self.n // 2 + 1, self.n, self.n), dtype=np.complex64)
+        self._check(self.lib.eor_density_spectrum(self.handle, int(z_index), out.ctypes.data_as(ctypes.c_void_p),
+                                                  EOR_HOST))
+        return out
+
+    def eor_walker_ladder(self, walker: int) -> np.ndarray:
+        radii = np.zeros(MAX_RADII, dtype=np.float64)
+        cnt = ctypes.c_int()
+        self._check(self.lib.eor_walker_ladder(self.handle, int(walker), radii.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.byref(cnt)))
+        return radii[:cnt.value].copy()
+
+    def eor_box_power_spectrum(self, box):
+        p, mem, keep = _arg(box, np.float32)
+        dev = mem == EOR_DEVICE
+        d2 = self._out(dev, (self.n_bins,), np.float64)
+        km = self._out(dev, (self.n_bins,), np.float64)
+        cnt = self._out(dev, (self.n_bins,), np.int64)
+        self._check(self.lib.eor_box_power_spectrum(self.handle, p, _arg(d2, np.float64)[0], _arg(km, np.float64)[0],
+                                                    _arg(cnt, np.int64)[0], mem))
+        return d2, km, cnt
+
+    def eor_trace(self, enable: bool = True):
+        self._check(self.lib.eor_trace(self.handle, 1 if enable else 0))
+
+    def eor_trace_read(self) -> dict:
+        """{class name: (milliseconds, launches)} of the last call."""
+        ms = np.zeros(KERNEL_CLASSES)
+        cnt = np.zeros(KERNEL_CLASSES, dtype=np.int64)
+        self._check(self.lib.eor_trace_read(self.handle, ms.ctypes.data_as(ctypes.c_void_p),
+                                            cnt.ctypes.data_as(ctypes.c_void_p), KERNEL_CLASSES))
+        return {self.lib.eor_kernel_class_name(k).decode(): (float(ms[k]), int(cnt[k]))
+                for k in range(KERNEL_CLASSES)}
+
+    def eor_launch_count(self) -> int:
+        return int(self.lib.eor_launch_count(self.handle))
+
+    # short aliases
+    init_boxes = eor_init_boxes
+    set_params = eor_set_params
+    run_ionization = eor_run_ionization
+    power_spectrum = eor_power_spectrum
+    chi2 = eor_chi2
+    likelihood = eor_likelihood
+    filtered_density = eor_filtered_density
+    density_spectrum = eor_density_spectrum
+    walker_ladder = eor_walker_ladder
+    box_power_spectrum = eor_box_power_spectrum
+    trace = eor_trace
+    trace_read = eor_trace_read
+    launch_count = eor_launch_count
+
+
+def version() -> str:
+    return load_library().eor_version().decode()
