@@ -149,6 +149,13 @@ int eor_walker_ladder(eor_ctx* ctx, int walker, double* radii, int* n_radii);
 int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* kmean, long long* nmodes,
                            int mem);
 
+/* Launch schedule of eor_run_ionization / eor_likelihood (results do not depend on it):
+ * group = radii per pencil launch (1..16), pairs = (walker, redshift) pairs in flight
+ * (1..64; scratch memory grows with group * pairs), plane_threads = CTA size of the
+ * 128^3 plane kernels (512 or 1024; ignored for smaller grids). Defaults 8, 8, 512.
+ * Reallocates the scratch buffers and drops the captured graph. */
+int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
+
 /* Tracing (not part of the method). With tracing on, every kernel launch of the
  * following calls is bracketed by CUDA events on the context's stream, also inside the
  * captured graph of eor_likelihood (switching tracing re-captures it). eor_trace_read

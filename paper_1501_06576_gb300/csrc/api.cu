@@ -140,11 +140,20 @@ cudaError_t trace_reserve(eor_ctx* c, size_t pairs) {
 
 namespace eor {
 
+// Record on the context's stream; while the stream is being captured, as an external event
+// node so the graph records it on every replay.
+static void trace_record(eor_ctx* c, cudaEvent_t e) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &st);
+    if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->stream);
+}
+
 void trace_begin(eor_ctx* c, int cls) {
     if (!c->trace_on) return;
     const size_t i = 2 * (size_t)c->trace_used;
     if (i + 1 >= c->trace_events.size()) return;   // pool sized beforehand; beyond it, untraced
-    cudaEventRecord(c->trace_events[i], c->stream);
+    trace_record(c, c->trace_events[i]);
     c->trace_class.push_back(cls);
 }
 
@@ -153,7 +162,7 @@ void trace_end(eor_ctx* c) {
     if (!c->trace_on) return;
     const size_t i = 2 * (size_t)c->trace_used;
     if (i + 1 >= c->trace_events.size() || c->trace_class.size() != (size_t)c->trace_used + 1) return;
-    cudaEventRecord(c->trace_events[i + 1], c->stream);
+    trace_record(c, c->trace_events[i + 1]);
     c->trace_used++;
 }
 
@@ -195,7 +204,7 @@ void eor_destroy(eor_ctx* c) {
                     c->d_nmodes, c->d_ksum, c->d_params, c->d_walkers, c->d_pairs, c->d_wtab, c->d_inter,
                     c->d_flags, c->d_psinter, c->d_ps_sum, c->d_xhi_sum, c->d_chi2, c->d_mock, c->d_d2,
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
-                    c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_err};
+                    c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_err};
     for (void* p : bufs) dev_free(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -263,7 +272,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_d2, pairs * B) && alloc_n(c, &c->d_kmean, pairs * B) &&
               alloc_n(c, &c->d_nmodes_pair, pairs * B) && alloc_n(c, &c->d_scratch_box, c->n3) &&
               alloc_n(c, &c->d_diag_pair, 1) && alloc_n(c, &c->d_diag_wtab, c->n_m2) &&
-              alloc_n(c, &c->d_diag_ps, 4 * B) && alloc_n(c, &c->d_diag_cnt, B) && alloc_n(c, &c->d_err, 1);
+              alloc_n(c, &c->d_diag_ps, 4 * B) && alloc_n(c, &c->d_diag_cnt, B) && alloc_n(c, &c->d_chi2_use, B) &&
+              alloc_n(c, &c->d_err, 1);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed");
@@ -480,6 +490,36 @@ int eor_box_power_spectrum(eor_ctx* c, const float* box, double* d2, double* kme
     if (kmean && (r = copy_out(c, kmean, c->d_diag_ps + 2 * nb, sizeof(double) * nb, mem))) return r;
     if (nmodes && (r = copy_out(c, nmodes, c->d_diag_cnt, sizeof(long long) * nb, mem))) return r;
     return finish(c, mem);
+}
+
+int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
+    if (!c) return EOR_EINVAL;
+    if (group < 1 || group > 16 || pairs < 1 || pairs > 64 || (plane_threads != 512 && plane_threads != 1024))
+        return fail(c, EOR_EINVAL, "tuning out of range (group 1..16, pairs 1..64, plane_threads 512|1024)");
+    CK(cudaStreamSynchronize(c->stream), "tuning");
+    float2* inter = nullptr;
+    uint32_t* flags = nullptr;
+    float2* psinter = nullptr;
+    if (!alloc_n(c, &inter, (size_t)pairs * group * c->nspec) || !alloc_n(c, &flags, (size_t)pairs * c->flag_words) ||
+        !alloc_n(c, &psinter, (size_t)pairs * c->nspec)) {
+        dev_free(c, inter);
+        dev_free(c, flags);
+        dev_free(c, psinter);
+        return fail(c, EOR_ENOMEM, "tuning scratch");
+    }
+    dev_free(c, c->d_inter);
+    dev_free(c, c->d_flags);
+    dev_free(c, c->d_psinter);
+    c->d_inter = inter;
+    c->d_flags = flags;
+    c->d_psinter = psinter;
+    c->tune = eor::Tuning{group, pairs, plane_threads};
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_walkers = -1;
+    }
+    return EOR_OK;
 }
 
 int eor_trace(eor_ctx* c, int enable) {

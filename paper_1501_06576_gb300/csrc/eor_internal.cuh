@@ -60,8 +60,9 @@ enum KernelClass : int {
 };
 
 struct Tuning {
-    int group;        // radii per pencil launch (G)
-    int pairs;        // (walker, redshift) pairs in flight (P)
+    int group;          // radii per pencil launch (G)
+    int pairs;          // (walker, redshift) pairs in flight (P)
+    int plane_threads;  // CTA size of the 128^3 plane kernels (512 or 1024)
 };
 
 }  // namespace eor
@@ -74,7 +75,7 @@ struct eor_ctx {
     int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
     size_t n3 = 0, nspec = 0;
     eor::CosmoParams cosmo{};
-    eor::Tuning tune{4, 2};
+    eor::Tuning tune{8, 8, 512};
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]
@@ -83,6 +84,7 @@ struct eor_ctx {
     double* d_growth = nullptr;      // [n_z]
     double* d_cosmo_amp = nullptr;   // [1] P(k) amplitude
     signed char* d_bin_of_m2 = nullptr;   // [n_m2] bin of |m|^2 or -1
+    signed char* d_chi2_use = nullptr;    // [n_bins] 1 where the bin enters chi^2
     long long* d_nmodes = nullptr;   // [n_bins]
     double* d_ksum = nullptr;        // [n_bins]
     double* d_params = nullptr;      // [max_walkers][3]

@@ -50,47 +50,73 @@ __device__ __forceinline__ float2 rot16(float2 v) {
     }
 }
 
-template <int R>
-__host__ __device__ constexpr int bitrev(int i) {
-    int r = 0;
-    for (int b = 1; b < R; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
-    return r;
+// Multiply by DIR * i.
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 v) {
+    return DIR > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
 }
 
-// In-register R-point DFT (R = 2, 4, 8 or 16), natural order in and out.
+// Straight-line DFT codelets (natural order in and out). Written out statement by
+// statement so that every value stays in a register.
+template <int DIR>
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+    const float2 t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_i<DIR>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+// 8 points: two 4-point DFTs on the even and odd samples, then twiddles w8^k and butterflies.
+template <int DIR>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    dft4<DIR>(v[0], v[2], v[4], v[6]);
+    dft4<DIR>(v[1], v[3], v[5], v[7]);
+    const float2 o0 = v[1], o1 = rot16<2, DIR>(v[3]), o2 = rot16<4, DIR>(v[5]), o3 = rot16<6, DIR>(v[7]);
+    const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+// 16 points as 4 x 4: DFT over n1 of x[n2 + 4 n1], twiddle w16^(n2 k1), DFT over n2;
+// X[k1 + 4 k2] ends in v[4 k1 + k2] and is renamed into natural order.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    dft4<DIR>(v[0], v[4], v[8], v[12]);
+    dft4<DIR>(v[1], v[5], v[9], v[13]);
+    dft4<DIR>(v[2], v[6], v[10], v[14]);
+    dft4<DIR>(v[3], v[7], v[11], v[15]);
+    v[5] = rot16<1, DIR>(v[5]);  v[6] = rot16<2, DIR>(v[6]);  v[7] = rot16<3, DIR>(v[7]);
+    v[9] = rot16<2, DIR>(v[9]);  v[10] = rot16<4, DIR>(v[10]); v[11] = rot16<6, DIR>(v[11]);
+    v[13] = rot16<3, DIR>(v[13]); v[14] = rot16<6, DIR>(v[14]); v[15] = rot16<9, DIR>(v[15]);
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+    dft4<DIR>(v[4], v[5], v[6], v[7]);
+    dft4<DIR>(v[8], v[9], v[10], v[11]);
+    dft4<DIR>(v[12], v[13], v[14], v[15]);
+    const float2 t1 = v[1], t2 = v[2], t3 = v[3], t6 = v[6], t7 = v[7], t11 = v[11];
+    v[1] = v[4]; v[2] = v[8]; v[3] = v[12];
+    v[4] = t1; v[6] = v[9]; v[7] = v[13];
+    v[8] = t2; v[9] = t6; v[11] = v[14];
+    v[12] = t3; v[13] = t7; v[14] = t11;
+}
+
+// In-register R-point DFT (R = 1, 2, 4, 8 or 16), natural order in and out.
 template <int R, int DIR>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
-    if constexpr (R == 1) return;
-    float2 t[R];
-#pragma unroll
-    for (int i = 0; i < R; i++) t[i] = v[bitrev<R>(i)];
-#pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
-#pragma unroll
-        for (int base = 0; base < R; base += len) {
-#pragma unroll
-            for (int k = 0; k < len / 2; k++) {
-                float2 a = t[base + k];
-                float2 b = t[base + k + len / 2];
-                // twiddle w_len^(DIR*k) = w_16^(DIR*k*16/len)
-                switch (k * (16 / len)) {
-                    case 0: break;
-                    case 1: b = rot16<1, DIR>(b); break;
-                    case 2: b = rot16<2, DIR>(b); break;
-                    case 3: b = rot16<3, DIR>(b); break;
-                    case 4: b = rot16<4, DIR>(b); break;
-                    case 5: b = rot16<5, DIR>(b); break;
-                    case 6: b = rot16<6, DIR>(b); break;
-                    case 7: b = rot16<7, DIR>(b); break;
-                }
-                t[base + k] = cadd(a, b);
-                t[base + k + len / 2] = csub(a, b);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < R; i++) v[i] = t[i];
+    if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<DIR>(v);
+    else if constexpr (R == 16) dft16<DIR>(v);
 }
 
 // Radix split of each supported length: N = R1 * R2 with R1 >= R2.

@@ -28,12 +28,12 @@ __device__ __forceinline__ int signed_index(int i, int n) { return i < n / 2 ? i
 
 // ------------------------------------------------------------------ plane pass
 
-template <int N>
+template <int N, int TMAX = 512>
 struct Plane {
     static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
     static constexpr int S = N + 1;                        // padded row stride (float2)
     static constexpr int UNITS = N * R2;                   // (line, team member) pairs per pass
-    static constexpr int THREADS = UNITS < 512 ? UNITS : 512;
+    static constexpr int THREADS = UNITS < TMAX ? UNITS : TMAX;
     static constexpr int LPT = UNITS / THREADS;            // lines per thread per pass
     static constexpr int NB = R1 / R2;                     // stage-B DFTs per unit
     static constexpr size_t SMEM = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 64 * sizeof(double);
@@ -41,10 +41,10 @@ struct Plane {
 
 // 2D FFT of an n x n complex plane. load(r, c) gives the natural-order input; on return
 // hold[l][q][k2] is the output at row rowOf(l) and column colOf(l, q, k2).
-template <int N, int DIR, class Load>
+template <int N, int T, int DIR, class Load>
 __device__ __forceinline__ void plane_fft(float2* buf, const float2* tw, Load load,
-                                          float2 (&hold)[Plane<N>::LPT][Plane<N>::NB][Plane<N>::R2]) {
-    using P = Plane<N>;
+                                          float2 (&hold)[Plane<N, T>::LPT][Plane<N, T>::NB][Plane<N, T>::R2]) {
+    using P = Plane<N, T>;
     const int t = threadIdx.x;
     // transform along the row index r, one line per column c
 #pragma unroll
@@ -108,28 +108,28 @@ __device__ __forceinline__ void plane_fft(float2* buf, const float2* tw, Load lo
     }
 }
 
-template <int N>
-__device__ __forceinline__ int plane_row(int l) { return (threadIdx.x + Plane<N>::THREADS * l) % N; }
-template <int N>
+template <int N, int T>
+__device__ __forceinline__ int plane_row(int l) { return (threadIdx.x + Plane<N, T>::THREADS * l) % N; }
+template <int N, int T>
 __device__ __forceinline__ int plane_col(int l, int q, int k2) {
-    using P = Plane<N>;
+    using P = Plane<N, T>;
     const int i = (threadIdx.x + P::THREADS * l) / N;
     return i + P::R2 * q + P::R1 * k2;
 }
 
 // After plane_fft: write hold to dst[r][c] (n x n, natural order) through shared memory.
-template <int N>
+template <int N, int T>
 __device__ __forceinline__ void plane_store(float2* buf,
-                                            const float2 (&hold)[Plane<N>::LPT][Plane<N>::NB][Plane<N>::R2],
+                                            const float2 (&hold)[Plane<N, T>::LPT][Plane<N, T>::NB][Plane<N, T>::R2],
                                             float2* dst) {
-    using P = Plane<N>;
+    using P = Plane<N, T>;
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < P::LPT; l++)
 #pragma unroll
         for (int q = 0; q < P::NB; q++)
 #pragma unroll
-            for (int k2 = 0; k2 < P::R2; k2++) buf[plane_row<N>(l) * P::S + plane_col<N>(l, q, k2)] = hold[l][q][k2];
+            for (int k2 = 0; k2 < P::R2; k2++) buf[plane_row<N, T>(l) * P::S + plane_col<N, T>(l, q, k2)] = hold[l][q][k2];
     __syncthreads();
     for (int e = threadIdx.x; e < N * N; e += P::THREADS) dst[e] = buf[(e / N) * P::S + (e % N)];
 }
@@ -145,9 +145,9 @@ struct Pass1Args {
 
 // Pass 1: delta_hat(k) W(|k| R) -> inverse 2D FFT over (kx, ky) for one kz plane of one
 // (walker, redshift, radius) task.
-template <int N>
-__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_filter_inverse(Pass1Args a) {
-    using P = Plane<N>;
+template <int N, int T>
+__global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_filter_inverse(Pass1Args a) {
+    using P = Plane<N, T>;
     constexpr int NH = N / 2 + 1;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
@@ -170,15 +170,15 @@ __global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_filter_inverse(P
         return make_float2(v.x * wv, v.y * wv);
     };
     float2 hold[P::LPT][P::NB][P::R2];
-    plane_fft<N, +1>(buf, tw, load, hold);
+    plane_fft<N, T, +1>(buf, tw, load, hold);
     float2* dst = a.inter + (((size_t)slot * a.G + tg) * NH + kz) * N * N;
-    plane_store<N>(buf, hold, dst);
+    plane_store<N, T>(buf, hold, dst);
 }
 
 // Forward 2D FFT of plane kz of src ([nh][n][n], [x][y]) into dst ([nh][n][n], [kx][ky]).
-template <int N>
-__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_forward(const float2* src, float2* dst) {
-    using P = Plane<N>;
+template <int N, int T>
+__global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_forward(const float2* src, float2* dst) {
+    using P = Plane<N, T>;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = smem + N * P::S;
@@ -188,8 +188,8 @@ __global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_forward(const fl
     const float2* s = src + (size_t)kz * N * N;
     auto load = [&](int r, int c) { return __ldg(s + r * N + c); };
     float2 hold[P::LPT][P::NB][P::R2];
-    plane_fft<N, -1>(buf, tw, load, hold);
-    plane_store<N>(buf, hold, dst + (size_t)kz * N * N);
+    plane_fft<N, T, -1>(buf, tw, load, hold);
+    plane_store<N, T>(buf, hold, dst + (size_t)kz * N * N);
 }
 
 struct PSArgs {
@@ -203,9 +203,9 @@ struct PSArgs {
 
 // Forward 2D FFT of one kz plane of delta T_b's z-transformed box, then the shell sums
 // S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2: the conjugate half).
-template <int N>
-__global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_ps(PSArgs a) {
-    using P = Plane<N>;
+template <int N, int T>
+__global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) {
+    using P = Plane<N, T>;
     constexpr int NH = N / 2 + 1;
     constexpr int WARPS = P::THREADS / 32 > 0 ? P::THREADS / 32 : 1;
     extern __shared__ __align__(16) float2 smem[];
@@ -221,18 +221,18 @@ __global__ void __launch_bounds__(Plane<N>::THREADS, 1) k_plane_ps(PSArgs a) {
     const float2* s = a.ps_inter + ((size_t)slot * NH + kz) * N * N;
     auto load = [&](int r, int c) { return __ldg(s + r * N + c); };
     float2 hold[P::LPT][P::NB][P::R2];
-    plane_fft<N, -1>(buf, tw, load, hold);
+    plane_fft<N, T, -1>(buf, tw, load, hold);
     const float weight = (kz == 0 || kz == N / 2) ? 1.0f : 2.0f;
     const int warp = threadIdx.x / 32;
     const int mz2 = kz * kz;
 #pragma unroll
     for (int l = 0; l < P::LPT; l++) {
-        const int mx = signed_index(plane_row<N>(l), N);
+        const int mx = signed_index(plane_row<N, T>(l), N);
 #pragma unroll
         for (int q = 0; q < P::NB; q++)
 #pragma unroll
             for (int k2 = 0; k2 < P::R2; k2++) {
-                const int my = signed_index(plane_col<N>(l, q, k2), N);
+                const int my = signed_index(plane_col<N, T>(l, q, k2), N);
                 const int m2 = mx * mx + my * my + mz2;
                 const int b = a.bin_of_m2[m2];
                 if (b >= 0) {
@@ -551,24 +551,23 @@ __global__ void k_xhi_mean(const double* xhi_sum, int n_pairs, double inv_n3, do
 
 struct Chi2Args {
     const double* d2;          // [walker][n_z][n_bins]
+    const signed char* use;    // [n_bins] 1 where the bin enters chi^2
     const long long* nmodes;   // [n_bins]
     const double* mock;        // [n_z][n_bins]
     const double* sigma;       // [n_z][n_bins]
     double* chi2;              // [walker]
     int n_walkers, n_z, n_bins;
-    double k_lo, k_hi, chi_lo, chi_hi;
 };
 
-// chi^2 per walker, summed linearly over redshifts (Sec. 3.4), bins chosen by their
-// geometric centre in [chi_lo, chi_hi] (Sec. 2.5). FP64.
+// chi^2 per walker, summed linearly over redshifts (Sec. 3.4) over the bins the table
+// marks (geometric centre in [chi2_k_lo, chi2_k_hi], Sec. 2.5). FP64.
 __global__ void k_chi2(Chi2Args a) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= a.n_walkers) return;
     double acc = 0.0;
     for (int zi = 0; zi < a.n_z; zi++)
         for (int b = 0; b < a.n_bins; b++) {
-            double centre = a.k_lo * pow(a.k_hi / a.k_lo, (b + 0.5) / a.n_bins);
-            if (centre < a.chi_lo || centre > a.chi_hi || a.nmodes[b] == 0) continue;
+            if (!a.use[b] || a.nmodes[b] == 0) continue;
             double r = (a.d2[((size_t)w * a.n_z + zi) * a.n_bins + b] - a.mock[zi * a.n_bins + b]) /
                        a.sigma[zi * a.n_bins + b];
             acc += r * r;
@@ -583,19 +582,19 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N>
+template <int N, int T>
 cudaError_t prepare_n() {
     cudaError_t e;
     if ((e = set_smem(k_pencil_forward<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_forward<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_filter_inverse<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_forward<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_filter_inverse<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_ps<N>, Plane<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-template <int N>
+template <int N, int T>
 cudaError_t forward_spectrum_n(eor_ctx* c, int zi) {
     constexpr int NH = N / 2 + 1;
     float2* tmp = c->d_psinter;   // slot 0 of the PS scratch
@@ -604,12 +603,13 @@ cudaError_t forward_spectrum_n(eor_ctx* c, int zi) {
         c->d_delta + (size_t)zi * c->n3, tmp);
     trace_end(c);
     trace_begin(c, kKForward);
-    k_plane_forward<N><<<NH, Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(tmp, c->d_spec + (size_t)zi * c->nspec);
+    k_plane_forward<N, T><<<NH, Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(
+        tmp, c->d_spec + (size_t)zi * c->nspec);
     trace_end(c);
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int T>
 cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
     constexpr int NH = N / 2 + 1;
     const int n_pairs = c->n_walkers * c->cfg.n_z;
@@ -623,7 +623,7 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
             Pass1Args a1{c->d_spec, c->d_inter, c->d_pairs, c->d_wtab, c->max_radii, c->n_m2,
                          pair0, n_pairs, g * G, G};
             trace_begin(c, kKFilterPlane);
-            k_plane_filter_inverse<N><<<dim3(NH, G, P), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(a1);
+            k_plane_filter_inverse<N, T><<<dim3(NH, G, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
             trace_end(c);
             Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, c->d_delta, xhi_out,
                          c->d_xhi_sum, c->d_psinter, pair0, n_pairs, g * G, G, (float)c->cfg.delta_c};
@@ -634,13 +634,13 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         trace_begin(c, kKPsPlane);
-        k_plane_ps<N><<<dim3(NH, P), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(ap);
+        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
         trace_end(c);
     }
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int T>
 cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab) {
     constexpr int NH = N / 2 + 1;
     cudaError_t e;
@@ -652,7 +652,7 @@ cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab
         return e;
     Pass1Args a1{c->d_spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
     trace_begin(c, kKFilterPlane);
-    k_plane_filter_inverse<N><<<dim3(NH, 1, 1), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(a1);
+    k_plane_filter_inverse<N, T><<<dim3(NH, 1, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
     trace_end(c);
     trace_begin(c, kKOther);
     k_pencil_density<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(c->d_inter, out);
@@ -660,7 +660,7 @@ cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int T>
 cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     constexpr int NH = N / 2 + 1;
     const int nb = c->cfg.n_bins;
@@ -676,7 +676,7 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     trace_end(c);
     PSArgs ap{c->d_psinter, c->d_diag_pair, c->d_bin_of_m2, c->d_diag_ps, 0, 1, nb, kf * kf * kf};
     trace_begin(c, kKPsPlane);
-    k_plane_ps<N><<<dim3(NH, 1), Plane<N>::THREADS, Plane<N>::SMEM, c->stream>>>(ap);
+    k_plane_ps<N, T><<<dim3(NH, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
     trace_end(c);
     const double dx = c->cfg.box_mpc / c->n;
     const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
@@ -689,17 +689,20 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     return cudaGetLastError();
 }
 
+// Grid-size dispatch; the 128^3 plane kernels come in 512- and 1024-thread CTAs.
+#define EOR_DISPATCH(c, FN, ...)                                                            \
+    switch ((c)->n) {                                                                       \
+        case 16: return FN<16, 512>(__VA_ARGS__);                                           \
+        case 32: return FN<32, 512>(__VA_ARGS__);                                           \
+        case 64: return FN<64, 512>(__VA_ARGS__);                                           \
+        case 128:                                                                           \
+            return (c)->tune.plane_threads >= 1024 ? FN<128, 1024>(__VA_ARGS__) : FN<128, 512>(__VA_ARGS__); \
+        default: return cudaErrorInvalidValue;                                              \
+    }
+
 }  // namespace
 
-cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box) {
-    switch (c->n) {
-        case 16: return box_power_spectrum_n<16>(c, box);
-        case 32: return box_power_spectrum_n<32>(c, box);
-        case 64: return box_power_spectrum_n<64>(c, box);
-        case 128: return box_power_spectrum_n<128>(c, box);
-        default: return cudaErrorInvalidValue;
-    }
-}
+cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box) { EOR_DISPATCH(c, box_power_spectrum_n, c, box) }
 
 size_t estimate_launches(const eor_ctx* c) {
     const int n_pairs = (c->n_walkers > 0 ? c->n_walkers : 1) * c->cfg.n_z;
@@ -710,32 +713,23 @@ size_t estimate_launches(const eor_ctx* c) {
 
 bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 
-cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) {
-    switch (c->n) {
-        case 16: return forward_spectrum_n<16>(c, zi);
-        case 32: return forward_spectrum_n<32>(c, zi);
-        case 64: return forward_spectrum_n<64>(c, zi);
-        case 128: return forward_spectrum_n<128>(c, zi);
-        default: return cudaErrorInvalidValue;
-    }
-}
+cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) { EOR_DISPATCH(c, forward_spectrum_n, c, zi) }
 
-cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
-    switch (c->n) {
-        case 16: return ionization_n<16>(c, xhi_out);
-        case 32: return ionization_n<32>(c, xhi_out);
-        case 64: return ionization_n<64>(c, xhi_out);
-        case 128: return ionization_n<128>(c, xhi_out);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) { EOR_DISPATCH(c, ionization_n, c, xhi_out) }
+
+cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab) {
+    EOR_DISPATCH(c, filtered_density_n, c, zi, out, wtab)
 }
 
 cudaError_t prepare_kernels(int n) {
     switch (n) {
-        case 16: return prepare_n<16>();
-        case 32: return prepare_n<32>();
-        case 64: return prepare_n<64>();
-        case 128: return prepare_n<128>();
+        case 16: return prepare_n<16, 512>();
+        case 32: return prepare_n<32, 512>();
+        case 64: return prepare_n<64, 512>();
+        case 128: {
+            cudaError_t e = prepare_n<128, 512>();
+            return e != cudaSuccess ? e : prepare_n<128, 1024>();
+        }
         default: return cudaErrorInvalidValue;
     }
 }
@@ -759,16 +753,6 @@ cudaError_t launch_xhi_mean(eor_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab) {
-    switch (c->n) {
-        case 16: return filtered_density_n<16>(c, zi, out, wtab);
-        case 32: return filtered_density_n<32>(c, zi, out, wtab);
-        case 64: return filtered_density_n<64>(c, zi, out, wtab);
-        case 128: return filtered_density_n<128>(c, zi, out, wtab);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t launch_power_spectrum(eor_ctx* c) {
     const int n_pairs = c->n_walkers * c->cfg.n_z, nb = c->cfg.n_bins;
     const double dx = c->cfg.box_mpc / c->n;
@@ -784,8 +768,8 @@ cudaError_t launch_power_spectrum(eor_ctx* c) {
 
 cudaError_t launch_chi2(eor_ctx* c) {
     const eor_config& g = c->cfg;
-    Chi2Args a{c->d_d2, c->d_nmodes, c->d_mock, c->d_mock + g.n_z * g.n_bins, c->d_chi2, c->n_walkers, g.n_z,
-               g.n_bins, g.k_lo, g.k_hi, g.chi2_k_lo, g.chi2_k_hi};
+    Chi2Args a{c->d_d2, c->d_chi2_use, c->d_nmodes, c->d_mock, c->d_mock + g.n_z * g.n_bins, c->d_chi2, c->n_walkers,
+               g.n_z, g.n_bins};
     trace_begin(c, kKFinish);
     k_chi2<<<(c->n_walkers + 127) / 128, 128, 0, c->stream>>>(a);
     trace_end(c);

@@ -186,6 +186,14 @@ __global__ void k_mode_counts(int n, double kf, const signed char* bin, int n_bi
     }
 }
 
+// Bins that enter chi^2: geometric centre k_lo (k_hi/k_lo)^((b + 1/2)/n_bins) in [lo, hi].
+__global__ void k_chi2_bins(int n_bins, double k_lo, double k_hi, double lo, double hi, signed char* use) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bins) return;
+    double centre = k_lo * pow(k_hi / k_lo, (b + 0.5) / n_bins);
+    use[b] = (centre >= lo && centre <= hi) ? 1 : 0;
+}
+
 __device__ double interp_lnsig(const double* lnsig, double lnr_lo, double dlnr, double r, int* err) {
     double u = (log(r) - lnr_lo) / dlnr;
     int i = (int)floor(u);
@@ -332,6 +340,9 @@ cudaError_t build_cosmology_tables(eor_ctx* c) {
     trace_begin(c, kKOther);
     k_bin_table<<<(c->n_m2 + 255) / 256, 256, 0, c->stream>>>(c->n_m2, kf, g.k_lo, g.k_hi, g.n_bins,
                                                               c->d_bin_of_m2);
+    trace_end(c);
+    trace_begin(c, kKOther);
+    k_chi2_bins<<<1, 64, 0, c->stream>>>(g.n_bins, g.k_lo, g.k_hi, g.chi2_k_lo, g.chi2_k_hi, c->d_chi2_use);
     trace_end(c);
     cudaMemsetAsync(c->d_nmodes, 0, sizeof(long long) * g.n_bins, c->stream);
     cudaMemsetAsync(c->d_ksum, 0, sizeof(double) * g.n_bins, c->stream);

@@ -21,7 +21,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 # names exported by include/eor21.h
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_trace",
+           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_last_error", "eor_version",
            "eor_destroy")
 KERNEL_CLASSES = 7
@@ -80,6 +80,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_density_spectrum": (I, [P, I, P, I]),
         "eor_walker_ladder": (I, [P, I, P, ctypes.POINTER(I)]),
         "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
+        "eor_set_tuning": (I, [P, I, I, I]),
         "eor_trace": (I, [P, I]),
         "eor_trace_read": (I, [P, P, P, I]),
         "eor_kernel_class_name": (ctypes.c_char_p, [I]),
@@ -270,6 +271,9 @@ class Context:
                                                     _arg(cnt, np.int64)[0], mem))
         return d2, km, cnt
 
+    def eor_set_tuning(self, group: int, pairs: int, plane_threads: int = 512):
+        self._check(self.lib.eor_set_tuning(self.handle, int(group), int(pairs), int(plane_threads)))
+
     def eor_trace(self, enable: bool = True):
         self._check(self.lib.eor_trace(self.handle, 1 if enable else 0))
 
@@ -297,6 +301,7 @@ class Context:
     walker_ladder = eor_walker_ladder
     box_power_spectrum = eor_box_power_spectrum
     trace = eor_trace
+    set_tuning = eor_set_tuning
     trace_read = eor_trace_read
     launch_count = eor_launch_count
 

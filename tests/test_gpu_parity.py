@@ -271,3 +271,25 @@ def test_full_size_batched_walkers_sampled():
             assert compare_ps(d2[w, 0], rd2, rcnt) <= PS_TOL, w
         else:
             assert np.max(np.abs(d2[w, 0] - rd2)) <= 1e-3 * max(np.max(np.abs(rd2)), 1e-6), w
+
+
+def test_tracing_counts_and_times_every_launch():
+    n, box, zs = 32, 64.0, (8.0, 9.0)
+    params = synth.walker_params(3, seed=4)
+    mock = np.full((2, 14), 5.0)
+    with make_ctx(n, box, zs, max_walkers=3) as ctx:
+        ctx.init_boxes(synth.density_boxes(n, box, zs, seed=5))
+        ref = ctx.likelihood(params, mock, 0.2 * mock)
+        untraced = ctx.launch_count()
+        ctx.trace(True)
+        for _ in range(2):                                   # capture, then a replay
+            got = ctx.likelihood(params, mock, 0.2 * mock)
+            t = ctx.trace_read()
+            assert sum(c for _, c in t.values()) == ctx.launch_count() == untraced
+            assert t["filter_plane"][1] > 0 and t["pencil_ionize"][1] == t["filter_plane"][1]
+            assert all(ms > 0 for ms, c in t.values() if c > 0)
+        np.testing.assert_allclose(got, ref, rtol=1e-12)
+        ctx.set_params(params)                               # traced outside a graph
+        ctx.run_ionization()
+        t = ctx.trace_read()
+        assert t["filter_plane"][1] > 0 and t["filter_plane"][0] > 0
