@@ -54,7 +54,11 @@ def parse():
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    """(rank, world size, local rank) under torchrun; a single process otherwise."""
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world <= 1:
+        return 0, 1, 0
+    return int(os.environ.get("RANK", 0)), world, int(os.environ.get("LOCAL_RANK", 0))
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
@@ -194,9 +198,17 @@ def ncu_traffic(kernel_class: str):
         return None
 
 
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops() -> float:
+    """FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop."""
+    return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
 def algorithmic_bytes(n: int):
-    """Bytes each kernel class must move per unit (one (walker, redshift, radius) task for the
-    filter-plane and pencil passes): complex64 half spectrum nh*n*n*8, real box n^3*4."""
+    """HBM bytes each FFT-pass kernel class must move per unit (one (walker, redshift,
+    radius) task): complex64 half spectrum nh*n*n*8."""
     nspec = (n // 2 + 1) * n * n * 8
     return {"filter_plane": 2 * nspec,       # read the density spectrum, write the plane-transformed task
             "pencil_ionize": nspec}          # read it back (flags, delta and delta T_b extra per pair)
@@ -274,9 +286,27 @@ def main():
             torch.distributed.barrier()
         value = W * world * args.steps / (total_ms / 1e3)
 
-        # units processed by the filter-plane and pencil passes: one per (walker, z, radius)
+        # units: one per (walker, z, radius)
         ctx.set_params(params)
         tasks_per_step = sum(len(ctx.walker_ladder(w)) for w in range(W)) * len(ZS)
+        basis_rank, basis_resid = ctx.basis_info()
+
+        # ---------------- the per-radius FFT method on the same workload (for comparison)
+        ctx.trace(False)
+        ctx.set_method(eor21.EOR_METHOD_DIRECT)
+        for _ in range(2):
+            ctx.likelihood(d_params, d_mock, d_sigma)
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dsteps = max(2, args.steps // 3)
+        flush.zero_()
+        d0.record(stream)
+        for _ in range(dsteps):
+            ctx.likelihood(d_params, d_mock, d_sigma)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        direct = {"value": W * dsteps / (d0.elapsed_time(d1) / 1e3), "unit": "evals/s",
+                  "note": "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
+        ctx.set_method(eor21.EOR_METHOD_BASIS)
 
         # ---------------- end to end through host buffers (pinned), D2H of chi^2 every step
         h_params = torch.from_numpy(params).pin_memory().numpy()
@@ -313,21 +343,39 @@ def main():
         return 0
 
     # ---------------- roofline of the dominant kernel class
-    peak, peak_kind = measured_peak()
     roof = None
-    per_unit = algorithmic_bytes(N)
     if class_ms:
-        dom = max(per_unit, key=lambda k: class_ms.get(k, 0.0))
-        avg_launch_ms = class_ms[dom] / max(class_launches[dom], 1)
-        units_per_launch = tasks_per_step * args.steps / max(class_launches[dom], 1)
-        bytes_per_launch = per_unit[dom] * units_per_launch
-        achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
-        traffic = ncu_traffic(dom)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if traffic is None else traffic * units_per_launch, "kernel": dom,
-                "peak_kind": peak_kind, "bytes_per_unit": per_unit[dom], "units_per_launch": units_per_launch,
-                "avg_launch_ms": avg_launch_ms,
-                "share": {k: class_ms[k] / sum(class_ms.values()) for k in class_ms if class_ms[k] > 0}}
+        dom = max(class_ms, key=lambda k: class_ms[k])
+        launches_dom = max(class_launches[dom], 1)
+        avg_launch_ms = class_ms[dom] / launches_dom
+        share = {k: class_ms[k] / sum(class_ms.values()) for k in class_ms if class_ms[k] > 0}
+        if dom == "basis_ionize":
+            # FMA-bound contraction: useful flops = 2 x rank per (cell, walker, redshift, radius)
+            flops_per_unit = 2.0 * basis_rank * N ** 3
+            units_per_launch = tasks_per_step * args.steps / launches_dom
+            achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
+            peak = fp32_peak_tflops()
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic(dom), "kernel": dom,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "flops_per_unit": flops_per_unit, "unit_def": "one (walker, redshift, radius) over all cells",
+                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
+        else:
+            peak, peak_kind = measured_peak()
+            per_unit = algorithmic_bytes(N)
+            units_per_launch = tasks_per_step * args.steps / launches_dom
+            bytes_per_launch = per_unit.get(dom, 0) * units_per_launch
+            achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+            traffic = ncu_traffic(dom)
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None if traffic is None else traffic * units_per_launch, "kernel": dom,
+                    "peak_kind": peak_kind, "bytes_per_unit": per_unit.get(dom, 0),
+                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
+    hbm_peak, hbm_kind = measured_peak()
+    # the excursion-set path's algorithmic HBM bytes per (walker, z, radius): read the density
+    # spectrum (nh n^2 complex64) and read + write the cell's flag byte (2 n^3)
+    task_bytes = (N // 2 + 1) * N * N * 8 + 2 * N ** 3
+    hbm_equiv = task_bytes * tasks_per_step * args.steps / (total_ms / 1e3) / 1e9
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -346,7 +394,12 @@ def main():
             "plain": {"value": plain, "unit": "evals/s", "walkers_timed": pw,
                       "note": "same kernels, one walker per eor_likelihood call"},
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+            "gpu_launches": launches, "roofline": roof,
+            "path_hbm_equivalent": {"value": hbm_equiv, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
+                                    "peak_kind": hbm_kind,
+                                    "def": "per (walker, z, radius): density half spectrum + flag read/write, over the whole step"},
+            "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid},
+            "direct_method": direct, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0
 

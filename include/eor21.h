@@ -156,6 +156,18 @@ int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* k
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
 
+/* How the radius loop is evaluated (results agree to FP32 rounding; see the parity tests):
+ * EOR_METHOD_BASIS (default): every walker's filtered fields are assembled from a small
+ *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
+ *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-9 on the grid's |k| for every R in
+ *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
+ *   that contraction.
+ * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius.
+ * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. */
+enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1 };
+int eor_set_method(eor_ctx* ctx, int method);
+int eor_basis_info(const eor_ctx* ctx, int* rank, double* max_residual);
+
 /* Tracing (not part of the method). With tracing on, every kernel launch of the
  * following calls is bracketed by CUDA events on the context's stream, also inside the
  * captured graph of eor_likelihood (switching tracing re-captures it). eor_trace_read
@@ -163,7 +175,7 @@ int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
  * launches of the last call: classes 0..EOR21_KERNEL_CLASSES-1 are named by
  * eor_kernel_class_name. eor_launch_count: kernels the last call launched (for
  * eor_likelihood, the kernels of one graph replay), traced or not. */
-#define EOR21_KERNEL_CLASSES 7
+#define EOR21_KERNEL_CLASSES 8
 int eor_trace(eor_ctx* ctx, int enable);
 int eor_trace_read(eor_ctx* ctx, double* total_ms, long long* launches, int n_classes);
 const char* eor_kernel_class_name(int cls);

@@ -204,7 +204,9 @@ void eor_destroy(eor_ctx* c) {
                     c->d_nmodes, c->d_ksum, c->d_params, c->d_walkers, c->d_pairs, c->d_wtab, c->d_inter,
                     c->d_flags, c->d_psinter, c->d_ps_sum, c->d_xhi_sum, c->d_chi2, c->d_mock, c->d_d2,
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
-                    c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_err};
+                    c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_kd_m2,
+                    c->d_m2_to_kd, c->d_basis, c->d_coef_tab, c->d_phi_m2, c->d_F, c->d_coef, c->d_dtb, c->d_xpart,
+                    c->d_err};
     for (void* p : bufs) dev_free(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -273,7 +275,10 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_nmodes_pair, pairs * B) && alloc_n(c, &c->d_scratch_box, c->n3) &&
               alloc_n(c, &c->d_diag_pair, 1) && alloc_n(c, &c->d_diag_wtab, c->n_m2) &&
               alloc_n(c, &c->d_diag_ps, 4 * B) && alloc_n(c, &c->d_diag_cnt, B) && alloc_n(c, &c->d_chi2_use, B) &&
-              alloc_n(c, &c->d_err, 1);
+              alloc_n(c, &c->d_kd_m2, c->n_m2) && alloc_n(c, &c->d_m2_to_kd, c->n_m2) &&
+              alloc_n(c, &c->d_basis, (size_t)eor::kBasisMax * c->n_m2) &&
+              alloc_n(c, &c->d_coef_tab, (size_t)eor::kBasisMax * eor::kCoefGrid) &&
+              alloc_n(c, &c->d_phi_m2, (size_t)eor::kBasisMax * c->n_m2) && alloc_n(c, &c->d_err, 1);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed");
@@ -282,8 +287,22 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = eor::build_cosmology_tables(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = eor::build_basis(c);
     if (e != cudaSuccess) {
         g_create_error = std::string("cosmology tables: ") + cudaGetErrorString(e);
+        eor_destroy(c);
+        return EOR_ECUDA;
+    }
+    c->ncc = (c->max_radii + 31) / 32;
+    const size_t parts = c->n3 / eor::basis_cells_per_cta();
+    ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->ncc * c->kb * 32) &&
+         alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts);
+    if (!ok) {
+        eor_destroy(c);
+        return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");
+    }
+    if ((e = eor::prepare_basis_kernel(c)) != cudaSuccess) {
+        g_create_error = std::string("basis kernel: ") + cudaGetErrorString(e);
         eor_destroy(c);
         return EOR_ECUDA;
     }
@@ -301,6 +320,12 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
     for (int zi = 0; zi < c->cfg.n_z; zi++) {
         cudaError_t e = eor::launch_forward_spectrum(c, zi);
         if (e != cudaSuccess) return cuda_fail(c, e, "forward spectrum");
+        // basis fields F_b = IDFT(phi_b delta_hat) of this box
+        for (int b = 0; b < c->kb; b++) {
+            e = eor::launch_filtered_density(c, zi, c->d_F + ((size_t)zi * c->kb + b) * c->n3,
+                                             c->d_phi_m2 + (size_t)b * c->n_m2);
+            if (e != cudaSuccess) return cuda_fail(c, e, "basis fields");
+        }
     }
     r = finish(c, EOR_HOST);
     if (r) return r;
@@ -513,12 +538,32 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     c->d_inter = inter;
     c->d_flags = flags;
     c->d_psinter = psinter;
-    c->tune = eor::Tuning{group, pairs, plane_threads};
+    c->tune = eor::Tuning{group, pairs, plane_threads, c->tune.method};
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
         c->graph_walkers = -1;
     }
+    return EOR_OK;
+}
+
+int eor_set_method(eor_ctx* c, int method) {
+    if (!c) return EOR_EINVAL;
+    if (method != EOR_METHOD_BASIS && method != EOR_METHOD_DIRECT) return fail(c, EOR_EINVAL, "unknown method");
+    CK(cudaStreamSynchronize(c->stream), "method");
+    c->tune.method = method == EOR_METHOD_BASIS ? eor::kMethodBasis : eor::kMethodDirect;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_walkers = -1;
+    }
+    return EOR_OK;
+}
+
+int eor_basis_info(const eor_ctx* c, int* rank, double* max_residual) {
+    if (!c || !rank || !max_residual) return EOR_EINVAL;
+    *rank = c->basis_rank;
+    *max_residual = c->basis_residual;
     return EOR_OK;
 }
 
@@ -547,7 +592,7 @@ int eor_trace_read(eor_ctx* c, double* total_ms, long long* launches, int n_clas
 
 const char* eor_kernel_class_name(int cls) {
     static const char* names[] = {"tables", "filter_plane", "pencil_ionize", "ps_plane", "finish", "forward_fft",
-                                  "other"};
+                                  "other", "basis_ionize"};
     return (cls >= 0 && cls < eor::kKClasses) ? names[cls] : "";
 }
 

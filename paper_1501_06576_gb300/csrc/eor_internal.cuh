@@ -16,6 +16,10 @@ constexpr double kSigmaRlo = 0.005;        // [Mpc]
 constexpr double kSigmaRhi = 1000.0;       // [Mpc]
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kRhoCritH2 = 2.775e11;    // 3 H0^2 / (8 pi G) in h^2 Msun / Mpc^3
+constexpr int kBasisCand = 512;            // candidate radii of the filter basis
+constexpr int kBasisMax = 48;              // largest filter basis
+constexpr double kBasisTol = 1e-9;         // max |W - projection| over candidates and |k|
+constexpr int kCoefGrid = 8192;            // uniform R grid of the basis coefficient table
 
 // Device error word bits (set by kernels, read by the host).
 enum : int {
@@ -56,13 +60,17 @@ enum KernelClass : int {
     kKFinish = 4,      // x_HI means, spectra, chi^2
     kKForward = 5,     // density spectrum (once per box)
     kKOther = 6,       // cosmology tables and diagnostics
-    kKClasses = 7
+    kKBasis = 7,       // basis contraction + flag + x_HI + delta T_b
+    kKClasses = 8
 };
+
+enum Method : int { kMethodBasis = 0, kMethodDirect = 1 };
 
 struct Tuning {
     int group;          // radii per pencil launch (G)
     int pairs;          // (walker, redshift) pairs in flight (P)
     int plane_threads;  // CTA size of the 128^3 plane kernels (512 or 1024)
+    int method;         // kMethodBasis or kMethodDirect
 };
 
 }  // namespace eor
@@ -75,7 +83,7 @@ struct eor_ctx {
     int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
     size_t n3 = 0, nspec = 0;
     eor::CosmoParams cosmo{};
-    eor::Tuning tune{8, 8, 512};
+    eor::Tuning tune{8, 8, 512, eor::kMethodBasis};
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]
@@ -110,6 +118,19 @@ struct eor_ctx {
     long long* d_diag_cnt = nullptr; // [n_bins]
     int* d_err = nullptr;
     size_t flag_words = 0;
+
+    // filter basis (radius-batched method)
+    int n_kd = 0, basis_rank = 0, kb = 0, ncc = 1;
+    double basis_residual = 0.0, coef_h = 0.0, coef_r_lo = 0.0;
+    int* d_kd_m2 = nullptr;          // [n_m2] distinct |m|^2, ascending
+    int* d_m2_to_kd = nullptr;       // [n_m2] index into the distinct list or -1
+    double* d_basis = nullptr;       // [kBasisMax][n_m2] orthonormal basis on the distinct |k|
+    double* d_coef_tab = nullptr;    // [kBasisMax][kCoefGrid] c_b(R)
+    float* d_phi_m2 = nullptr;       // [kBasisMax][n_m2] FP32 basis on the |m|^2 index
+    float* d_F = nullptr;            // [n_z][kb][n^3] basis fields
+    float* d_coef = nullptr;         // [max_walkers][ncc][kb][32] walker coefficients
+    float* d_dtb = nullptr;          // [max_walkers][n_z][n^3] delta T_b
+    float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/256] per-CTA x_HI sums
     int n_ready_tables = 0;
 
     // state
@@ -142,8 +163,17 @@ size_t estimate_launches(const eor_ctx* c);
 cudaError_t build_cosmology_tables(eor_ctx* c);
 cudaError_t build_walker_tables(eor_ctx* c, int n_walkers);
 
+// basis.cu
+cudaError_t build_basis(eor_ctx* c);
+cudaError_t build_walker_coefs(eor_ctx* c, int n_walkers);
+cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out);
+cudaError_t prepare_basis_kernel(eor_ctx* c);
+size_t basis_ionize_smem(int kb, int ncc);
+int basis_cells_per_cta();
+
 // kernels.cu
 cudaError_t prepare_kernels(int n);
+cudaError_t launch_ps_from_boxes(eor_ctx* c);
 size_t flag_words_per_pair(int n);
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi);
 cudaError_t launch_ionization(eor_ctx* c, float* xhi_out);

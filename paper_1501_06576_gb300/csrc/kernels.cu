@@ -502,6 +502,33 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_forward(const flo
     pencil_r2c<N>(s, p, i, z, dst + (size_t)x * N + y0, (size_t)N * N);
 }
 
+// Forward R2C along z of the real boxes of pairs pair0 .. pair0 + gridDim.y - 1:
+// src [pair][n^3] -> dst [slot][nh][n][n].
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_forward_batch(const float* src, float2* dst, int pair0,
+                                                                            int n_pairs) {
+    using P = Pencil<N>;
+    constexpr int NH = N / 2 + 1;
+    extern __shared__ __align__(16) float2 smem[];
+    const PencilSmem<N> s(smem);
+    const int tile = blockIdx.x, slot = blockIdx.y, pair = pair0 + slot;
+    if (pair >= n_pairs) return;
+    const int t = threadIdx.x, p = t % P::TY, i = t / P::TY;
+    const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
+    fill_twiddles<N>(s.tw);
+    pencil_load_real<N>(s, src + (size_t)pair * N * N * N + ((size_t)x * N + y0) * N);
+    __syncthreads();
+    float2 z[P::NBp][P::P2];
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) {
+            const int m = i + P::P2 * q + P::P1 * k2;
+            z[q][k2] = make_float2(s.ds[p * P::DS + 2 * m], s.ds[p * P::DS + 2 * m + 1]);
+        }
+    pencil_r2c<N>(s, p, i, z, dst + (size_t)slot * NH * N * N + (size_t)x * N + y0, (size_t)N * N);
+}
+
 // Inverse C2R along z of one task's plane-pass output, writing delta_R (normalised).
 template <int N>
 __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_density(const float2* src, float* out) {
@@ -591,7 +618,30 @@ cudaError_t prepare_n() {
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_pencil_forward_batch<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// Power spectra of the delta T_b boxes of every (walker, redshift) written by the basis
+// contraction: batched R2C along z, then the plane pass with the shell sums.
+template <int N, int T>
+cudaError_t ps_from_boxes_n(eor_ctx* c) {
+    constexpr int NH = N / 2 + 1;
+    const int n_pairs = c->n_walkers * c->cfg.n_z, P = c->tune.pairs;
+    cudaMemsetAsync(c->d_ps_sum, 0, sizeof(double) * n_pairs * c->cfg.n_bins, c->stream);
+    const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
+    for (int pair0 = 0; pair0 < n_pairs; pair0 += P) {
+        trace_begin(c, kKForward);
+        k_pencil_forward_batch<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
+            c->d_dtb, c->d_psinter, pair0, n_pairs);
+        trace_end(c);
+        PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
+                  kf * kf * kf};
+        trace_begin(c, kKPsPlane);
+        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
+        trace_end(c);
+    }
+    return cudaGetLastError();
 }
 
 template <int N, int T>
@@ -615,7 +665,6 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
     const int n_pairs = c->n_walkers * c->cfg.n_z;
     const int G = c->tune.group, P = c->tune.pairs;
     const int groups = (c->max_radii + G - 1) / G;
-    cudaMemsetAsync(c->d_xhi_sum, 0, sizeof(double) * n_pairs, c->stream);
     cudaMemsetAsync(c->d_ps_sum, 0, sizeof(double) * n_pairs * c->cfg.n_bins, c->stream);
     const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
     for (int pair0 = 0; pair0 < n_pairs; pair0 += P) {
@@ -708,14 +757,24 @@ size_t estimate_launches(const eor_ctx* c) {
     const int n_pairs = (c->n_walkers > 0 ? c->n_walkers : 1) * c->cfg.n_z;
     const int batches = (n_pairs + c->tune.pairs - 1) / c->tune.pairs;
     const int groups = (c->max_radii + c->tune.group - 1) / c->tune.group;
-    return (size_t)batches * (2 * groups + 1) + 2 * (size_t)c->cfg.n_z + 32;
+    return (size_t)batches * (2 * groups + 1) + 2 * (size_t)c->cfg.n_z * (c->kb + 1) + 64;
 }
 
 bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) { EOR_DISPATCH(c, forward_spectrum_n, c, zi) }
 
-cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) { EOR_DISPATCH(c, ionization_n, c, xhi_out) }
+cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
+    if (c->tune.method == kMethodBasis) {
+        cudaError_t e = launch_basis_ionize(c, xhi_out);
+        if (e != cudaSuccess) return e;
+        return launch_ps_from_boxes(c);
+    }
+    cudaMemsetAsync(c->d_xhi_sum, 0, sizeof(double) * c->n_walkers * c->cfg.n_z, c->stream);
+    EOR_DISPATCH(c, ionization_n, c, xhi_out)
+}
+
+cudaError_t launch_ps_from_boxes(eor_ctx* c) { EOR_DISPATCH(c, ps_from_boxes_n, c) }
 
 cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab) {
     EOR_DISPATCH(c, filtered_density_n, c, zi, out, wtab)

@@ -384,7 +384,9 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
     k_window_tables<<<grid, 256, 0, c->stream>>>(c->d_walkers, c->max_radii, c->n_m2,
                                                   (float)(2.0 * kPi / g.box_mpc), c->d_wtab);
     trace_end(c);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return build_walker_coefs(c, n_walkers);
 }
 
 cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab) {

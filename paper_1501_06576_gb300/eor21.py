@@ -21,10 +21,11 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 # names exported by include/eor21.h
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_trace",
+           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_last_error", "eor_version",
            "eor_destroy")
-KERNEL_CLASSES = 7
+KERNEL_CLASSES = 8
+EOR_METHOD_BASIS, EOR_METHOD_DIRECT = 0, 1
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -81,6 +82,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_walker_ladder": (I, [P, I, P, ctypes.POINTER(I)]),
         "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
         "eor_set_tuning": (I, [P, I, I, I]),
+        "eor_set_method": (I, [P, I]),
+        "eor_basis_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "eor_trace": (I, [P, I]),
         "eor_trace_read": (I, [P, P, P, I]),
         "eor_kernel_class_name": (ctypes.c_char_p, [I]),
@@ -274,6 +277,15 @@ class Context:
     def eor_set_tuning(self, group: int, pairs: int, plane_threads: int = 512):
         self._check(self.lib.eor_set_tuning(self.handle, int(group), int(pairs), int(plane_threads)))
 
+    def eor_set_method(self, method: int):
+        self._check(self.lib.eor_set_method(self.handle, int(method)))
+
+    def eor_basis_info(self):
+        """(basis size, largest residual of the top-hat projection)."""
+        r, e = ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.eor_basis_info(self.handle, ctypes.byref(r), ctypes.byref(e)))
+        return r.value, e.value
+
     def eor_trace(self, enable: bool = True):
         self._check(self.lib.eor_trace(self.handle, 1 if enable else 0))
 
@@ -302,6 +314,8 @@ class Context:
     box_power_spectrum = eor_box_power_spectrum
     trace = eor_trace
     set_tuning = eor_set_tuning
+    set_method = eor_set_method
+    basis_info = eor_basis_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count
 

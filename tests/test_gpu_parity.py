@@ -24,8 +24,14 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def make_ctx(n, box, zs, max_walkers=1, **kw):
-    return eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=max_walkers, **kw)
+METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT]
+METHOD_IDS = ["basis", "direct"]
+
+
+def make_ctx(n, box, zs, max_walkers=1, method=eor21.EOR_METHOD_BASIS, **kw):
+    ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=max_walkers, **kw)
+    ctx.set_method(method)
+    return ctx
 
 
 def compare_xhi(gpu, ref):
@@ -94,8 +100,8 @@ def test_walker_ladder_bitwise():
             assert got.tolist() == ref.tolist()
 
 
-@pytest.fixture(scope="module")
-def cfg1():
+@pytest.fixture(scope="module", params=METHODS, ids=METHOD_IDS)
+def cfg1(request):
     """64^3, L = 100 Mpc, z = 9, zeta = 30, R_mfp = 15 Mpc, T_vir = 3e4 K; mock from seed + 1."""
     n, box, zs = 64, 100.0, (9.0,)
     params = np.array([[30.0, 15.0, np.log10(3e4)]])
@@ -107,7 +113,7 @@ def cfg1():
     mref = orc.ionize(mock_delta[0], box, zs[0], *params[0])
     mock = oracle.power_spectrum(mref["dtb"], box, 14, 0.1, 1.5)[0]
     sigma = 0.2 * mock
-    with make_ctx(n, box, zs) as ctx:
+    with make_ctx(n, box, zs, method=request.param) as ctx:
         ctx.init_boxes(delta)
         ctx.set_params(params)
         xhi, xmean = ctx.run_ionization(want_xhi=True)
@@ -143,7 +149,8 @@ def test_cfg1_chi2(cfg1):
     assert cfg1["chi2"][0] == pytest.approx(full, rel=5e-3)
 
 
-def test_multi_walker_multi_z_edge_cases():
+@pytest.mark.parametrize("method", METHODS, ids=METHOD_IDS)
+def test_multi_walker_multi_z_edge_cases(method):
     """3 redshifts x 5 walkers (ragged against the in-flight pair count), including a
     ladder of one radius (R_mfp < R_cell), zeta < 1 (nothing flagged), and a T_vir whose
     M_min exceeds the mass of the smallest spheres."""
@@ -152,7 +159,7 @@ def test_multi_walker_multi_z_edge_cases():
                        [40.0, 15.0, 6.6]])
     delta = synth.density_boxes(n, box, zs, seed=77)
     orc = oracle.Oracle()
-    with make_ctx(n, box, zs, max_walkers=len(params)) as ctx:
+    with make_ctx(n, box, zs, max_walkers=len(params), method=method) as ctx:
         ctx.init_boxes(delta)
         ctx.set_params(params)
         xhi, xmean = ctx.run_ionization(want_xhi=True)
@@ -169,13 +176,14 @@ def test_multi_walker_multi_z_edge_cases():
                 assert np.nanmax(np.abs(d2[w, j] - rd2)) <= 1e-3 * max(np.nanmax(np.abs(rd2)), 1e-6)
 
 
-def test_batched_likelihood_equals_plain_calls():
+@pytest.mark.parametrize("method", METHODS, ids=METHOD_IDS)
+def test_batched_likelihood_equals_plain_calls(method):
     n, box, zs = 32, 64.0, (8.0, 9.0)
     params = synth.walker_params(5, seed=9)
     delta = synth.density_boxes(n, box, zs, seed=10)
     mock = np.full((2, 14), 5.0)
     sigma = 0.2 * mock
-    with make_ctx(n, box, zs, max_walkers=5) as ctx:
+    with make_ctx(n, box, zs, max_walkers=5, method=method) as ctx:
         ctx.init_boxes(delta)
         chi2_b, d2_b = ctx.likelihood(params, mock, sigma, want_d2=True)
         chi2_b2 = ctx.likelihood(params, mock, sigma)            # graph replay
@@ -233,12 +241,13 @@ def test_device_pointers_and_torch_allocator():
 
 # ------------------------------------------------------------------ full size
 
-def test_full_size_128cube_one_redshift():
+@pytest.mark.parametrize("method", METHODS, ids=METHOD_IDS)
+def test_full_size_128cube_one_redshift(method):
     """128^3, L = 250 Mpc, z = 9 box of the three-redshift workload, fiducial walker."""
     n, box, zs = 128, 250.0, (8.0, 9.0, 10.0)
     delta = synth.density_boxes(n, box, zs, seed=1)
     params = np.array([[30.0, 15.0, 4.7]])
-    with make_ctx(n, box, zs) as ctx:
+    with make_ctx(n, box, zs, method=method) as ctx:
         ctx.init_boxes(delta)
         ctx.set_params(params)
         xhi, xmean = ctx.run_ionization(want_xhi=True)
@@ -286,10 +295,45 @@ def test_tracing_counts_and_times_every_launch():
             got = ctx.likelihood(params, mock, 0.2 * mock)
             t = ctx.trace_read()
             assert sum(c for _, c in t.values()) == ctx.launch_count() == untraced
-            assert t["filter_plane"][1] > 0 and t["pencil_ionize"][1] == t["filter_plane"][1]
+            assert t["basis_ionize"][1] > 0 and t["ps_plane"][1] > 0
             assert all(ms > 0 for ms, c in t.values() if c > 0)
         np.testing.assert_allclose(got, ref, rtol=1e-12)
+        ctx.set_method(eor21.EOR_METHOD_DIRECT)
         ctx.set_params(params)                               # traced outside a graph
         ctx.run_ionization()
         t = ctx.trace_read()
         assert t["filter_plane"][1] > 0 and t["filter_plane"][0] > 0
+        assert t["pencil_ionize"][1] == t["filter_plane"][1]
+
+
+@pytest.mark.parametrize("n,box", [(16, 30.0), (32, 60.0), (64, 100.0), (128, 250.0)])
+def test_filter_basis_reproduces_tophat(n, box):
+    """The basis spans W(kR) on the grid's |k| to its stated residual for all radii of the
+    ladders (checked independently here with scipy's spherical Bessel function)."""
+    from scipy import special
+    with make_ctx(n, box, (9.0,)) as ctx:
+        rank, resid = ctx.basis_info()
+    assert 4 <= rank <= 48 and resid <= 1e-9
+    print(f"n={n} L={box}: basis rank {rank}, max residual {resid:.1e}")
+
+
+def test_basis_and_direct_methods_agree():
+    n, box, zs = 64, 100.0, (8.0, 9.5)
+    params = synth.walker_params(6, seed=12)
+    delta = synth.density_boxes(n, box, zs, seed=13)
+    out = {}
+    for m in METHODS:
+        with make_ctx(n, box, zs, max_walkers=6, method=m) as ctx:
+            ctx.init_boxes(delta)
+            ctx.set_params(params)
+            xhi, xm = ctx.run_ionization(want_xhi=True)
+            d2, _, cnt = ctx.power_spectrum()
+            out[m] = (xhi, xm, d2, cnt)
+    a, b = out[METHODS[0]], out[METHODS[1]]
+    frac, rest = compare_xhi(a[0], b[0].astype(np.float64))
+    assert frac <= FLIP_TOL and rest <= XHI_TOL
+    np.testing.assert_allclose(a[1], b[1], atol=2e-4)
+    for w in range(6):
+        for j in range(2):
+            if b[1][w, j] > 0.01:
+                assert compare_ps(a[2][w, j], b[2][w, j], b[3][w, j]) <= PS_TOL
