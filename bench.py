@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-trace", action="store_true", help="time without the per-kernel event brackets")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
     return ap.parse_args()
 
 
@@ -214,6 +215,24 @@ def algorithmic_bytes(n: int):
             "pencil_ionize": nspec}          # read it back (flags, delta and delta T_b extra per pair)
 
 
+def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, steps):
+    """Batched evals/s of the per-radius FFT method on the same walkers (comparison only)."""
+    ctx.set_method(eor21.EOR_METHOD_DIRECT)
+    for _ in range(2):
+        ctx.likelihood(d_params, d_mock, d_sigma)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dsteps = max(2, steps // 3)
+    flush.zero_()
+    d0.record(stream)
+    for _ in range(dsteps):
+        ctx.likelihood(d_params, d_mock, d_sigma)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_method(eor21.EOR_METHOD_BASIS)
+    return {"value": W * dsteps / (d0.elapsed_time(d1) / 1e3), "unit": "evals/s",
+            "note": "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -293,20 +312,9 @@ def main():
 
         # ---------------- the per-radius FFT method on the same workload (for comparison)
         ctx.trace(False)
-        ctx.set_method(eor21.EOR_METHOD_DIRECT)
-        for _ in range(2):
-            ctx.likelihood(d_params, d_mock, d_sigma)
-        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        dsteps = max(2, args.steps // 3)
-        flush.zero_()
-        d0.record(stream)
-        for _ in range(dsteps):
-            ctx.likelihood(d_params, d_mock, d_sigma)
-        d1.record(stream)
-        torch.cuda.synchronize()
-        direct = {"value": W * dsteps / (d0.elapsed_time(d1) / 1e3), "unit": "evals/s",
-                  "note": "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
-        ctx.set_method(eor21.EOR_METHOD_BASIS)
+        direct = None
+        for _ in range(0 if args.no_direct else 1):
+            direct = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps)
 
         # ---------------- end to end through host buffers (pinned), D2H of chi^2 every step
         h_params = torch.from_numpy(params).pin_memory().numpy()

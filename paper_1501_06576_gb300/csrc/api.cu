@@ -295,7 +295,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     }
     c->ncc = (c->max_radii + 31) / 32;
     const size_t parts = c->n3 / eor::basis_cells_per_cta();
-    ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->ncc * c->kb * 32) &&
+    ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->max_radii * c->kb) &&
          alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts);
     if (!ok) {
         eor_destroy(c);

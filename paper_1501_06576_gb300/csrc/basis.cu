@@ -180,11 +180,11 @@ __global__ void k_basis_m2(const double* basis, int n_kd, const int* m2_to_kd, i
 }
 
 // Walker radius j -> coefficients c_b(R_j), 4-point Lagrange in the FP64 table, stored FP32
-// as [walker][chunk of 32 radii][b][32]; zero beyond the ladder and beyond the rank.
-__global__ void k_walker_coefs(const WalkerInfo* walkers, const double* tab, int rank, int kb, int ncc, double r_lo,
-                               double h, int n_grid, float* coef, int* err) {
+// as [walker][radius][b]; zero beyond the ladder and beyond the rank.
+__global__ void k_walker_coefs(const WalkerInfo* walkers, const double* tab, int rank, int kb, int max_radii,
+                               double r_lo, double h, int n_grid, float* coef, int* err) {
     const int w = blockIdx.y;
-    const int j = blockIdx.x;             // radius slot 0 .. ncc*32-1
+    const int j = blockIdx.x;             // radius slot 0 .. max_radii-1
     const int b = threadIdx.x;            // basis index
     if (b >= kb) return;
     const int n_r = walkers[w].n_r;
@@ -204,132 +204,143 @@ __global__ void k_walker_coefs(const WalkerInfo* walkers, const double* tab, int
         const double l3 = (t + 1.0) * t * (t - 1.0) / 6.0;
         out = (float)(l0 * f[0] + l1 * f[1] + l2 * f[2] + l3 * f[3]);
     }
-    const int cc = j / 32, jj = j % 32;
-    coef[(((size_t)w * ncc + cc) * kb + b) * 32 + jj] = out;
+    coef[((size_t)w * max_radii + j) * kb + b] = out;
 }
 
 // ------------------------------------------------------------------ the contraction
 
-constexpr int kTC = 256;        // cells per CTA
-constexpr int kWCH = 8;         // walkers per coefficient chunk
-constexpr int kBThreads = 256;  // 8 warps
+constexpr int kCPL = 2;                 // cells per thread
+constexpr int kBThreads = 256;          // 8 warps
+constexpr int kTC = kCPL * kBThreads;   // cells per CTA
+constexpr int kWCH = 16;                // walkers per coefficient chunk
 
 struct BasisArgs {
     const float* F;             // [n_z][kb][n3] basis fields
-    const float* coef;          // [walker][ncc][kb][32]
+    const float* coef;          // [walker][max_radii][kb] coefficients c_b(R_j)
     const PairInfo* pairs;      // [walker * n_z + zi]
     const float* delta;         // [n_z][n3]
     float* dtb;                 // [pair][n3]
     float* xhi_out;             // optional [pair][n3]
     float* xpart;               // [pair][n3 / kTC] per-CTA neutral-fraction sums
-    int n_walkers, n_z, kb, ncc;
+    int n_walkers, n_z, max_radii;
     long long n3;
     float delta_c;
 };
 
-// One CTA: kTC cells of one redshift against every walker. A warp task is 16 cells x one
-// walker's 32 radius slots; lane (cg, jg) holds 4 cells x 4 radii and runs the kb-term
-// contraction from shared memory, then the epilogue: delta_R >= delta_crit per radius,
-// OR over the lane's radii and across the 8 lanes of its cells, and (in the lane that
-// holds R_cell) x_HI = 1 - (flag ? 1 : min(1, zeta f_coll(R_cell))), delta T_b.
+// Per-walker constants of a chunk, staged in shared memory.
+struct WalkerConst {
+    float zeta, t0, inv, cell_ok;
+};
+
+// One CTA: kTC cells of one redshift against every walker. Each thread keeps the KB basis
+// values of its kCPL cells in registers; the block walks the flattened list of (walker,
+// radius) columns of a chunk of walkers, each column a shared-memory record
+// [c_0 .. c_{KB-1}, delta_crit, last, slot, -] read by every lane at the same address.
+// Per column: delta_R = sum_b c_b F_b, flag |= delta_R >= delta_crit (Eq. 1). At a walker's
+// last column (R_cell, warp-uniform): x_HI = 1 - (flag ? 1 : min(1, zeta f_coll(R_cell))),
+// delta T_b = T0 x_HI (1 + delta) stored for the thread's cells (coalesced), flag reset.
+template <int KB>
 __global__ void __launch_bounds__(kBThreads) k_basis_ionize(BasisArgs a) {
+    constexpr int REC = KB + 4;                          // floats per column record
     extern __shared__ __align__(16) float sm[];
-    const int kb = a.kb, ncc = a.ncc;
-    float* Fs = sm;                                   // [kb][kTC]
-    float* Cs = Fs + (size_t)kb * kTC;                // [kWCH][ncc][kb][32]
-    float* Ds = Cs + (size_t)kWCH * ncc * kb * 32;    // [kTC]
-    float* Dc = Ds + kTC;                             // [kWCH][ncc*32] thresholds
-    float* Xs = Dc + kWCH * ncc * 32;                 // [kWCH][kTC/4] neutral-fraction partial sums
+    float* Rc = sm;                                      // [kWCH * max_radii][REC]
+    WalkerConst* Wc = reinterpret_cast<WalkerConst*>(Rc + (size_t)kWCH * a.max_radii * REC);   // [kWCH]
+    float* Xs = reinterpret_cast<float*>(Wc + kWCH);     // [kWCH][8 warps]
+    int* Off = reinterpret_cast<int*>(Xs + kWCH * (kBThreads / 32));   // [kWCH + 1] column offsets
     const int zi = blockIdx.y;
     const long long cell0 = (long long)blockIdx.x * kTC;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int cg = lane >> 3, jg = lane & 7;
+    const long long mycell = cell0 + (long long)kCPL * t;
 
-    for (int e = t; e < kb * kTC / 4; e += kBThreads) {
-        const int b = e / (kTC / 4), c4 = e % (kTC / 4);
-        reinterpret_cast<float4*>(Fs + (size_t)b * kTC)[c4] =
-            __ldg(reinterpret_cast<const float4*>(a.F + ((size_t)zi * kb + b) * a.n3 + cell0) + c4);
+    float f[kCPL][KB];
+#pragma unroll
+    for (int b = 0; b < KB; b++) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(a.F + ((size_t)zi * KB + b) * a.n3 + mycell));
+        f[0][b] = v.x;
+        f[1][b] = v.y;
     }
-    for (int e = t; e < kTC / 4; e += kBThreads)
-        reinterpret_cast<float4*>(Ds)[e] = __ldg(reinterpret_cast<const float4*>(a.delta + (size_t)zi * a.n3 + cell0) + e);
+    const float2 dens = __ldg(reinterpret_cast<const float2*>(a.delta + (size_t)zi * a.n3 + mycell));
 
     for (int w0 = 0; w0 < a.n_walkers; w0 += kWCH) {
         const int nw = min(kWCH, a.n_walkers - w0);
-        __syncthreads();   // the previous chunk is done with Cs, Dc, Xs
-        const float4* csrc = reinterpret_cast<const float4*>(a.coef + (size_t)w0 * ncc * kb * 32);
-        for (int e = t; e < nw * ncc * kb * 8; e += kBThreads) reinterpret_cast<float4*>(Cs)[e] = __ldg(csrc + e);
-        for (int e = t; e < nw * ncc * 32; e += kBThreads) {
-            const int wl = e / (ncc * 32), j = e % (ncc * 32);
-            Dc[e] = a.pairs[(size_t)(w0 + wl) * a.n_z + zi].delta_crit[j];
+        __syncthreads();   // the previous chunk is done with the shared buffers
+        if (t == 0) {
+            int run = 0;
+            for (int wl = 0; wl < nw; wl++) {
+                Off[wl] = run;
+                run += a.pairs[(size_t)(w0 + wl) * a.n_z + zi].n_r;
+            }
+            Off[nw] = run;
+        }
+        if (t < nw) {
+            const PairInfo& pi = a.pairs[(size_t)(w0 + t) * a.n_z + zi];
+            Wc[t] = WalkerConst{pi.zeta, pi.t0, pi.inv_sqrt2s2_cell, pi.cell_ok};
         }
         __syncthreads();
-        for (int task = warp; task < nw * (kTC / 16); task += kBThreads / 32) {
-            const int wl = task / (kTC / 16), cs = task % (kTC / 16);
-            const PairInfo& pi = a.pairs[(size_t)(w0 + wl) * a.n_z + zi];
-            const int n_r = pi.n_r;
-            const int jl = n_r - 1;                         // R_cell's slot
-            const int cb0 = cs * 16 + cg * 4;               // first of this lane's 4 cells
-            uint32_t flag4 = 0;
-            float dcell[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int cc = 0; cc < ncc && cc * 32 < n_r; cc++) {
-                float acc[4][4];
+        const int ncols = Off[nw];
+        // column records: coefficients (KB floats) + threshold, last flag, walker slot
+        for (int e = t; e < nw * a.max_radii; e += kBThreads) {
+            const int wl = e / a.max_radii, j = e % a.max_radii;
+            const int n_r = Off[wl + 1] - Off[wl];
+            if (j >= n_r) continue;
+            float* rec = Rc + (size_t)(Off[wl] + j) * REC;
+            const float4* src = reinterpret_cast<const float4*>(a.coef + ((size_t)(w0 + wl) * a.max_radii + j) * KB);
 #pragma unroll
-                for (int ci = 0; ci < 4; ci++)
+            for (int q = 0; q < KB / 4; q++) reinterpret_cast<float4*>(rec)[q] = __ldg(src + q);
+            rec[KB] = a.pairs[(size_t)(w0 + wl) * a.n_z + zi].delta_crit[j];
+            rec[KB + 1] = (j == n_r - 1) ? 1.0f : 0.0f;
+            rec[KB + 2] = (float)wl;
+            rec[KB + 3] = 0.0f;
+        }
+        __syncthreads();
+        bool fl[kCPL] = {false, false};
+        for (int col = 0; col < ncols; col++) {
+            const float* rec = Rc + (size_t)col * REC;
+            float acc[kCPL], acc2[kCPL];   // two partial sums per cell for instruction-level parallelism
 #pragma unroll
-                    for (int jc = 0; jc < 4; jc++) acc[ci][jc] = 0.0f;
-                const float* cp = Cs + ((size_t)(wl * ncc + cc) * kb) * 32 + jg * 4;
-                const float* fp = Fs + cb0;
-#pragma unroll 4
-                for (int b = 0; b < kb; b++) {
-                    const float4 f = *reinterpret_cast<const float4*>(fp + (size_t)b * kTC);
-                    const float4 c = *reinterpret_cast<const float4*>(cp + (size_t)b * 32);
-                    const float fv[4] = {f.x, f.y, f.z, f.w}, cv[4] = {c.x, c.y, c.z, c.w};
+            for (int ci = 0; ci < kCPL; ci++) acc[ci] = acc2[ci] = 0.0f;
 #pragma unroll
-                    for (int ci = 0; ci < 4; ci++)
+            for (int q = 0; q < KB / 4; q++) {
+                const float4 c = *reinterpret_cast<const float4*>(rec + 4 * q);
 #pragma unroll
-                        for (int jc = 0; jc < 4; jc++) acc[ci][jc] = fmaf(fv[ci], cv[jc], acc[ci][jc]);
-                }
-                const float* dc = Dc + wl * ncc * 32 + cc * 32 + jg * 4;
-#pragma unroll
-                for (int jc = 0; jc < 4; jc++) {
-                    const float thr = dc[jc];
-                    const bool is_cell = (cc * 32 + jg * 4 + jc) == jl;
-#pragma unroll
-                    for (int ci = 0; ci < 4; ci++) {
-                        flag4 |= (uint32_t)(acc[ci][jc] >= thr) << ci;
-                        if (is_cell) dcell[ci] = acc[ci][jc];
-                    }
+                for (int ci = 0; ci < kCPL; ci++) {
+                    acc[ci] = fmaf(f[ci][4 * q + 0], c.x, acc[ci]);
+                    acc2[ci] = fmaf(f[ci][4 * q + 1], c.y, acc2[ci]);
+                    acc[ci] = fmaf(f[ci][4 * q + 2], c.z, acc[ci]);
+                    acc2[ci] = fmaf(f[ci][4 * q + 3], c.w, acc2[ci]);
                 }
             }
-            flag4 |= __shfl_xor_sync(0xffffffffu, flag4, 1);
-            flag4 |= __shfl_xor_sync(0xffffffffu, flag4, 2);
-            flag4 |= __shfl_xor_sync(0xffffffffu, flag4, 4);
-            if (n_r > 0 && jg == (jl % 32) / 4) {
-                const float zeta = pi.zeta, t0 = pi.t0, inv = pi.inv_sqrt2s2_cell, dcv = a.delta_c;
-                const bool cell_ok = pi.cell_ok > 0.5f;
-                float out[4], xh[4], xsum = 0.0f;
 #pragma unroll
-                for (int ci = 0; ci < 4; ci++) {
-                    const float dr = dcell[ci];
-                    float f = 0.0f;
-                    if (cell_ok) f = dr >= dcv ? 1.0f : erfcf((dcv - dr) * inv);
-                    const float xhii = ((flag4 >> ci) & 1u) ? 1.0f : fminf(1.0f, zeta * f);
-                    xh[ci] = 1.0f - xhii;
-                    out[ci] = t0 * xh[ci] * (1.0f + Ds[cb0 + ci]);
+            for (int ci = 0; ci < kCPL; ci++) acc[ci] += acc2[ci];
+            const float4 tail = *reinterpret_cast<const float4*>(rec + KB);   // threshold, last, slot
+#pragma unroll
+            for (int ci = 0; ci < kCPL; ci++) fl[ci] |= acc[ci] >= tail.x;
+            if (tail.y != 0.0f) {   // R_cell of walker `slot`: same column for the whole block
+                const int wl = (int)tail.z;
+                const WalkerConst w = Wc[wl];
+                float xh[kCPL], xsum = 0.0f;
+#pragma unroll
+                for (int ci = 0; ci < kCPL; ci++) {
+                    float fc = 0.0f;
+                    if (w.cell_ok > 0.5f) fc = acc[ci] >= a.delta_c ? 1.0f : erfcf((a.delta_c - acc[ci]) * w.inv);
+                    xh[ci] = fl[ci] ? 0.0f : 1.0f - fminf(1.0f, w.zeta * fc);
                     xsum += xh[ci];
+                    fl[ci] = false;
                 }
                 const size_t pair = (size_t)(w0 + wl) * a.n_z + zi;
-                reinterpret_cast<float4*>(a.dtb + pair * a.n3 + cell0 + cb0)[0] = make_float4(out[0], out[1], out[2], out[3]);
-                if (a.xhi_out)
-                    reinterpret_cast<float4*>(a.xhi_out + pair * a.n3 + cell0 + cb0)[0] = make_float4(xh[0], xh[1], xh[2], xh[3]);
-                Xs[wl * (kTC / 4) + cs * 4 + cg] = xsum;
+                reinterpret_cast<float2*>(a.dtb + pair * a.n3 + mycell)[0] =
+                    make_float2(w.t0 * xh[0] * (1.0f + dens.x), w.t0 * xh[1] * (1.0f + dens.y));
+                if (a.xhi_out) reinterpret_cast<float2*>(a.xhi_out + pair * a.n3 + mycell)[0] = make_float2(xh[0], xh[1]);
+                for (int off = 16; off > 0; off >>= 1) xsum += __shfl_xor_sync(0xffffffffu, xsum, off);
+                if (lane == 0) Xs[wl * (kBThreads / 32) + warp] = xsum;
             }
         }
         __syncthreads();
         if (t < nw) {   // fixed-order sum: the result does not depend on scheduling
             double sum = 0.0;
-            for (int i = 0; i < kTC / 4; i++) sum += Xs[t * (kTC / 4) + i];
-            a.xpart[((size_t)(w0 + t) * a.n_z + zi) * (a.n3 / kTC) + blockIdx.x] = (float)sum;
+            for (int i = 0; i < kBThreads / 32; i++) sum += Xs[t * (kBThreads / 32) + i];
+            const int n_r = Off[t + 1] - Off[t];
+            a.xpart[((size_t)(w0 + t) * a.n_z + zi) * (a.n3 / kTC) + blockIdx.x] = n_r > 0 ? (float)sum : 0.0f;
         }
     }
 }
@@ -345,8 +356,9 @@ __global__ void k_xpart_reduce(const float* xpart, int parts, double* xhi_sum) {
 
 }  // namespace
 
-size_t basis_ionize_smem(int kb, int ncc) {
-    return sizeof(float) * ((size_t)kb * kTC + (size_t)kWCH * ncc * kb * 32 + kTC + kWCH * ncc * 32 + kWCH * kTC / 4);
+size_t basis_ionize_smem(int kb, int max_radii) {
+    return sizeof(float) * ((size_t)kWCH * max_radii * (kb + 4)) + sizeof(WalkerConst) * kWCH +
+           sizeof(float) * kWCH * (kBThreads / 32) + sizeof(int) * (kWCH + 1);
 }
 
 int basis_cells_per_cta() { return kTC; }
@@ -431,27 +443,56 @@ cudaError_t build_basis(eor_ctx* c) {
 
 cudaError_t build_walker_coefs(eor_ctx* c, int n_walkers) {
     trace_begin(c, kKTables);
-    k_walker_coefs<<<dim3(c->ncc * 32, n_walkers), 64, 0, c->stream>>>(c->d_walkers, c->d_coef_tab, c->basis_rank,
-                                                                      c->kb, c->ncc, c->coef_r_lo, c->coef_h,
-                                                                      kCoefGrid, c->d_coef, c->d_err);
+    k_walker_coefs<<<dim3(c->max_radii, n_walkers), 64, 0, c->stream>>>(c->d_walkers, c->d_coef_tab, c->basis_rank,
+                                                                       c->kb, c->max_radii, c->coef_r_lo, c->coef_h,
+                                                                       kCoefGrid, c->d_coef, c->d_err);
     trace_end(c);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_basis_kernel(eor_ctx* c) {
-    return cudaFuncSetAttribute(k_basis_ionize, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)basis_ionize_smem(c->kb, c->ncc));
+#define EOR_KB_DISPATCH(kb, FN, ...)          \
+    switch (kb) {                             \
+        case 4: return FN<4>(__VA_ARGS__);    \
+        case 8: return FN<8>(__VA_ARGS__);    \
+        case 12: return FN<12>(__VA_ARGS__);  \
+        case 16: return FN<16>(__VA_ARGS__);  \
+        case 20: return FN<20>(__VA_ARGS__);  \
+        case 24: return FN<24>(__VA_ARGS__);  \
+        case 28: return FN<28>(__VA_ARGS__);  \
+        case 32: return FN<32>(__VA_ARGS__);  \
+        case 36: return FN<36>(__VA_ARGS__);  \
+        case 40: return FN<40>(__VA_ARGS__);  \
+        case 44: return FN<44>(__VA_ARGS__);  \
+        case 48: return FN<48>(__VA_ARGS__);  \
+        default: return cudaErrorInvalidValue; \
+    }
+
+template <int KB>
+cudaError_t prepare_kb(eor_ctx* c) {
+    return cudaFuncSetAttribute(k_basis_ionize<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)basis_ionize_smem(KB, c->max_radii));
 }
+
+template <int KB>
+cudaError_t launch_kb(eor_ctx* c, const BasisArgs& a, size_t smem) {
+    k_basis_ionize<KB><<<dim3((unsigned)(c->n3 / kTC), c->cfg.n_z), kBThreads, smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_basis_kernel(eor_ctx* c) { EOR_KB_DISPATCH(c->kb, prepare_kb, c) }
+
+cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_DISPATCH(c->kb, launch_kb, c, a, smem) }
 
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
     BasisArgs a{c->d_F, c->d_coef, c->d_pairs, c->d_delta, c->d_dtb, xhi_out, c->d_xpart, c->n_walkers, n_z,
-                c->kb, c->ncc, (long long)c->n3, (float)c->cfg.delta_c};
-    const size_t smem = basis_ionize_smem(c->kb, c->ncc);
+                c->max_radii, (long long)c->n3, (float)c->cfg.delta_c};
+    const size_t smem = basis_ionize_smem(c->kb, c->max_radii);
     const int parts = (int)(c->n3 / kTC);
     trace_begin(c, kKBasis);
-    k_basis_ionize<<<dim3(parts, n_z), kBThreads, smem, c->stream>>>(a);
+    cudaError_t e = launch_kb_any(c, a, smem);
     trace_end(c);
+    if (e != cudaSuccess) return e;
     trace_begin(c, kKFinish);
     k_xpart_reduce<<<c->n_walkers * n_z, 256, 0, c->stream>>>(c->d_xpart, parts, c->d_xhi_sum);
     trace_end(c);

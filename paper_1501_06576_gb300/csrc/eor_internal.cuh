@@ -128,9 +128,9 @@ struct eor_ctx {
     double* d_coef_tab = nullptr;    // [kBasisMax][kCoefGrid] c_b(R)
     float* d_phi_m2 = nullptr;       // [kBasisMax][n_m2] FP32 basis on the |m|^2 index
     float* d_F = nullptr;            // [n_z][kb][n^3] basis fields
-    float* d_coef = nullptr;         // [max_walkers][ncc][kb][32] walker coefficients
+    float* d_coef = nullptr;         // [max_walkers][max_radii][kb] walker coefficients
     float* d_dtb = nullptr;          // [max_walkers][n_z][n^3] delta T_b
-    float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/256] per-CTA x_HI sums
+    float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/cells per CTA] per-CTA x_HI sums
     int n_ready_tables = 0;
 
     // state
@@ -168,7 +168,7 @@ cudaError_t build_basis(eor_ctx* c);
 cudaError_t build_walker_coefs(eor_ctx* c, int n_walkers);
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out);
 cudaError_t prepare_basis_kernel(eor_ctx* c);
-size_t basis_ionize_smem(int kb, int ncc);
+size_t basis_ionize_smem(int kb, int max_radii);
 int basis_cells_per_cta();
 
 // kernels.cu

@@ -37,6 +37,7 @@ struct Plane {
     static constexpr int LPT = UNITS / THREADS;            // lines per thread per pass
     static constexpr int NB = R1 / R2;                     // stage-B DFTs per unit
     static constexpr size_t SMEM = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 64 * sizeof(double);
+    static constexpr size_t SMEM_PS = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 16 * THREADS * sizeof(float);
 };
 
 // 2D FFT of an n x n complex plane. load(r, c) gives the natural-order input; on return
@@ -201,30 +202,36 @@ struct PSArgs {
     float kf3;                 // (2 pi / L)^3
 };
 
+constexpr int kPrivBins = 16;   // bins kept in per-thread shared-memory slots
+
 // Forward 2D FFT of one kz plane of delta T_b's z-transformed box, then the shell sums
-// S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2: the conjugate half).
+// S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2: the conjugate half). Each thread
+// first sums its own modes per bin in FP32 (at most 32 modes each) in private shared-memory
+// slots; the slots of all threads are then added in FP64 in a fixed order, and the plane's
+// FP64 sums go to the global shell sums.
 template <int N, int T>
 __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) {
     using P = Plane<N, T>;
     constexpr int NH = N / 2 + 1;
-    constexpr int WARPS = P::THREADS / 32 > 0 ? P::THREADS / 32 : 1;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = smem + N * P::S;
-    __shared__ double s_bins[WARPS][EOR21_MAX_BINS];
+    float* priv = reinterpret_cast<float*>(tw + N);          // [kPrivBins][THREADS]
+    __shared__ double s_bins[EOR21_MAX_BINS];
     const int kz = blockIdx.x, slot = blockIdx.y;
     const int pair = a.pair0 + slot;
     if (pair >= a.n_pairs) return;
     fill_twiddles<N>(tw);
-    for (int e = threadIdx.x; e < WARPS * EOR21_MAX_BINS; e += P::THREADS) (&s_bins[0][0])[e] = 0.0;
+    for (int e = threadIdx.x; e < kPrivBins * P::THREADS; e += P::THREADS) priv[e] = 0.0f;
+    for (int e = threadIdx.x; e < EOR21_MAX_BINS; e += P::THREADS) s_bins[e] = 0.0;
     __syncthreads();
     const float2* s = a.ps_inter + ((size_t)slot * NH + kz) * N * N;
     auto load = [&](int r, int c) { return __ldg(s + r * N + c); };
     float2 hold[P::LPT][P::NB][P::R2];
     plane_fft<N, T, -1>(buf, tw, load, hold);
     const float weight = (kz == 0 || kz == N / 2) ? 1.0f : 2.0f;
-    const int warp = threadIdx.x / 32;
     const int mz2 = kz * kz;
+    const bool priv_ok = a.n_bins <= kPrivBins;
 #pragma unroll
     for (int l = 0; l < P::LPT; l++) {
         const int mx = signed_index(plane_row<N, T>(l), N);
@@ -239,16 +246,26 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
                     const float2 v = hold[l][q][k2];
                     const float fm2 = (float)m2;
                     const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (v.x * v.x + v.y * v.y);
-                    atomicAdd(&s_bins[warp][b], (double)val);
+                    if (priv_ok) priv[b * P::THREADS + threadIdx.x] += val;
+                    else atomicAdd(&s_bins[b], (double)val);
                 }
             }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < a.n_bins; b += P::THREADS) {
-        double sum = 0.0;
-        for (int wi = 0; wi < WARPS; wi++) sum += s_bins[wi][b];
-        if (sum != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], sum);
+    if (priv_ok) {
+        // warp w adds the slots of bins w, w + warps, ... in FP64, lanes then tree
+        constexpr int WARPS = P::THREADS / 32 > 0 ? P::THREADS / 32 : 1;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x / 32;
+        for (int b = warp; b < a.n_bins; b += WARPS) {
+            double sum = 0.0;
+            for (int i = lane; i < P::THREADS; i += 32) sum += (double)priv[b * P::THREADS + i];
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            if (lane == 0) s_bins[b] = sum;
+        }
+        __syncthreads();
     }
+    for (int b = threadIdx.x; b < a.n_bins; b += P::THREADS)
+        if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
 }
 
 // ------------------------------------------------------------------ pencil pass
@@ -616,7 +633,7 @@ cudaError_t prepare_n() {
     if ((e = set_smem(k_plane_forward<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_plane_filter_inverse<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM_PS)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_forward_batch<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -638,7 +655,7 @@ cudaError_t ps_from_boxes_n(eor_ctx* c) {
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
+        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
         trace_end(c);
     }
     return cudaGetLastError();
@@ -683,7 +700,7 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
+        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
         trace_end(c);
     }
     return cudaGetLastError();
@@ -725,7 +742,7 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     trace_end(c);
     PSArgs ap{c->d_psinter, c->d_diag_pair, c->d_bin_of_m2, c->d_diag_ps, 0, 1, nb, kf * kf * kf};
     trace_begin(c, kKPsPlane);
-    k_plane_ps<N, T><<<dim3(NH, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(ap);
+    k_plane_ps<N, T><<<dim3(NH, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
     trace_end(c);
     const double dx = c->cfg.box_mpc / c->n;
     const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
