@@ -181,6 +181,29 @@ int eor_trace_read(eor_ctx* ctx, double* total_ms, long long* launches, int n_cl
 const char* eor_kernel_class_name(int cls);
 long long eor_launch_count(const eor_ctx* ctx);
 
+/* Allocation-free power spectrum of one box. The paper has no counterpart: this is a
+ * service for callers that cannot allocate GPU memory where they need the result, such as
+ * code running while a stream is captured into a CUDA graph (cudaMalloc there fails or
+ * breaks the capture), code that must not synchronize the device (cudaMalloc and cudaFree
+ * can), or applications that give all device memory to their own pool. It needs no
+ * context and calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (the box's half spectrum, the bin of every |m|^2, the shell sums and mode counts) is one
+ * static device array of EOR21_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads
+ * the library until the process exits; n is at most EOR21_NOALLOC_MAX_N (larger n gives
+ * EOR_EINVAL). Same definition as eor_box_power_spectrum: box is a device pointer to
+ * float [n][n][n]; d2 (double [n_bins]) and nmodes (long long [n_bins], optional) are
+ * device pointers; bins are n_bins logarithmic bins on [k_lo, k_hi) for a box of side
+ * box_mpc. The work is ordered on cuda_stream (NULL: the legacy default stream) and the
+ * call returns without waiting. The first call on a device looks up the array's device
+ * address and sets kernel attributes, with that device current: make that first call
+ * before any stream capture. All calls share the array and the last call's contents stay
+ * in it (each call clears what it accumulates): calls that overlap on the GPU race, so
+ * issue them on one stream. Errors: EOR_EINVAL, EOR_ECUDA; message via eor_last_error(NULL). */
+#define EOR21_NOALLOC_MAX_N 128
+#define EOR21_NOALLOC_SCRATCH_BYTES (9u << 20)
+int eor_box_power_spectrum_noalloc(int n, double box_mpc, int n_bins, double k_lo, double k_hi, const float* box,
+                                   double* d2, long long* nmodes, void* cuda_stream);
+
 /* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
 const char* eor_last_error(const eor_ctx* ctx);
 const char* eor_version(void);

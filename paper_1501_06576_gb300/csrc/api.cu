@@ -140,6 +140,8 @@ cudaError_t trace_reserve(eor_ctx* c, size_t pairs) {
 
 namespace eor {
 
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+
 // Record on the context's stream; while the stream is being captured, as an external event
 // node so the graph records it on every replay.
 static void trace_record(eor_ctx* c, cudaEvent_t e) {

@@ -174,6 +174,11 @@ int basis_cells_per_cta();
 // kernels.cu
 cudaError_t prepare_kernels(int n);
 cudaError_t launch_ps_from_boxes(eor_ctx* c);
+cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signed char* bins, double* sums, int n_bins,
+                              float kf3, const PairInfo* pair_info, cudaStream_t stream);
+
+// api.cu: message returned by eor_last_error(NULL)
+void set_global_error(const std::string& msg);
 size_t flag_words_per_pair(int n);
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi);
 cudaError_t launch_ionization(eor_ctx* c, float* xhi_out);

@@ -766,7 +766,30 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
         default: return cudaErrorInvalidValue;                                              \
     }
 
+// Box power spectrum on caller-provided buffers (no context): R2C along z into spec, then
+// the plane pass adding the shell sums into sums. pair_info points at one zeroed PairInfo.
+template <int N, int T>
+cudaError_t box_ps_raw_n(const float* box, float2* spec, const signed char* bins, double* sums, int n_bins,
+                         float kf3, const PairInfo* pair_info, cudaStream_t stream) {
+    constexpr int NH = N / 2 + 1;
+    k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, stream>>>(box, spec);
+    PSArgs ap{spec, pair_info, bins, sums, 0, 1, n_bins, kf3};
+    k_plane_ps<N, T><<<dim3(NH, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, stream>>>(ap);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signed char* bins, double* sums, int n_bins,
+                              float kf3, const PairInfo* pair_info, cudaStream_t stream) {
+    switch (n) {
+        case 16: return box_ps_raw_n<16, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
+        case 32: return box_ps_raw_n<32, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
+        case 64: return box_ps_raw_n<64, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
+        case 128: return box_ps_raw_n<128, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box) { EOR_DISPATCH(c, box_power_spectrum_n, c, box) }
 

@@ -22,8 +22,8 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
            "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_method", "eor_basis_info", "eor_trace",
-           "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_last_error", "eor_version",
-           "eor_destroy")
+           "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
+           "eor_last_error", "eor_version", "eor_destroy")
 KERNEL_CLASSES = 8
 EOR_METHOD_BASIS, EOR_METHOD_DIRECT = 0, 1
 
@@ -88,6 +88,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_trace_read": (I, [P, P, P, I]),
         "eor_kernel_class_name": (ctypes.c_char_p, [I]),
         "eor_launch_count": (ctypes.c_longlong, [P]),
+        "eor_box_power_spectrum_noalloc": (I, [I, D, I, D, D, P, P, P, P]),
         "eor_last_error": (ctypes.c_char_p, [P]),
         "eor_version": (ctypes.c_char_p, []),
         "eor_destroy": (None, [P]),
@@ -318,6 +319,22 @@ class Context:
     basis_info = eor_basis_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count
+
+
+def box_power_spectrum_noalloc(n: int, box_mpc: float, box, d2, nmodes=None, n_bins: int = 14, k_lo: float = 0.1,
+                               k_hi: float = 1.5, stream=None) -> None:
+    """eor_box_power_spectrum_noalloc on CUDA tensors (box float32 [n,n,n], d2 float64 [n_bins],
+    nmodes int64 [n_bins] or None); ordered on `stream` (a cudaStream_t handle), no wait."""
+    lib = load_library()
+    for t in (box, d2) + (() if nmodes is None else (nmodes,)):
+        if not _is_torch_cuda(t) or not t.is_contiguous():
+            raise ValueError("box, d2 and nmodes must be contiguous CUDA tensors")
+    rc = lib.eor_box_power_spectrum_noalloc(int(n), float(box_mpc), int(n_bins), float(k_lo), float(k_hi),
+                                            ctypes.c_void_p(box.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                                            None if nmodes is None else ctypes.c_void_p(nmodes.data_ptr()),
+                                            ctypes.c_void_p(stream) if stream else None)
+    if rc != EOR_OK:
+        raise EorError(rc, lib.eor_last_error(None).decode())
 
 
 def version() -> str:
