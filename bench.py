@@ -240,7 +240,7 @@ def main():
         return reference_arm(args, rank, world)
 
     import torch
-    from paper_1501_06576_gb300 import eor21, synth
+    from paper_1501_06576_gb300 import eor21, shard, synth
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
@@ -299,9 +299,7 @@ def main():
         clk = clocks.stop()
         total_ms = sum(step_ms)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = shard.max_over_ranks(total_ms)      # timing only: no data-path collective
             torch.distributed.barrier()
         value = W * world * args.steps / (total_ms / 1e3)
 
