@@ -185,6 +185,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def basis_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", "basis.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def ncu_traffic(kernel_class: str):
     """DRAM bytes per task of a kernel class from the committed ncu summary, or None if the
     kernel source changed since it was captured."""
@@ -195,6 +200,21 @@ def ncu_traffic(kernel_class: str):
         if d.get("source_hash") != kernel_source_hash():
             return None
         return d["bytes_per_task"].get(kernel_class)
+    except Exception:
+        return None
+
+
+def ncu_launch_traffic(kernel_class: str, walkers: int):
+    """DRAM bytes of one full launch from the committed ncu capture, or None if the kernel
+    source or the workload differs from the capture's."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d["per_launch"][kernel_class]
+        if d.get("basis_source_hash") != basis_source_hash() or e["walkers"] != walkers or e["n"] != N:
+            return None
+        return e["bytes"]
     except Exception:
         return None
 
@@ -362,7 +382,7 @@ def main():
             achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
             peak = fp32_peak_tflops()
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic(dom), "kernel": dom,
+                    "traffic": ncu_launch_traffic(dom, W), "kernel": dom,
                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                     "flops_per_unit": flops_per_unit, "unit_def": "one (walker, redshift, radius) over all cells",
                     "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
