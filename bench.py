@@ -227,6 +227,19 @@ def fp32_peak_tflops() -> float:
     return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured BF16 GEMM peak (sustained: the contraction runs
+    inside a long step) times the nominal TF32/BF16 ratio 1.1/2.25."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            bf16 = float(json.load(f)["bf16_tflops_sustained"])
+        kind = "measured bf16 sustained x 1.1/2.25"
+    except Exception:
+        bf16, kind = 1700.0, "fallback bf16 sustained x 1.1/2.25"
+    return bf16 * 1.1 / 2.25, kind
+
+
 def algorithmic_bytes(n: int):
     """HBM bytes each FFT-pass kernel class must move per unit (one (walker, redshift,
     radius) task): complex64 half spectrum nh*n*n*8."""
@@ -235,9 +248,10 @@ def algorithmic_bytes(n: int):
             "pencil_ionize": nspec}          # read it back (flags, delta and delta T_b extra per pair)
 
 
-def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, steps):
-    """Batched evals/s of the per-radius FFT method on the same walkers (comparison only)."""
-    ctx.set_method(eor21.EOR_METHOD_DIRECT)
+def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, steps, method=None, note=None):
+    """Batched evals/s of another method on the same walkers (comparison only): by default
+    the per-radius FFT method."""
+    ctx.set_method(eor21.EOR_METHOD_DIRECT if method is None else method)
     for _ in range(2):
         ctx.likelihood(d_params, d_mock, d_sigma)
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -250,7 +264,7 @@ def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, 
     torch.cuda.synchronize()
     ctx.set_method(eor21.EOR_METHOD_BASIS)
     return {"value": W * dsteps / (d0.elapsed_time(d1) / 1e3), "unit": "evals/s",
-            "note": "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
+            "note": note or "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
 
 
 def main():
@@ -327,12 +341,16 @@ def main():
         ctx.set_params(params)
         tasks_per_step = sum(len(ctx.walker_ladder(w)) for w in range(W)) * len(ZS)
         basis_rank, basis_resid = ctx.basis_info()
+        uses_tensor_cores = basis_rank <= 32     # the default method's contraction runs on tcgen05
 
         # ---------------- the per-radius FFT method on the same workload (for comparison)
         ctx.trace(False)
-        direct = None
+        direct = simt = None
         for _ in range(0 if args.no_direct else 1):
             direct = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps)
+            simt = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps,
+                               method=eor21.EOR_METHOD_BASIS_SIMT,
+                               note="basis contraction on the FP32 units (EOR_METHOD_BASIS_SIMT), same walkers")
 
         # ---------------- end to end through host buffers (pinned), D2H of chi^2 every step
         h_params = torch.from_numpy(params).pin_memory().numpy()
@@ -376,16 +394,24 @@ def main():
         avg_launch_ms = class_ms[dom] / launches_dom
         share = {k: class_ms[k] / sum(class_ms.values()) for k in class_ms if class_ms[k] > 0}
         if dom == "basis_ionize":
-            # FMA-bound contraction: useful flops = 2 x rank per (cell, walker, redshift, radius)
+            # contraction: useful flops = 2 x rank per (cell, walker, redshift, radius)
             flops_per_unit = 2.0 * basis_rank * N ** 3
             units_per_launch = tasks_per_step * args.steps / launches_dom
             achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
-            peak = fp32_peak_tflops()
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": ncu_launch_traffic(dom, W), "kernel": dom,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            if uses_tensor_cores:
+                peak, peak_kind = tf32_peak_tflops()
+                # executed: 3 TF32 products (hi*hi, hi*lo, lo*hi) over K = 32 and 128-column chunks
+                cols_per_z = tasks_per_step // len(ZS)
+                executed = 3 * 2 * 32 * N ** 3 * (-(-cols_per_z // 128) * 128) * len(ZS)
+                extra = {"executed_tf32_tflops": executed * args.steps / launches_dom / (avg_launch_ms / 1e3) / 1e12}
+                bound = "tensor"
+            else:
+                peak, peak_kind = fp32_peak_tflops(), "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                extra, bound = {}, "alu"
+            roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": ncu_launch_traffic(dom, W), "kernel": dom, "peak_kind": peak_kind,
                     "flops_per_unit": flops_per_unit, "unit_def": "one (walker, redshift, radius) over all cells",
-                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
+                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share, **extra}
         else:
             peak, peak_kind = measured_peak()
             per_unit = algorithmic_bytes(N)
@@ -424,7 +450,9 @@ def main():
             "path_hbm_equivalent": {"value": hbm_equiv, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
                                     "peak_kind": hbm_kind,
                                     "def": "per (walker, z, radius): density half spectrum + flag read/write, over the whole step"},
-            "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid},
+            "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
+                       "contraction": "tcgen05 3xTF32" if uses_tensor_cores else "FP32 FMA"},
+            "basis_fp32_units": simt,
             "direct_method": direct, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0

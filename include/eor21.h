@@ -161,10 +161,14 @@ int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
  *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
  *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-9 on the grid's |k| for every R in
  *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
- *   that contraction.
+ *   that contraction, which runs on the tensor cores (tcgen05, TF32 split into hi + lo
+ *   parts, three products per step, FP32 accumulation) when the basis has at most 32
+ *   functions, else on the FP32 units.
+ * EOR_METHOD_BASIS_SIMT: the same contraction on the FP32 units only.
  * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius.
- * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. */
-enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1 };
+ * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. A bounded
+ * tensor-core wait that runs out makes the call return EOR_ETIMEOUT. */
+enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2 };
 int eor_set_method(eor_ctx* ctx, int method);
 int eor_basis_info(const eor_ctx* ctx, int* rank, double* max_residual);
 
@@ -203,6 +207,14 @@ long long eor_launch_count(const eor_ctx* ctx);
 #define EOR21_NOALLOC_SCRATCH_BYTES (9u << 20)
 int eor_box_power_spectrum_noalloc(int n, double box_mpc, int n_bins, double k_lo, double k_hi, const float* box,
                                    double* d2, long long* nmodes, void* cuda_stream);
+
+/* Check of the tensor-core (tcgen05, TF32) path on the current device: D = A B^T with
+ * A float [128][32], B float [n][32] (n a multiple of 16, 16..256) and D float [128][n],
+ * all device pointers, through the same operand layout, descriptors and tensor-memory
+ * reads as the tensor-core contraction; err (device int) gets bit 0 set if the MMA did not
+ * complete within its bounded wait. Ordered on cuda_stream, no wait. Not part of the
+ * method: a diagnostic of the build on this GPU. */
+int eor_tensor_core_check(const float* a, const float* b, float* d, int n, int* err, void* cuda_stream);
 
 /* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
 const char* eor_last_error(const eor_ctx* ctx);

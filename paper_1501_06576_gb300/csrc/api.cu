@@ -104,6 +104,7 @@ int check_device_error(eor_ctx* c) {
                                                          "(zeta > 0, 0 < R_mfp <= r_mfp_max, 0 < log10 T_vir < 12)");
     if (err & eor::kErrLadder) return fail(c, EOR_EINVAL, "radius ladder longer than the tables (raise r_mfp_max)");
     if (err & eor::kErrSigmaRange) return fail(c, EOR_EINVAL, "radius or halo mass outside the sigma^2 table range");
+    if (err & eor::kErrTimeout) return fail(c, EOR_ETIMEOUT, "a bounded tensor-core wait ran out");
     return EOR_OK;
 }
 
@@ -208,7 +209,7 @@ void eor_destroy(eor_ctx* c) {
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
                     c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_kd_m2,
                     c->d_m2_to_kd, c->d_basis, c->d_coef_tab, c->d_phi_m2, c->d_F, c->d_coef, c->d_dtb, c->d_xpart,
-                    c->d_err};
+                    c->d_cols, c->d_ncols, c->d_err};
     for (void* p : bufs) dev_free(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -296,14 +297,15 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
         return EOR_ECUDA;
     }
     c->ncc = (c->max_radii + 31) / 32;
-    const size_t parts = c->n3 / eor::basis_cells_per_cta();
+    const size_t parts = c->n3 / 128;   // the finest x_HI partial sums (per warp of 128 cells)
     ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->max_radii * c->kb) &&
-         alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts);
+         alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts) &&
+         alloc_n(c, &c->d_cols, (size_t)W * c->max_radii) && alloc_n(c, &c->d_ncols, 1);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");
     }
-    if ((e = eor::prepare_basis_kernel(c)) != cudaSuccess) {
+    if ((e = eor::prepare_basis_kernel(c)) != cudaSuccess || (e = eor::prepare_basis_tc(c)) != cudaSuccess) {
         g_create_error = std::string("basis kernel: ") + cudaGetErrorString(e);
         eor_destroy(c);
         return EOR_ECUDA;
@@ -551,9 +553,11 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
 
 int eor_set_method(eor_ctx* c, int method) {
     if (!c) return EOR_EINVAL;
-    if (method != EOR_METHOD_BASIS && method != EOR_METHOD_DIRECT) return fail(c, EOR_EINVAL, "unknown method");
+    if (method != EOR_METHOD_BASIS && method != EOR_METHOD_DIRECT && method != EOR_METHOD_BASIS_SIMT)
+        return fail(c, EOR_EINVAL, "unknown method");
     CK(cudaStreamSynchronize(c->stream), "method");
-    c->tune.method = method == EOR_METHOD_BASIS ? eor::kMethodBasis : eor::kMethodDirect;
+    c->tune.method = method == EOR_METHOD_BASIS ? eor::kMethodBasis
+                     : method == EOR_METHOD_DIRECT ? eor::kMethodDirect : eor::kMethodBasisSimt;
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;

@@ -26,6 +26,7 @@ enum : int {
     kErrLadder = 1,       // a walker's ladder exceeds the table size
     kErrSigmaRange = 2,   // a radius outside the sigma^2 table
     kErrParam = 4,        // non-finite or out-of-range walker parameter
+    kErrTimeout = 8,      // a bounded tensor-core wait ran out
 };
 
 // Per (walker, redshift): everything the fused kernels need.
@@ -64,7 +65,7 @@ enum KernelClass : int {
     kKClasses = 8
 };
 
-enum Method : int { kMethodBasis = 0, kMethodDirect = 1 };
+enum Method : int { kMethodBasis = 0, kMethodDirect = 1, kMethodBasisSimt = 2 };
 
 struct Tuning {
     int group;          // radii per pencil launch (G)
@@ -130,7 +131,9 @@ struct eor_ctx {
     float* d_F = nullptr;            // [n_z][kb][n^3] basis fields
     float* d_coef = nullptr;         // [max_walkers][max_radii][kb] walker coefficients
     float* d_dtb = nullptr;          // [max_walkers][n_z][n^3] delta T_b
-    float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/cells per CTA] per-CTA x_HI sums
+    float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/128] partial x_HI sums
+    int* d_cols = nullptr;           // [max_walkers * max_radii] (walker << 8 | radius) columns
+    int* d_ncols = nullptr;          // [1] number of columns
     int n_ready_tables = 0;
 
     // state
@@ -170,6 +173,12 @@ cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out);
 cudaError_t prepare_basis_kernel(eor_ctx* c);
 size_t basis_ionize_smem(int kb, int max_radii);
 int basis_cells_per_cta();
+
+// tcgen05.cu
+size_t basis_tc_smem();
+cudaError_t prepare_basis_tc(eor_ctx* c);
+cudaError_t build_columns(eor_ctx* c, int n_walkers);
+cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out);
 
 // kernels.cu
 cudaError_t prepare_kernels(int n);

@@ -805,7 +805,7 @@ bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) { EOR_DISPATCH(c, forward_spectrum_n, c, zi) }
 
 cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
-    if (c->tune.method == kMethodBasis) {
+    if (c->tune.method == kMethodBasis || c->tune.method == kMethodBasisSimt) {
         cudaError_t e = launch_basis_ionize(c, xhi_out);
         if (e != cudaSuccess) return e;
         return launch_ps_from_boxes(c);

@@ -386,7 +386,8 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
     trace_end(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return build_walker_coefs(c, n_walkers);
+    if ((e = build_walker_coefs(c, n_walkers)) != cudaSuccess) return e;
+    return build_columns(c, n_walkers);
 }
 
 cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab) {

@@ -23,9 +23,9 @@ EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
            "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
-           "eor_last_error", "eor_version", "eor_destroy")
+           "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy")
 KERNEL_CLASSES = 8
-EOR_METHOD_BASIS, EOR_METHOD_DIRECT = 0, 1
+EOR_METHOD_BASIS, EOR_METHOD_DIRECT, EOR_METHOD_BASIS_SIMT = 0, 1, 2
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -89,6 +89,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_kernel_class_name": (ctypes.c_char_p, [I]),
         "eor_launch_count": (ctypes.c_longlong, [P]),
         "eor_box_power_spectrum_noalloc": (I, [I, D, I, D, D, P, P, P, P]),
+        "eor_tensor_core_check": (I, [P, P, P, I, P, P]),
         "eor_last_error": (ctypes.c_char_p, [P]),
         "eor_version": (ctypes.c_char_p, []),
         "eor_destroy": (None, [P]),
@@ -335,6 +336,23 @@ def box_power_spectrum_noalloc(n: int, box_mpc: float, box, d2, nmodes=None, n_b
                                             ctypes.c_void_p(stream) if stream else None)
     if rc != EOR_OK:
         raise EorError(rc, lib.eor_last_error(None).decode())
+
+
+def tensor_core_check(a, b, stream=None):
+    """D = A B^T through the tcgen05 TF32 path (a: CUDA float32 [128, 32], b: [n, 32]);
+    returns (D, err) as CUDA tensors after synchronising the stream."""
+    import torch
+    lib = load_library()
+    n = int(b.shape[0])
+    d = torch.zeros((128, n), dtype=torch.float32, device=a.device)
+    err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    rc = lib.eor_tensor_core_check(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                   ctypes.c_void_p(d.data_ptr()), n, ctypes.c_void_p(err.data_ptr()),
+                                   ctypes.c_void_p(stream) if stream else None)
+    if rc != EOR_OK:
+        raise EorError(rc, lib.eor_last_error(None).decode())
+    torch.cuda.synchronize()
+    return d, err
 
 
 def version() -> str:

@@ -24,8 +24,8 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT]
-METHOD_IDS = ["basis", "direct"]
+METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_SIMT]
+METHOD_IDS = ["basis_tensor_cores", "direct", "basis_fp32_units"]
 
 
 def make_ctx(n, box, zs, max_walkers=1, method=eor21.EOR_METHOD_BASIS, **kw):
@@ -317,19 +317,21 @@ def test_filter_basis_reproduces_tophat(n, box):
     print(f"n={n} L={box}: basis rank {rank}, max residual {resid:.1e}")
 
 
-def test_basis_and_direct_methods_agree():
+@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_BASIS_SIMT],
+                         ids=["basis_tensor_cores", "basis_fp32_units"])
+def test_basis_and_direct_methods_agree(method):
     n, box, zs = 64, 100.0, (8.0, 9.5)
     params = synth.walker_params(6, seed=12)
     delta = synth.density_boxes(n, box, zs, seed=13)
     out = {}
-    for m in METHODS:
+    for m in (method, eor21.EOR_METHOD_DIRECT):
         with make_ctx(n, box, zs, max_walkers=6, method=m) as ctx:
             ctx.init_boxes(delta)
             ctx.set_params(params)
             xhi, xm = ctx.run_ionization(want_xhi=True)
             d2, _, cnt = ctx.power_spectrum()
             out[m] = (xhi, xm, d2, cnt)
-    a, b = out[METHODS[0]], out[METHODS[1]]
+    a, b = out[method], out[eor21.EOR_METHOD_DIRECT]
     frac, rest = compare_xhi(a[0], b[0].astype(np.float64))
     assert frac <= FLIP_TOL and rest <= XHI_TOL
     np.testing.assert_allclose(a[1], b[1], atol=2e-4)
