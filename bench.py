@@ -341,7 +341,7 @@ def main():
         ctx.set_params(params)
         tasks_per_step = sum(len(ctx.walker_ladder(w)) for w in range(W)) * len(ZS)
         basis_rank, basis_resid = ctx.basis_info()
-        uses_tensor_cores = basis_rank <= 32     # the default method's contraction runs on tcgen05
+        uses_tensor_cores = basis_rank + 1 <= 32   # basis values plus the folded threshold fit K = 32
 
         # ---------------- the per-radius FFT method on the same workload (for comparison)
         ctx.trace(False)
@@ -400,9 +400,9 @@ def main():
             achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
             if uses_tensor_cores:
                 peak, peak_kind = tf32_peak_tflops()
-                # executed: 3 TF32 products (hi*hi, hi*lo, lo*hi) over K = 32 and 128-column chunks
+                # executed: 3 TF32 products (hi*hi, hi*lo, lo*hi) over K = 32 and 64-column chunks
                 cols_per_z = tasks_per_step // len(ZS)
-                executed = 3 * 2 * 32 * N ** 3 * (-(-cols_per_z // 128) * 128) * len(ZS)
+                executed = 3 * 2 * 32 * N ** 3 * (-(-cols_per_z // 64) * 64) * len(ZS)
                 extra = {"executed_tf32_tflops": executed * args.steps / launches_dom / (avg_launch_ms / 1e3) / 1e12}
                 bound = "tensor"
             else:

@@ -485,11 +485,11 @@ cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_
 
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
-    if (c->tune.method == kMethodBasis && c->kb <= 32) {   // tensor cores: K padded to 32
+    if (c->tune.method == kMethodBasis && basis_tc_fits(c->kb)) {   // tensor cores
         cudaError_t e = launch_basis_ionize_tc(c, xhi_out);
         if (e != cudaSuccess) return e;
         trace_begin(c, kKFinish);
-        k_xpart_reduce<<<c->n_walkers * n_z, 256, 0, c->stream>>>(c->d_xpart, (int)(c->n3 / 128), c->d_xhi_sum);
+        k_xpart_reduce<<<c->n_walkers * n_z, 256, 0, c->stream>>>(c->d_xpart, (int)(c->n3 / 64), c->d_xhi_sum);
         trace_end(c);
         return cudaGetLastError();
     }

@@ -133,6 +133,8 @@ struct eor_ctx {
     float* d_dtb = nullptr;          // [max_walkers][n_z][n^3] delta T_b
     float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/128] partial x_HI sums
     int* d_cols = nullptr;           // [max_walkers * max_radii] (walker << 8 | radius) columns
+    unsigned char* d_tcA = nullptr;  // tensor-core A operands of every CTA (TF32 hi/lo core matrices)
+    unsigned char* d_tcB = nullptr;  // tensor-core coefficient chunks per redshift
     int* d_ncols = nullptr;          // [1] number of columns
     int n_ready_tables = 0;
 
@@ -176,7 +178,11 @@ int basis_cells_per_cta();
 
 // tcgen05.cu
 size_t basis_tc_smem();
+bool basis_tc_fits(int kb);
+size_t basis_tc_a_bytes(long long n3, int n_z);
+size_t basis_tc_b_bytes(int max_columns, int n_z);
 cudaError_t prepare_basis_tc(eor_ctx* c);
+cudaError_t format_basis_tc(eor_ctx* c);
 cudaError_t build_columns(eor_ctx* c, int n_walkers);
 cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out);
 
