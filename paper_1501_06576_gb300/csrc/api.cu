@@ -209,7 +209,7 @@ void eor_destroy(eor_ctx* c) {
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
                     c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_kd_m2,
                     c->d_m2_to_kd, c->d_basis, c->d_coef_tab, c->d_phi_m2, c->d_F, c->d_coef, c->d_dtb, c->d_xpart,
-                    c->d_cols, c->d_ncols, c->d_tcA, c->d_tcB, c->d_err};
+                    c->d_cols, c->d_gmeta, c->d_goff, c->d_ncols, c->d_tcA, c->d_tcB, c->d_xq, c->d_err};
     for (void* p : bufs) dev_free(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -297,13 +297,15 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
         return EOR_ECUDA;
     }
     c->ncc = (c->max_radii + 31) / 32;
-    const size_t parts = c->n3 / 64;   // the finest x_HI partial sums (per warp of 64 cells)
+    const size_t parts = c->n3 / 128;   // the finest x_HI partial sums (per warp of 128 cells)
     ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->max_radii * c->kb) &&
          alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts) &&
-         alloc_n(c, &c->d_cols, (size_t)W * c->max_radii) && alloc_n(c, &c->d_ncols, 1);
+         alloc_n(c, &c->d_ncols, 1);
     if (ok && eor::basis_tc_fits(c->kb))
         ok = alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, Z)) &&
-             alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(W * c->max_radii, Z));
+             alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
+             alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
+             alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");

@@ -132,9 +132,12 @@ struct eor_ctx {
     float* d_coef = nullptr;         // [max_walkers][max_radii][kb] walker coefficients
     float* d_dtb = nullptr;          // [max_walkers][n_z][n^3] delta T_b
     float* d_xpart = nullptr;        // [max_walkers][n_z][n^3/128] partial x_HI sums
-    int* d_cols = nullptr;           // [max_walkers * max_radii] (walker << 8 | radius) columns
+    int* d_cols = nullptr;           // tensor-core column slots: (walker << 8 | radius) or -1
+    int* d_gmeta = nullptr;          // per group of 32 column slots: walker << 2 | first << 1 | last
+    int* d_goff = nullptr;           // [max_walkers + 1] first group of each walker
     unsigned char* d_tcA = nullptr;  // tensor-core A operands of every CTA (TF32 hi/lo core matrices)
     unsigned char* d_tcB = nullptr;  // tensor-core coefficient chunks per redshift
+    unsigned long long* d_xq = nullptr;   // [pairs] fixed-point x_HI sums of the tensor-core path
     int* d_ncols = nullptr;          // [1] number of columns
     int n_ready_tables = 0;
 
@@ -180,7 +183,8 @@ int basis_cells_per_cta();
 size_t basis_tc_smem();
 bool basis_tc_fits(int kb);
 size_t basis_tc_a_bytes(long long n3, int n_z);
-size_t basis_tc_b_bytes(int max_columns, int n_z);
+size_t basis_tc_b_bytes(const eor_ctx* c);
+size_t basis_tc_column_slots(const eor_ctx* c);
 cudaError_t prepare_basis_tc(eor_ctx* c);
 cudaError_t format_basis_tc(eor_ctx* c);
 cudaError_t build_columns(eor_ctx* c, int n_walkers);

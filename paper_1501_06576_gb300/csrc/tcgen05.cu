@@ -87,21 +87,28 @@ extern "C" int eor_tensor_core_check(const float* a, const float* b, float* d, i
 namespace eor {
 namespace {
 
-constexpr int kTcTiles = 4;                            // M tiles of 128 cells
+constexpr int kTcTiles = 2;                            // M tiles of 128 cells per CTA
 constexpr int kTcCells = 128 * kTcTiles;               // cells per CTA
-constexpr int kTcN = 64;                               // (walker, radius) columns per chunk
+constexpr int kTcN = 128;                              // (walker, radius) columns per chunk (MMA N)
+constexpr int kTcStages = 3;                           // coefficient chunks in flight
+constexpr int kGroup = 32;                             // epilogue columns per tensor-memory read
 constexpr uint32_t kTileBytes = 128 * tc::kKMax * 4;   // one 128 x 32 TF32 tile (16 KB)
-constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (128 KB)
-constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a 64-column chunk (16 KB)
-// column meta: walker, zeta, T_0, 1/sqrt(2 s^2) at R_cell columns (64 each), end masks (4 + pad 12)
-constexpr int kMetaEnds = 4 * kTcN;
-constexpr uint32_t kMBytes = (4 * kTcN + 16) * 4;
+constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (64 KB)
+constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chunk (32 KB)
+// chunk meta: one 16-byte record per group of kGroup columns: (walker << 2 | first << 1 |
+// last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0)
+constexpr int kGroupsPerChunk = kTcN / kGroup;
+constexpr uint32_t kMBytes = kGroupsPerChunk * 16;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
-constexpr uint32_t kTmemCols = 512;                       // 2 buffers x 4 tiles x 64 columns
-constexpr int kTcThreads = 384;                           // warp 0 producer, warps 4-11 epilogue
-constexpr int kTcEpi = 256;                               // epilogue threads
+constexpr uint32_t kTmemCols = 512;                       // 2 buffers x kTcTiles x kTcN columns
+constexpr int kTcThreads = 640;                           // warp 0 producer, warps 4-19 epilogue
+constexpr int kTcEpi = 512;                               // epilogue threads: 2 per cell
 constexpr float kNever = 1.0e30f;                         // folded threshold that no delta_R reaches
-constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact warp sums
+constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
+static_assert(2 * kTcTiles * kTcN <= (int)kTmemCols, "tensor memory");
+static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+static_assert(kTcEpi == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
+static_assert(kTcN == 128 && kGroup == 32, "k_format_b: one block per chunk, one warp per group; 4 epilogue groups");
 
 // Basis fields -> the CTAs' A operands: [z][cta][hi/lo][tile][128 x 32 core-matrix layout],
 // K index kb holding the constant 1 (kb + 1 <= 32).
@@ -123,37 +130,28 @@ __global__ void k_format_a(const float* F, int kb, long long n3, int n_z, unsign
     }
 }
 
-// Walker coefficients -> chunks of 64 columns: [z][chunk][B hi | B lo | meta]. Column
-// (walker w, radius j) holds c_b(R_j) for b < kb and, at K index kb, minus its threshold, so
-// that the contraction yields D = delta_R - threshold: delta_crit(R_j) (Eq. 1 flag test
-// D >= 0) above R_cell, delta_c at R_cell (where f_coll needs delta_c - delta_R). An
-// infinite delta_crit (no ionization possible) becomes kNever. Column slots past the last
-// column carry zero coefficients and -kNever. Meta, per column: the walker at its R_cell
-// column (-1 elsewhere), and there zeta, T_0 and 1/sqrt(2 s^2(R_cell)) (0 when s^2 <= 0);
-// then the mask of R_cell columns of each 16 columns.
-__global__ void k_format_b(const int* cols, const int* ncols, const float* coef, const PairInfo* pairs, int kb,
-                           int max_radii, int n_z, int slots, float delta_c, unsigned char* out) {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x, zi = blockIdx.y;
-    if (slot >= slots) return;   // slots is a multiple of 64: whole warps leave together
+// Walker coefficients -> chunks of kTcN columns: [z][chunk][B hi | B lo | meta], one block
+// per chunk and one warp per group of kGroup columns. Column (walker w, radius j) holds
+// c_b(R_j) for b < kb and, at K index kb, minus its threshold, so that the contraction
+// yields D = delta_R - threshold: delta_crit(R_j) (Eq. 1 flag test D >= 0) above R_cell,
+// delta_c at R_cell (where f_coll needs delta_c - delta_R). An infinite delta_crit (no
+// ionization possible) becomes kNever. Padding columns carry zero coefficients and
+// -kNever, so that D = -kNever there.
+__global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* gmeta, const int* ncols,
+                                                   const float* coef, const PairInfo* pairs, int kb, int max_radii,
+                                                   int n_z, int chunks_per_z, float delta_c, unsigned char* out) {
+    const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kTcN + row;
     const int nc = *ncols;
-    unsigned char* chunk = out + ((size_t)zi * (slots / kTcN) + slot / kTcN) * kChunkBytes;
-    const int row = slot % kTcN;
-    float thr = kNever, zeta = 0.0f, t0 = 0.0f, inv = 0.0f;
-    int walker_end = -1;
+    unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * kChunkBytes;
+    float thr = kNever;
     const float* src = nullptr;
-    if (slot < nc) {
-        const int cw = cols[slot], w = cw >> 8, j = cw & 255;
+    const int cw = slot < nc ? cols[slot] : -1;
+    if (cw >= 0) {
+        const int w = cw >> 8, j = cw & 255;
         const PairInfo& pi = pairs[(size_t)w * n_z + zi];
         src = coef + ((size_t)w * max_radii + j) * kb;
-        const bool last = j == pi.n_r - 1;
         const float dcrit = pi.delta_crit[j];
-        thr = last ? delta_c : (isfinite(dcrit) ? dcrit : kNever);
-        if (last) {
-            walker_end = w;
-            zeta = pi.zeta;
-            t0 = pi.t0;
-            inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
-        }
+        thr = j == pi.n_r - 1 ? delta_c : (isfinite(dcrit) ? dcrit : kNever);
     }
     for (int b = 0; b < tc::kKMax; b++) {
         const float v = b < kb ? (src ? src[b] : 0.0f) : (b == kb ? -thr : 0.0f);
@@ -161,69 +159,94 @@ __global__ void k_format_b(const int* cols, const int* ncols, const float* coef,
         *reinterpret_cast<uint32_t*>(chunk + tc::core_offset(row, b)) = hi;
         *reinterpret_cast<uint32_t*>(chunk + kBBytes / 2 + tc::core_offset(row, b)) = lo;
     }
-    int* meta = reinterpret_cast<int*>(chunk + kBBytes);
-    float* metaf = reinterpret_cast<float*>(meta);
-    meta[row] = walker_end;
-    metaf[kTcN + row] = zeta;
-    metaf[2 * kTcN + row] = t0;
-    metaf[3 * kTcN + row] = inv;
-    const unsigned ends = __ballot_sync(0xffffffffu, walker_end >= 0);
-    if ((row & 15) == 0) meta[kMetaEnds + row / 16] = (int)((ends >> (threadIdx.x & 16)) & 0xFFFFu);
-    if (row < 12) meta[kMetaEnds + 4 + row] = 0;
+    if ((row & (kGroup - 1)) == 0) {
+        const int g = row / kGroup, gi = blockIdx.x * kGroupsPerChunk + g;
+        const int info = gi < nc / kGroup ? gmeta[gi] : -1;
+        float zeta = 0.0f, t0 = 0.0f, inv = 0.0f;
+        if (info >= 0) {
+            const PairInfo& pi = pairs[(size_t)(info >> 2) * n_z + zi];
+            zeta = pi.zeta;
+            t0 = pi.t0;
+            inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
+        }
+        reinterpret_cast<int4*>(chunk + kBBytes)[g] =
+            make_int4(info, __float_as_int(zeta), __float_as_int(t0), __float_as_int(inv));
+    }
 }
 
-// Pairwise maximum tree of 16 values (depth 4).
-__device__ __forceinline__ float max16(const float (&v)[16]) {
-    float m8[8];
+// AND of v[1..31] (LOP3 tree): its sign bit is clear iff some of them has a clear sign bit.
+__device__ __forceinline__ uint32_t and31(const float (&v)[32]) {
+    uint32_t m[8];
 #pragma unroll
-    for (int i = 0; i < 8; i++) m8[i] = fmaxf(v[i], v[i + 8]);
-#pragma unroll
-    for (int i = 0; i < 4; i++) m8[i] = fmaxf(m8[i], m8[i + 4]);
-    return fmaxf(fmaxf(m8[0], m8[2]), fmaxf(m8[1], m8[3]));
+    for (int i = 0; i < 8; i++)
+        m[i] = (i == 0 ? 0xFFFFFFFFu : __float_as_uint(v[i])) & __float_as_uint(v[i + 8]) &
+               __float_as_uint(v[i + 16]) & __float_as_uint(v[i + 24]);
+    return (m[0] & m[1] & m[2]) & (m[3] & m[4] & m[5]) & (m[6] & m[7]);
+}
+
+// erfc(x) for x >= 0 from the Chebyshev fit of Numerical Recipes (Press et al. 1992, Sec. 6.2,
+// "erfcc"; fractional error below 1.2e-7 everywhere): t = 1 / (1 + x/2) and
+// erfc(x) = t exp(-x^2 + P(t)) with P a degree-9 polynomial. Branch-free.
+__device__ __forceinline__ float erfc_cheb(float x) {
+    const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    return t * expf(fmaf(-x, x, p));
 }
 
 struct TcArgs {
     const unsigned char* A;     // [n_z][cta][kABytes]
     const unsigned char* B;     // [n_z][chunk][kChunkBytes]
     const int* ncols;           // [1] number of columns
-    const PairInfo* pairs;      // [walker * n_z + zi]
     const float* delta;         // [n_z][n3]
     float* dtb;                 // [pair][n3]
     float* xhi_out;             // optional [pair][n3]
-    float* xpart;               // [pair][n3 / 64] per-warp neutral-fraction sums
+    unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
     int* err;
     int n_z, chunks_per_z;
     long long n3;
-    float delta_c;
 };
 
-// One CTA: 512 cells of one redshift against every (walker, radius) column, as four 128-row
-// tiles. The cells' basis values (A) and each 64-column chunk of coefficients (B) arrive by
-// bulk copy in the TF32 hi/lo core-matrix layout; thread 0 issues, per tile and K step,
-// hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation) into one of two tensor-memory buffers,
-// so D(cell, column) = sum_b F_b c_b - threshold = delta_R - threshold. Warps 4-11 run the
-// epilogue of the other buffer meanwhile, each thread two cells: the Eq. 1 flag of a
-// walker is "D >= 0 at some radius above R_cell" (a max over 16 columns where no walker
-// ends, bit masks of D >= 0 where one does); at the walker's R_cell column
-// (D = delta_R - delta_c) it forms x_HI and delta T_b (coalesced stores) and an exact
-// fixed-point warp sum of x_HI.
-// Buffer hand-offs: B(c) is reloaded only after MMA(c) completed; the thresholds / meta of
-// chunk c (read by the epilogue) only after the epilogue released its buffer; MMA(c + 2)
-// waits for both. Every wait is bounded; on a timeout the CTA sets kErrTimeout, waits for
-// its copies and MMAs in flight and frees its tensor memory.
+// One CTA: 256 cells of one redshift (two 128-row tiles) against every (walker, radius)
+// column. The cells' basis values (A) and each 128-column chunk of coefficients (B) arrive by
+// bulk copy in the TF32 hi/lo core-matrix layout; thread 0 issues, per K step, product and
+// tile, hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation) into one of two tensor-memory
+// buffers, so D(cell, column) = sum_b F_b c_b - threshold = delta_R - threshold. Each
+// walker's columns start on a group of 32: its R_cell column first (D = delta_R - delta_c),
+// then its radii from R_mfp down, then padding. Warps 4-11 run the epilogue of the other
+// buffer meanwhile, two threads per cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag
+// of a walker, "D >= 0 (sign bit clear) at some radius above R_cell", is an AND of sign bits
+// over its columns; at its last group the thread forms x_HI and delta T_b (coalesced stores)
+// and the warp adds its exact fixed-point x_HI sum to the pair's total.
+// Roles: thread 32 issues the bulk copies, thread 0 the MMAs (it waits only for operands and
+// a free accumulator buffer, so the tensor pipe stays fed), warps 4-19 the epilogue.
+// Hand-offs: chunk c + 3 reuses chunk c's stage after MMA(c) (coefficients) and the
+// epilogue's read of chunk c's meta; MMA(c) reuses the tensor memory of chunk c - 2 after
+// its epilogue. Every wait is bounded; on a timeout the CTA sets kErrTimeout, waits for its
+// copies and MMAs in flight and frees its tensor memory.
 __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* As = sm;                                // A hi tiles then lo tiles
-    unsigned char* Bs = As + kABytes;                      // [2][kBBytes]
-    unsigned char* Ms = Bs + 2 * kBBytes;                  // [2][kMBytes]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + 2 * kMBytes);
-    uint64_t* barA = bars + 0;
-    uint64_t* barB = bars + 1;       // [2] coefficient tile landed
-    uint64_t* barM = bars + 3;       // [2] thresholds / meta landed
-    uint64_t* barD = bars + 5;       // [2] MMAs into tensor-memory buffer done
-    uint64_t* barE = bars + 7;       // [2] epilogue released the buffer
-    uint64_t* barF = bars + 9;       // MMAs drained (abort path)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 10);
+    unsigned char* Bs = As + kABytes;                      // [kTcStages][kBBytes]
+    unsigned char* Ms = Bs + kTcStages * kBBytes;          // [kTcStages][kMBytes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kTcStages * kMBytes);
+    uint64_t* barA = bars;
+    uint64_t* barB = bars + 1;                  // [kTcStages] coefficient tile landed
+    uint64_t* barBe = barB + kTcStages;         // [kTcStages] its MMAs are done: stage free
+    uint64_t* barM = barBe + kTcStages;         // [kTcStages] meta landed
+    uint64_t* barMe = barM + kTcStages;         // [kTcStages] the epilogue has read it: stage free
+    uint64_t* barD = barMe + kTcStages;         // [2] MMAs into tensor-memory buffer done
+    uint64_t* barE = barD + 2;                  // [2] epilogue released the buffer
+    uint64_t* barF = barE + 2;                  // MMAs drained (abort path)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(barF + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -236,9 +259,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
     if (t == 0) {
         tc::mbar_init(barA, 1);
         tc::mbar_init(barF, 1);
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < kTcStages; s++) {
             tc::mbar_init(barB + s, 1);
+            tc::mbar_init(barBe + s, 1);
             tc::mbar_init(barM + s, 1);
+            tc::mbar_init(barMe + s, kTcEpi);
+        }
+        for (int s = 0; s < 2; s++) {
             tc::mbar_init(barD + s, 1);
             tc::mbar_init(barE + s, kTcEpi);
         }
@@ -249,64 +276,72 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t kTries = 1u << 24;
-    // producer bookkeeping: parity of the phase each copy barrier still owes, or -1
-    int owedA = -1, owedB[2] = {-1, -1}, owedM[2] = {-1, -1};
+    // copy-thread bookkeeping: parity of the phase each copy barrier still owes, or -1
+    int owedA = -1, owedB[kTcStages], owedM[kTcStages];
+#pragma unroll
+    for (int s = 0; s < kTcStages; s++) owedB[s] = owedM[s] = -1;
 
-    if (t == 0 && nch > 0) {
-        // ---------------- producer: bulk copies and MMA issue
+    if (t == 32 && nch > 0) {
+        // ---------------- copy thread: the CTA's A operands once, then chunk c into stage
+        // c % kTcStages as soon as chunk c - kTcStages has left it
         const unsigned char* Ag = a.A + ((size_t)zi * (a.n3 / kTcCells) + blockIdx.x) * kABytes;
         const unsigned char* Bg = a.B + (size_t)zi * a.chunks_per_z * kChunkBytes;
         tc::mbar_expect_tx(barA, kABytes);
         tc::bulk_g2s(As, Ag, kABytes, barA);
         owedA = 0;
-        for (int c = 0; c < 2 && c < nch; c++) {
-            tc::mbar_expect_tx(barB + c, kBBytes);
-            tc::bulk_g2s(Bs + c * kBBytes, Bg + (size_t)c * kChunkBytes, kBBytes, barB + c);
-            owedB[c] = 0;
-            tc::mbar_expect_tx(barM + c, kMBytes);
-            tc::bulk_g2s(Ms + c * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, kMBytes, barM + c);
-            owedM[c] = 0;
+        bool ok = true;
+        for (int c = 0; c < nch && ok; c++) {
+            const int st = c % kTcStages;
+            const uint32_t use = (uint32_t)(c / kTcStages);   // how many chunks used the stage before
+            if (use > 0) ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kTries, abort);
+            if (!ok) break;
+            tc::mbar_expect_tx(barB + st, kBBytes);
+            tc::bulk_g2s(Bs + st * kBBytes, Bg + (size_t)c * kChunkBytes, kBBytes, barB + st);
+            owedB[st] = (int)(use & 1u);
+            if (use > 0) ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kTries, abort);
+            if (!ok) break;
+            tc::mbar_expect_tx(barM + st, kMBytes);
+            tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, kMBytes, barM + st);
+            owedM[st] = (int)(use & 1u);
         }
+        if (!ok) {
+            *abort = 1;
+            atomicOr(a.err, kErrTimeout);
+        }
+    } else if (t == 0 && nch > 0) {
+        // ---------------- MMA thread: waits only for operands and a free accumulator buffer
         bool ok = tc::mbar_wait_or_abort(barA, 0, kTries, abort);
-        if (ok) owedA = -1;
         const uint32_t idesc = tc::idesc_tf32(128, kTcN);
         for (int c = 0; c < nch && ok; c++) {
-            const int s = c & 1;
-            const uint32_t par = (uint32_t)(c >> 1) & 1u;
-            ok = tc::mbar_wait_or_abort(barB + s, par, kTries, abort);
+            const int st = c % kTcStages, tb = c & 1;
+            ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
+            if (ok && c >= 2)   // the epilogue of chunk c - 2 has released tensor-memory buffer tb
+                ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - 2) >> 1) & 1u, kTries, abort);
             if (!ok) break;
-            owedB[s] = -1;
             tc::fence_after_sync();
-            for (int q = 0; q < kTcTiles; q++) {
-                const uint32_t d = tmem + (uint32_t)(s * kTcTiles * kTcN + q * kTcN);
-                for (int st = 0; st < tc::kKMax / 8; st++) {
-                    const uint32_t ko = (uint32_t)st * 2 * tc::kLBO;
-                    const uint64_t ah = tc::smem_desc(tc::smem_addr(As + q * kTileBytes) + ko, tc::kLBO, tc::kSBO);
-                    const uint64_t al =
-                        tc::smem_desc(tc::smem_addr(As + (kTcTiles + q) * kTileBytes) + ko, tc::kLBO, tc::kSBO);
-                    const uint64_t bh = tc::smem_desc(tc::smem_addr(Bs + s * kBBytes) + ko, tc::kLBO, tc::kSBO);
-                    const uint64_t bl =
-                        tc::smem_desc(tc::smem_addr(Bs + s * kBBytes + kBBytes / 2) + ko, tc::kLBO, tc::kSBO);
-                    tc::mma_tf32(d, ah, bh, idesc, st > 0 ? 1u : 0u);
-                    tc::mma_tf32(d, ah, bl, idesc, 1u);
-                    tc::mma_tf32(d, al, bh, idesc, 1u);
+            // the tiles' accumulators alternate, so that consecutive MMAs are independent
+            for (int ks = 0; ks < tc::kKMax / 8; ks++) {
+                const uint32_t ko = (uint32_t)ks * 2 * tc::kLBO;
+                const uint64_t bh = tc::smem_desc(tc::smem_addr(Bs + st * kBBytes) + ko, tc::kLBO, tc::kSBO);
+                const uint64_t bl = tc::smem_desc(tc::smem_addr(Bs + st * kBBytes + kBBytes / 2) + ko, tc::kLBO, tc::kSBO);
+                uint64_t ah[kTcTiles], al[kTcTiles];
+#pragma unroll
+                for (int q = 0; q < kTcTiles; q++) {
+                    ah[q] = tc::smem_desc(tc::smem_addr(As + q * kTileBytes) + ko, tc::kLBO, tc::kSBO);
+                    al[q] = tc::smem_desc(tc::smem_addr(As + (kTcTiles + q) * kTileBytes) + ko, tc::kLBO, tc::kSBO);
                 }
+#pragma unroll
+                for (int q = 0; q < kTcTiles; q++)
+                    tc::mma_tf32(tmem + (uint32_t)(tb * kTcTiles * kTcN + q * kTcN), ah[q], bh, idesc, ks > 0 ? 1u : 0u);
+#pragma unroll
+                for (int q = 0; q < kTcTiles; q++)
+                    tc::mma_tf32(tmem + (uint32_t)(tb * kTcTiles * kTcN + q * kTcN), ah[q], bl, idesc, 1u);
+#pragma unroll
+                for (int q = 0; q < kTcTiles; q++)
+                    tc::mma_tf32(tmem + (uint32_t)(tb * kTcTiles * kTcN + q * kTcN), al[q], bh, idesc, 1u);
             }
-            tc::mma_commit(barD + s);
-            if (c >= 1 && c + 1 < nch) {   // chunk c + 1 into the buffers chunk c - 1 used
-                const int s1 = (c + 1) & 1;
-                const uint32_t p1 = (uint32_t)((c - 1) >> 1) & 1u;
-                ok = tc::mbar_wait_or_abort(barD + s1, p1, kTries, abort);   // MMA(c - 1) has read B
-                if (!ok) break;
-                tc::mbar_expect_tx(barB + s1, kBBytes);
-                tc::bulk_g2s(Bs + s1 * kBBytes, Bg + (size_t)(c + 1) * kChunkBytes, kBBytes, barB + s1);
-                owedB[s1] = (int)(((c + 1) >> 1) & 1);
-                ok = tc::mbar_wait_or_abort(barE + s1, p1, kTries, abort);   // epilogue(c - 1) is done
-                if (!ok) break;
-                tc::mbar_expect_tx(barM + s1, kMBytes);
-                tc::bulk_g2s(Ms + s1 * kMBytes, Bg + (size_t)(c + 1) * kChunkBytes + kBBytes, kMBytes, barM + s1);
-                owedM[s1] = (int)(((c + 1) >> 1) & 1);
-            }
+            tc::mma_commit(barD + tb);    // accumulators ready for the epilogue
+            tc::mma_commit(barBe + st);   // coefficient stage free for the copy thread
         }
         if (!ok) {
             *abort = 1;
@@ -314,93 +349,76 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
         }
     } else if (warp >= 4 && nch > 0) {
         // ---------------- epilogue warps: warp 4 + e owns tensor-memory lanes 32 (e % 4) .. + 31
-        // (the quarter its warp index allows) of tiles 2 (e / 4) and 2 (e / 4) + 1
-        const int e = warp - 4, lq = warp & 3, q0 = 2 * (e >> 2);
-        long long cell[2];
-        float dens[2];
-#pragma unroll
-        for (int u = 0; u < 2; u++) {
-            cell[u] = cell0 + (q0 + u) * 128 + lq * 32 + lane;
-            dens[u] = __ldg(a.delta + (size_t)zi * a.n3 + cell[u]);
-        }
-        bool fl[2] = {false, false};   // the walker's Eq. 1 flag from the radii seen so far
+        // (the quarter its warp index allows) of tile (e / 4) % 2, and groups 2 (e / 8) and
+        // 2 (e / 8) + 1 of every chunk: one cell, half the columns. A walker never spans
+        // the two halves (multi-group walkers start on an even group).
+        const int e = warp - 4, lq = warp & 3, q = (e >> 2) & 1, g0 = 2 * (e >> 3);
+        const long long cell = cell0 + q * 128 + lq * 32 + lane;
+        const float dens = __ldg(a.delta + (size_t)zi * a.n3 + cell);
         for (int c = 0; c < nch; c++) {
-            const int s = c & 1;
-            const uint32_t par = (uint32_t)(c >> 1) & 1u;
-            if (!tc::mbar_wait_or_abort(barD + s, par, kTries, abort) ||
-                !tc::mbar_wait_or_abort(barM + s, par, kTries, abort)) {
+            const int st = c % kTcStages, tb = c & 1;
+            if (!tc::mbar_wait_or_abort(barD + tb, (uint32_t)(c >> 1) & 1u, kTries, abort) ||
+                !tc::mbar_wait_or_abort(barM + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort)) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 *abort = 1;
                 break;
             }
             tc::fence_after_sync();
-            const int* meta = reinterpret_cast<const int*>(Ms + s * kMBytes);
-            const float* metaf = reinterpret_cast<const float*>(meta);
-            const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(s * kTcTiles * kTcN + q0 * kTcN);
-            for (int g = 0; g < kTcN / 16 && c * kTcN + g * 16 < ncols; g++) {
-                float v[2][16];
-                tc::tmem_ld16x2(base + (uint32_t)(g * 16), base + (uint32_t)(kTcN + g * 16), v[0], v[1]);
-                uint32_t ends = (uint32_t)meta[kMetaEnds + g];
-                if (ends == 0u) {
+            const int4* gm = reinterpret_cast<const int4*>(Ms + st * kMBytes) + g0;
+            const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) +
+                                  (uint32_t)(tb * kTcTiles * kTcN + q * kTcN + g0 * kGroup);
+            int4 m[2];
+            float dd[2];
+            uint32_t fa[2];
+            {
+                float v[2][32];
+                tc::tmem_ld32x2(base, v[0], v[1]);
+                m[0] = gm[0];
+                m[1] = gm[1];
+                tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
+                // flags: AND of sign bits over the walker's radii above R_cell (column 0 of its
+                // first group is R_cell, D = delta_R - delta_c)
+                const uint32_t a0 = and31(v[0]), a1 = and31(v[1]);
+                const bool second = (m[1].x & 2) == 0;   // group 1 continues the walker of group 0
+                fa[0] = a0;
+                dd[0] = v[0][0];
+                fa[1] = second ? a0 & a1 & __float_as_uint(v[1][0]) : a1;
+                dd[1] = second ? v[0][0] : v[1][0];
+            }
+            float xh[2];
 #pragma unroll
-                    for (int u = 0; u < 2; u++) fl[u] = fl[u] || max16(v[u]) >= 0.0f;
-                    continue;
-                }
-                // columns of this group with D >= 0, as bits
-                uint32_t pos[2] = {0u, 0u};
+            for (int u = 0; u < 2; u++) {   // two independent chains
+                const float zeta = __int_as_float(m[u].y), inv = __int_as_float(m[u].w);
+                // f_coll at R_cell (1 where delta_R >= delta_c), no ionization where s^2 <= 0
+                const float f = dd[u] >= 0.0f ? 1.0f : erfc_cheb(-dd[u] * inv);
+                xh[u] = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+                xh[u] = (fa[u] >> 31) == 0u ? 0.0f : xh[u];   // flagged at a larger radius (Eq. 1)
+            }
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    pos[0] |= v[0][i] >= 0.0f ? (1u << i) : 0u;
-                    pos[1] |= v[1][i] >= 0.0f ? (1u << i) : 0u;
-                }
-                uint32_t start = 0;   // first column of the current walker within the group
-                while (ends) {        // the same for every thread
-                    const uint32_t p = (uint32_t)(__ffs(ends) - 1);
-                    ends &= ends - 1u;
-                    const uint32_t seg = ((1u << p) - 1u) & ~((1u << start) - 1u);   // radii above R_cell
-                    const int col = g * 16 + (int)p, w = meta[col];
-                    const float zeta = metaf[kTcN + col], t0 = metaf[2 * kTcN + col], inv = metaf[3 * kTcN + col];
-                    float d[2];   // D = delta_R(R_cell) - delta_c
-                    tc::tmem_ld1x2(base + (uint32_t)col, base + (uint32_t)(kTcN + col), d[0], d[1]);
-                    const size_t pair = (size_t)w * a.n_z + zi;
-                    int xq = 0;
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        float xh = 1.0f;
-                        if (fl[u] || (pos[u] & seg)) {
-                            xh = 0.0f;   // flagged at a larger radius (Eq. 1)
-                        } else if (inv > 0.0f) {
-                            const float f = d[u] >= 0.0f ? 1.0f : erfcf(-d[u] * inv);
-                            xh = 1.0f - fminf(1.0f, zeta * f);
-                        }
-                        a.dtb[pair * a.n3 + cell[u]] = t0 * xh * (1.0f + dens[u]);
-                        if (a.xhi_out) a.xhi_out[pair * a.n3 + cell[u]] = xh;
-                        xq += __float2int_rn(xh * kXScale);
-                        fl[u] = false;
-                    }
-                    xq = __reduce_add_sync(0xffffffffu, xq);   // exact: integers
-                    if (lane == 0)
-                        a.xpart[pair * (size_t)(a.n3 / 64) + (size_t)blockIdx.x * 8 + e] = (float)xq / kXScale;
-                    start = p + 1;
-                }
-                const uint32_t rest = 0xFFFFu & ~((1u << start) - 1u);   // the next walker's radii
-#pragma unroll
-                for (int u = 0; u < 2; u++) fl[u] = (pos[u] & rest) != 0u;
+            for (int u = 0; u < 2; u++) {
+                if (m[u].x < 0 || !(m[u].x & 1)) continue;   // no walker ends in this group (uniform)
+                const size_t pair = (size_t)(m[u].x >> 2) * a.n_z + zi;
+                a.dtb[pair * a.n3 + cell] = __int_as_float(m[u].z) * xh[u] * (1.0f + dens);
+                if (a.xhi_out) a.xhi_out[pair * a.n3 + cell] = xh[u];
+                const int xq = __reduce_add_sync(0xffffffffu, __float2int_rn(xh[u] * kXScale));   // exact
+                if (lane == 0) atomicAdd(a.xq + pair, (unsigned long long)xq);
             }
             tc::fence_before_sync();
-            tc::mbar_arrive(barE + s);
+            tc::mbar_arrive(barE + tb);
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t == 0 && nch > 0 && *abort) {
-        // drain: every MMA issued so far, then every bulk copy still owed
-        tc::mma_commit(barF);
-        tc::mbar_wait(barF, 0, kTries);
-        if (owedA >= 0) tc::mbar_wait(barA, (uint32_t)owedA, kTries);
-        for (int s = 0; s < 2; s++) {
-            if (owedB[s] >= 0) tc::mbar_wait(barB + s, (uint32_t)owedB[s], kTries);
-            if (owedM[s] >= 0) tc::mbar_wait(barM + s, (uint32_t)owedM[s], kTries);
+    if (nch > 0 && *abort) {
+        if (t == 0) {   // drain every MMA issued so far
+            tc::mma_commit(barF);
+            tc::mbar_wait(barF, 0, kTries);
+        } else if (t == 32) {   // wait for every bulk copy that may still land
+            if (owedA >= 0) tc::mbar_wait(barA, (uint32_t)owedA, kTries);
+            for (int s = 0; s < kTcStages; s++) {
+                if (owedB[s] >= 0) tc::mbar_wait(barB + s, (uint32_t)owedB[s], kTries);
+                if (owedM[s] >= 0) tc::mbar_wait(barM + s, (uint32_t)owedM[s], kTries);
+            }
         }
     }
     __syncthreads();
@@ -411,24 +429,66 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
     }
 }
 
-// Flattened (walker, radius) columns of the walkers, in walker order, and their count.
-__global__ void k_build_columns(const WalkerInfo* walkers, int n_walkers, int* cols, int* ncols) {
-    if (threadIdx.x != 0) return;
-    int c = 0;
-    for (int w = 0; w < n_walkers; w++)
-        for (int j = 0; j < walkers[w].n_r; j++) cols[c++] = (w << 8) | j;
-    *ncols = c;
+// Fixed-point x_HI totals -> the per-pair FP64 sums the power-spectrum stage reads.
+__global__ void k_xq_finish(const unsigned long long* xq, int pairs, double* xhi_sum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < pairs) xhi_sum[i] = (double)xq[i] / (double)kXScale;
+}
+
+// Columns of the walkers, in walker order, each walker starting on a group of kGroup columns
+// (on an even group when it needs two, so that no walker spans the two halves of a chunk):
+// its R_cell radius first, then its radii from R_mfp down, then padding (-1) to the end of
+// its last group. cols[] holds walker << 8 | radius index; gmeta[] per group walker << 2 |
+// first << 1 | last, or -1 for a group left empty; *ncols the number of columns including
+// padding. Thread 0 places the walkers, then the block fills the columns.
+__global__ void k_build_columns(const WalkerInfo* walkers, int n_walkers, int* goff, int* cols, int* gmeta,
+                                int* ncols) {
+    static_assert(kMaxRadii <= 2 * kGroup, "a walker spans at most two groups");
+    if (threadIdx.x == 0) {
+        int g = 0;
+        for (int w = 0; w < n_walkers; w++) {
+            const int ng = (walkers[w].n_r + kGroup - 1) / kGroup;
+            if (ng == 2 && (g & 1)) g++;
+            goff[w] = g;
+            g += ng;
+        }
+        goff[n_walkers] = g;
+        *ncols = g * kGroup;
+    }
+    __syncthreads();
+    const int total = goff[n_walkers];
+    for (int i = threadIdx.x; i < total * kGroup; i += blockDim.x) cols[i] = -1;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) gmeta[i] = -1;
+    __syncthreads();
+    for (int w = threadIdx.x / 32; w < n_walkers; w += blockDim.x / 32) {
+        const int nr = walkers[w].n_r, g0 = goff[w], ng = (nr + kGroup - 1) / kGroup;
+        for (int i = threadIdx.x % 32; i < ng * kGroup; i += 32) {
+            const int j = i == 0 ? nr - 1 : (i < nr ? i - 1 : -1);
+            cols[(size_t)g0 * kGroup + i] = j >= 0 ? (w << 8) | j : -1;
+        }
+        for (int i = threadIdx.x % 32; i < ng; i += 32)
+            gmeta[g0 + i] = (w << 2) | (i == 0 ? 2 : 0) | (i == ng - 1 ? 1 : 0);
+    }
+}
+
+// Column slots: every walker's radii rounded up to whole groups (plus the group an aligned
+// two-group walker may skip), then to whole chunks.
+int tc_slots(const eor_ctx* c) {
+    const int groups = (c->max_radii + kGroup - 1) / kGroup;
+    const int per_walker = (groups > 1 ? groups + 1 : groups) * kGroup;
+    return (c->cfg.max_walkers * per_walker + kTcN - 1) / kTcN * kTcN;
 }
 
 }  // namespace
 
 bool basis_tc_fits(int kb) { return kb + 1 <= tc::kKMax; }   // basis values plus the constant column
 
-size_t basis_tc_smem() { return kABytes + 2 * kBBytes + 2 * kMBytes + 10 * sizeof(uint64_t) + 16; }
-size_t basis_tc_a_bytes(long long n3, int n_z) { return (size_t)n_z * (size_t)(n3 / kTcCells) * kABytes; }
-size_t basis_tc_b_bytes(int max_columns, int n_z) {
-    return (size_t)n_z * (size_t)((max_columns + kTcN - 1) / kTcN) * kChunkBytes;
+size_t basis_tc_smem() {
+    return kABytes + kTcStages * (kBBytes + kMBytes) + (4 * kTcStages + 6) * sizeof(uint64_t) + 16;
 }
+size_t basis_tc_a_bytes(long long n3, int n_z) { return (size_t)n_z * (size_t)(n3 / kTcCells) * kABytes; }
+size_t basis_tc_b_bytes(const eor_ctx* c) { return (size_t)c->cfg.n_z * (size_t)(tc_slots(c) / kTcN) * kChunkBytes; }
+size_t basis_tc_column_slots(const eor_ctx* c) { return (size_t)tc_slots(c); }
 
 cudaError_t prepare_basis_tc(eor_ctx* c) {
     (void)c;
@@ -444,23 +504,29 @@ cudaError_t format_basis_tc(eor_ctx* c) {
 
 cudaError_t build_columns(eor_ctx* c, int n_walkers) {
     trace_begin(c, kKTables);
-    k_build_columns<<<1, 32, 0, c->stream>>>(c->d_walkers, n_walkers, c->d_cols, c->d_ncols);
+    k_build_columns<<<1, 256, 0, c->stream>>>(c->d_walkers, n_walkers, c->d_goff, c->d_cols, c->d_gmeta, c->d_ncols);
     trace_end(c);
-    const int slots = (c->cfg.max_walkers * c->max_radii + kTcN - 1) / kTcN * kTcN;
+    const int chunks = tc_slots(c) / kTcN;
     trace_begin(c, kKTables);
-    k_format_b<<<dim3((slots + 127) / 128, c->cfg.n_z), 128, 0, c->stream>>>(
-        c->d_cols, c->d_ncols, c->d_coef, c->d_pairs, c->kb, c->max_radii, c->cfg.n_z, slots, (float)c->cfg.delta_c,
-        c->d_tcB);
+    k_format_b<<<dim3(chunks, c->cfg.n_z), kTcN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
+                                                               c->d_pairs, c->kb, c->max_radii, c->cfg.n_z, chunks,
+                                                               (float)c->cfg.delta_c, c->d_tcB);
     trace_end(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
-    const int slots = (c->cfg.max_walkers * c->max_radii + kTcN - 1) / kTcN * kTcN;
-    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, c->d_pairs, c->d_delta, c->d_dtb, xhi_out, c->d_xpart, c->d_err,
-             c->cfg.n_z, slots / kTcN, (long long)c->n3, (float)c->cfg.delta_c};
+    const int pairs = c->n_walkers * c->cfg.n_z;
+    cudaError_t e = cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * pairs, c->stream);
+    if (e != cudaSuccess) return e;
+    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, c->d_delta, c->d_dtb, xhi_out, c->d_xq, c->d_err,
+             c->cfg.n_z, tc_slots(c) / kTcN, (long long)c->n3};
     trace_begin(c, kKBasis);
     k_basis_ionize_tc<<<dim3((unsigned)(c->n3 / kTcCells), c->cfg.n_z), kTcThreads, basis_tc_smem(), c->stream>>>(a);
+    trace_end(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    trace_begin(c, kKFinish);
+    k_xq_finish<<<(pairs + 255) / 256, 256, 0, c->stream>>>(c->d_xq, pairs, c->d_xhi_sum);
     trace_end(c);
     return cudaGetLastError();
 }
