@@ -186,8 +186,12 @@ def kernel_source_hash() -> str:
 
 
 def basis_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", "basis.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the sources of the contraction kernels (a stale traffic record is not used)."""
+    h = hashlib.sha256()
+    for name in ("basis.cu", "tcgen05.cu", "tc.cuh"):
+        with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_class: str):

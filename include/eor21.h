@@ -152,7 +152,7 @@ int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* k
 /* Launch schedule of eor_run_ionization / eor_likelihood (results do not depend on it):
  * group = radii per pencil launch (1..16), pairs = (walker, redshift) pairs in flight
  * (1..64; scratch memory grows with group * pairs), plane_threads = CTA size of the
- * 128^3 plane kernels (512 or 1024; ignored for smaller grids). Defaults 8, 8, 512.
+ * 128^3 plane kernels (512 or 1024; ignored for smaller grids). Defaults 8, 16, 512.
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
 

@@ -84,7 +84,7 @@ struct eor_ctx {
     int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
     size_t n3 = 0, nspec = 0;
     eor::CosmoParams cosmo{};
-    eor::Tuning tune{8, 8, 512, eor::kMethodBasis};
+    eor::Tuning tune{8, 16, 512, eor::kMethodBasis};
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]

@@ -375,17 +375,30 @@ __device__ __forceinline__ void pencil_load_spectrum(const PencilSmem<N>& s, con
         s.xs[row * P::TY + p] = __ldg(src + (size_t)row * kstride + p);
 }
 
-// Load the tile's TY pencils of a real box (contiguous TY * N floats) into ds.
+// Load the tile's TY pencils of a real box (contiguous TY * N floats) into ds: every load of
+// a thread is issued before the first store, so that enough bytes are in flight to cover the
+// memory latency.
 template <int N>
 __device__ __forceinline__ void pencil_load_real(const PencilSmem<N>& s, const float* src) {
     using P = Pencil<N>;
+    constexpr int V = P::TY * N / 4;                             // float4 per tile
+    constexpr int PER = (V + P::THREADS - 1) / P::THREADS;
     const float4* s4 = reinterpret_cast<const float4*>(src);
-    for (int e = threadIdx.x; e < P::TY * N / 4; e += P::THREADS) {
-        const float4 v = __ldg(s4 + e);
-        const int pp = (4 * e) / N, zz = (4 * e) % N;
-        float2* d = reinterpret_cast<float2*>(s.ds + pp * P::DS + zz);
-        d[0] = make_float2(v.x, v.y);
-        d[1] = make_float2(v.z, v.w);
+    float4 v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int e = threadIdx.x + k * P::THREADS;
+        if (e < V) v[k] = __ldg(s4 + e);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int e = threadIdx.x + k * P::THREADS;
+        if (e < V) {
+            const int pp = (4 * e) / N, zz = (4 * e) % N;
+            float2* d = reinterpret_cast<float2*>(s.ds + pp * P::DS + zz);
+            d[0] = make_float2(v[k].x, v[k].y);
+            d[1] = make_float2(v[k].z, v[k].w);
+        }
     }
 }
 
