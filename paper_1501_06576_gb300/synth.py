@@ -13,7 +13,8 @@ pipeline and are not reproduced here):
 * density boxes: a Gaussian random field with a BBKS LCDM spectrum, normalised
   to sigma_8, grown linearly to redshift z and clipped at delta > -1, stored as
   FP32 in row-major (x, y, z) order;
-* walker parameters: (zeta, R_mfp, log10 T_vir) drawn uniformly in a box.
+* walker parameters: (zeta, R_mfp, log10 T_vir) drawn uniformly in a box;
+* parameter vectors of the surrogate network (test inputs).
 
 All random numbers come from one counter-based generator, SplitMix64 (Steele,
 Lea & Flood 2014, "Fast splittable pseudorandom number generators"), with
@@ -130,6 +131,19 @@ def walker_params(count: int, seed: int, zeta=(5.0, 100.0), r_mfp=(5.0, 20.0),
     lo = np.array([zeta[0], r_mfp[0], log10_tvir[0]])
     hi = np.array([zeta[1], r_mfp[1], log10_tvir[1]])
     return lo + (hi - lo) * u
+
+
+def mlp_params(seed: int, dims) -> np.ndarray:
+    """Flat FP64 parameter vector of a multilayer perceptron with layers dims = [(fan_in,
+    fan_out), ...], laid out layer by layer as W [fan_out][fan_in] then b [fan_out]: weights
+    uniform on +-sqrt(3 / fan_in) (unit-variance pre-activations for unit inputs), biases
+    normal with standard deviation 0.1. Test and initialisation inputs only."""
+    parts = []
+    for li, (fi, fo) in enumerate(dims):
+        a = np.sqrt(3.0 / fi)
+        parts.append((uniform01(seed, 2000 + 2 * li, fi * fo) * 2.0 - 1.0) * a)
+        parts.append(0.1 * normals(seed, 2001 + 2 * li, fo))
+    return np.concatenate(parts)
 
 
 # Workloads (sizes and parameters of the hot path's configurations).
