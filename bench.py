@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-trace", action="store_true", help="time without the per-kernel event brackets")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
+    ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
+    ap.add_argument("--emu-steps", type=int, default=6000, help="Adam steps of the surrogate")
+    ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
     return ap.parse_args()
 
 
@@ -271,6 +275,82 @@ def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, 
             "note": note or "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
 
 
+def time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args):
+    """The learned surrogate on the same boxes: train on simulated spectra of args.emu_train
+    walkers (x 3 redshifts), calibrate the fallback threshold on 2048 more, then time
+    likelihood calls of args.emu_walkers walkers (emulated where trusted, simulated
+    otherwise) and measure the emulated spectra against the simulation on those walkers."""
+    cap = ctx.cfg.max_walkers
+
+    def simulate(p):
+        chis, d2s = [], []
+        for i in range(0, len(p), cap):
+            c, d = ctx.likelihood(torch.from_numpy(p[i:i + cap]).cuda(), d_mock, d_sigma, want_d2=True)
+            chis.append(c)
+            d2s.append(d)
+        return torch.cat(chis), torch.cat(d2s)
+
+    train_p = synth.walker_params(args.emu_train, seed=100)
+    val_p = synth.walker_params(2048, seed=101)
+    test_p = synth.walker_params(args.emu_walkers, seed=102)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, train_d2 = simulate(train_p)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    _, val_d2 = simulate(val_p)
+    test_chi, test_d2 = simulate(test_p)
+    emu = eor21.Emulator(z=ZS, members=4, max_rows=max(16384, len(ZS) * args.emu_walkers),
+                         max_samples=len(ZS) * args.emu_train, seed=3, stream=stream.cuda_stream)
+    emu.set_data(torch.from_numpy(train_p).cuda(), train_d2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = emu.train(args.emu_steps, 1024, 2e-3, seed=11)
+    train_s = time.perf_counter() - t0
+    tau, val_frac = emu.calibrate(torch.from_numpy(val_p).cuda(), val_d2, recall=0.99)
+    d_test = torch.from_numpy(test_p).cuda()
+    # accuracy on the timed walkers, against their simulated spectra
+    pred, _, fb = emu.predict(test_p)
+    truth = test_d2.cpu().numpy()
+    ok = np.isfinite(truth) & (truth > 1e-4)
+    err = np.where(ok, np.abs(10.0 ** pred / np.where(ok, truth, 1.0) - 1.0), 0.0).max(axis=(1, 2))
+    acc = fb == 0
+    # device time of the prediction alone (features, 4 layers x 4 members, combination)
+    for _ in range(3):
+        emu.predict(d_test)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        emu.predict(d_test)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    predict_ms = e0.elapsed_time(e1) / 10
+    for _ in range(2):
+        emu.likelihood(ctx, d_test, d_mock, d_sigma)
+    steps = max(3, args.steps // 2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        chi, _, fb2 = emu.likelihood(ctx, d_test, d_mock, d_sigma)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    same = bool(torch.equal(chi[fb2 == 1], test_chi[fb2 == 1]))
+    emu.close()
+    return {"value": args.emu_walkers * steps / (ms / 1e3), "unit": "evals/s", "walkers_per_call": args.emu_walkers,
+            "fallback_frac": float(1 - acc.mean()), "miss_frac_over_5pct": float(np.mean(err[acc] > 0.05)) if acc.any() else 0.0,
+            "median_rel_err_emulated": float(np.median(err[acc])) if acc.any() else None,
+            "p99_rel_err_emulated": float(np.quantile(err[acc], 0.99)) if acc.any() else None,
+            "tau_dex": tau, "val_fallback_frac": val_frac, "fallback_chi2_equals_simulation": same,
+            "predict_ms": predict_ms, "train": {"walkers": args.emu_train, "samples": args.emu_train * len(ZS),
+                                                "steps": args.emu_steps, "batch": 1024, "members": 4,
+                                                "seconds": train_s, "final_loss": [float(x) for x in loss]},
+            "datagen_s": gen_s,
+            "note": "surrogate (4 MLPs 4-256-256-256-14, bf16 weights) with simulation fallback; evals/s over "
+                    "likelihood calls of walkers_per_call walkers, device-resident inputs"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -387,6 +467,11 @@ def main():
         torch.cuda.synchronize()
         plain = pw / (p0.elapsed_time(p1) / 1e3)
 
+        # ---------------- the learned surrogate with simulation fallback (same boxes)
+        emulator = None
+        if not args.no_emulator and rank == 0:
+            emulator = time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args)
+
     if rank != 0:
         return 0
 
@@ -457,7 +542,7 @@ def main():
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
                        "contraction": "tcgen05 3xTF32" if uses_tensor_cores else "FP32 FMA"},
             "basis_fp32_units": simt,
-            "direct_method": direct, "cpu_baseline": cpu, "clocks": clk}
+            "direct_method": direct, "emulator": emulator, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0
 

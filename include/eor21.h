@@ -216,6 +216,119 @@ int eor_box_power_spectrum_noalloc(int n, double box_mpc, int n_bins, double k_l
  * method: a diagnostic of the build on this GPU. */
 int eor_tensor_core_check(const float* a, const float* b, float* d, int n, int* err, void* cuda_stream);
 
+/* ------------------------------------------------------------------------------------
+ * Learned surrogate of the power spectrum (not in the paper: a service around it).
+ *
+ * An ensemble of multilayer perceptrons maps a walker's (zeta, R_mfp, log10 T_vir) and a
+ * redshift to log10 Delta^2 in the n_bins bins of Sec. 2.2, so that a likelihood call can
+ * skip the simulation for walkers where the ensemble is trusted; every other walker runs
+ * the full excursion-set simulation above (the "fallback"), which also generates the
+ * training set and judges the surrogate's error.
+ *
+ * Network of each member: inputs x = (zeta, R_mfp, log10 T_vir, z), each mapped linearly
+ * from its prior interval onto [-1, 1] (z from [min z, max z]); hidden layers
+ * h = GELU(W h' + b), GELU(u) = u Phi(u); output y = W h' + b, with
+ * log10 Delta^2_b = mean_b + std_b y_b (mean and std of the training targets per bin).
+ * Weights are used rounded to bfloat16 (round to nearest even); sums and activations are
+ * FP32. Training: mean squared error of y over samples and bins, Adam (beta 0.9, 0.999,
+ * eps 1e-8) on FP32 master weights, the gradient passing the bf16 rounding unchanged.
+ *
+ * Parameter vector of one member (float, eor_emu_n_params values): layer by layer from
+ * the input, W [fan_out][fan_in] then b [fan_out]; members follow one another.
+ *
+ * Fallback rule: a walker is simulated instead of emulated when, at any redshift, the
+ * largest per-bin standard deviation of the members' log10 Delta^2 exceeds the threshold
+ * tau (set by eor_emu_calibrate or eor_emu_set_threshold; +infinity before), when a
+ * predicted bin lies below 10 x d2_floor, or when its parameters leave the prior box.
+ * -------------------------------------------------------------------------------------- */
+#define EOR21_EMU_MAX_HIDDEN 8
+#define EOR21_EMU_MAX_MEMBERS 8
+
+typedef struct eor_emu eor_emu;   /* opaque, library-owned */
+
+typedef struct {
+    int n_z;                     /* redshifts covered (the z input), 1..EOR21_MAX_Z */
+    double z[EOR21_MAX_Z];
+    int n_bins;                  /* outputs: log10 Delta^2 per bin, 1..EOR21_MAX_BINS */
+    int hidden;                  /* width of every hidden layer, 4..1024 (256) */
+    int n_hidden;                /* hidden layers, 1..EOR21_EMU_MAX_HIDDEN (3) */
+    int members;                 /* ensemble size, 1..EOR21_EMU_MAX_MEMBERS (4) */
+    int max_rows;                /* largest minibatch, and largest walkers x n_z of one prediction (16384) */
+    int max_samples;             /* largest training set in samples = walkers x n_z (65536) */
+    double prior_lo[3], prior_hi[3];   /* box of (zeta, R_mfp, log10 T_vir): (5, 5, 4) .. (100, 20, 6) */
+    double d2_floor;             /* Delta^2 floor before log10 [mK^2] (1e-4) */
+    double err_tol;              /* per-bin relative error the fallback guards (0.05) */
+    unsigned long long seed;     /* weight initialisation */
+} eor_emu_config;
+
+/* Defaults above for the 128^3, z = 8, 9, 10 workload's 14 bins. */
+void eor_emu_default_config(eor_emu_config* cfg);
+
+/* Create on the current device, ordered on cuda_stream (NULL: own stream); weights are
+ * initialised uniform in +-sqrt(3 / fan_in) (biases 0) from a counter-based SplitMix64
+ * stream keyed by cfg.seed and the member. */
+int eor_emu_create(const eor_emu_config* cfg, void* cuda_stream, eor_emu** out);
+long long eor_emu_n_params(const eor_emu* emu);   /* per member */
+
+/* Training set: params double [n_walkers][3] and the simulated spectra d2 double
+ * [n_walkers][n_z][n_bins] (eor_likelihood's d2). Targets are log10 max(d2, d2_floor)
+ * (NaN -> floor); their per-bin mean and standard deviation (FP64) become the output
+ * normalisation. n_walkers x n_z <= max_samples. */
+int eor_emu_set_data(eor_emu* emu, const double* params, const double* d2, int n_walkers, int mem);
+
+/* `steps` Adam steps of every member on minibatches of `batch` samples drawn with
+ * replacement (SplitMix64 keyed by seed, member and step), learning rate lr decaying by
+ * a cosine from lr to lr / 50 over the call. One captured CUDA graph per step, replayed.
+ * loss (optional, double [members], host): mean minibatch loss of the last min(steps, 64)
+ * steps. */
+int eor_emu_train(eor_emu* emu, int steps, int batch, double lr, unsigned long long seed, double* loss);
+
+/* Diagnostics of the training kernels on a caller batch shared by all members:
+ * x float [n][4] (network inputs), t float [n][n_bins] (standardised targets), n <= max_rows.
+ * eor_emu_forward: y float [members][n][n_bins]. eor_emu_loss_grad: loss double [members]
+ * and grad float [members][n_params]. eor_emu_train_batch: `steps` full-batch Adam steps at
+ * the constant rate lr; loss (optional) double [members] of the last step. */
+int eor_emu_forward(eor_emu* emu, const float* x, int n, float* y, int mem);
+int eor_emu_loss_grad(eor_emu* emu, const float* x, const float* t, int n, double* loss, float* grad, int mem);
+int eor_emu_train_batch(eor_emu* emu, const float* x, const float* t, int n, int steps, double lr, double* loss,
+                        int mem);
+
+/* Master weights float [members][n_params] out or in (set resets Adam's moments and step
+ * count), and the output normalisation double [2][n_bins] = (mean, std), std > 0. */
+int eor_emu_get_weights(eor_emu* emu, float* w, int mem);
+int eor_emu_set_weights(eor_emu* emu, const float* w, int mem);
+int eor_emu_get_normalization(eor_emu* emu, double* mean_std);
+int eor_emu_set_normalization(eor_emu* emu, const double* mean_std);
+
+/* Ensemble prediction for walkers params double [n_walkers][3] at every redshift
+ * (n_walkers x n_z <= max_rows): log10_d2 double [n_walkers][n_z][n_bins] (members'
+ * mean), spread double [n_walkers][n_z] (largest per-bin standard deviation over members,
+ * in dex) and fallback int [n_walkers] (1: the rule above sends it to the simulation);
+ * each output optional. */
+int eor_emu_predict(eor_emu* emu, const double* params, int n_walkers, double* log10_d2, double* spread,
+                    int* fallback, int mem);
+
+/* Choose tau on validation walkers with simulated spectra d2 (as in eor_emu_set_data): the
+ * largest threshold (capped at the largest score seen) such that at least `recall` of
+ * the walkers whose emulated Delta^2 misses the simulated one by more than err_tol in some
+ * bin with modes are sent to the simulation. tau (optional) and frac (optional: fraction
+ * of these walkers sent to the simulation) are host doubles. */
+int eor_emu_calibrate(eor_emu* emu, const double* params, const double* d2, int n_walkers, double recall,
+                      double* tau, double* frac, int mem);
+int eor_emu_set_threshold(eor_emu* emu, double tau);
+
+/* Likelihood of walkers (as eor_likelihood, whose arguments these follow) with the
+ * surrogate: emulated walkers get Delta^2 = 10^prediction (NaN in bins without modes) and
+ * chi^2 over them; the others run eor_likelihood on ctx (which must cover the same
+ * redshifts and bins; its max_walkers bounds one simulation batch) and get its results.
+ * fallback (optional) int [n_walkers]. The call reads the number of fallback walkers back
+ * to the host once; n_walkers x n_z <= max_rows. */
+int eor_emu_likelihood(eor_emu* emu, eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2,
+                       const double* sigma, double* chi2, double* d2, int* fallback, int mem);
+
+const char* eor_emu_last_error(const eor_emu* emu);
+void eor_emu_destroy(eor_emu* emu);
+
 /* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
 const char* eor_last_error(const eor_ctx* ctx);
 const char* eor_version(void);

@@ -23,7 +23,13 @@ EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
            "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
-           "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy")
+           "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
+           "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
+           "eor_emu_forward", "eor_emu_loss_grad", "eor_emu_train_batch", "eor_emu_get_weights",
+           "eor_emu_set_weights", "eor_emu_get_normalization", "eor_emu_set_normalization", "eor_emu_predict",
+           "eor_emu_calibrate", "eor_emu_set_threshold", "eor_emu_likelihood", "eor_emu_last_error",
+           "eor_emu_destroy")
+EMU_MAX_HIDDEN, EMU_MAX_MEMBERS = 8, 8
 KERNEL_CLASSES = 8
 EOR_METHOD_BASIS, EOR_METHOD_DIRECT, EOR_METHOD_BASIS_SIMT = 0, 1, 2
 
@@ -41,6 +47,14 @@ class EorConfig(ctypes.Structure):
                 ("k_hi", ctypes.c_double), ("chi2_k_lo", ctypes.c_double), ("chi2_k_hi", ctypes.c_double),
                 ("max_walkers", ctypes.c_int), ("r_mfp_max", ctypes.c_double),
                 ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p)]
+
+
+class EmuConfig(ctypes.Structure):
+    _fields_ = [("n_z", ctypes.c_int), ("z", ctypes.c_double * MAX_Z), ("n_bins", ctypes.c_int),
+                ("hidden", ctypes.c_int), ("n_hidden", ctypes.c_int), ("members", ctypes.c_int),
+                ("max_rows", ctypes.c_int), ("max_samples", ctypes.c_int),
+                ("prior_lo", ctypes.c_double * 3), ("prior_hi", ctypes.c_double * 3),
+                ("d2_floor", ctypes.c_double), ("err_tol", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
 
 
 class EorError(RuntimeError):
@@ -93,6 +107,24 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_last_error": (ctypes.c_char_p, [P]),
         "eor_version": (ctypes.c_char_p, []),
         "eor_destroy": (None, [P]),
+        "eor_emu_default_config": (None, [ctypes.POINTER(EmuConfig)]),
+        "eor_emu_create": (I, [ctypes.POINTER(EmuConfig), P, ctypes.POINTER(P)]),
+        "eor_emu_n_params": (ctypes.c_longlong, [P]),
+        "eor_emu_set_data": (I, [P, P, P, I, I]),
+        "eor_emu_train": (I, [P, I, I, D, ctypes.c_ulonglong, P]),
+        "eor_emu_forward": (I, [P, P, I, P, I]),
+        "eor_emu_loss_grad": (I, [P, P, P, I, P, P, I]),
+        "eor_emu_train_batch": (I, [P, P, P, I, I, D, P, I]),
+        "eor_emu_get_weights": (I, [P, P, I]),
+        "eor_emu_set_weights": (I, [P, P, I]),
+        "eor_emu_get_normalization": (I, [P, P]),
+        "eor_emu_set_normalization": (I, [P, P]),
+        "eor_emu_predict": (I, [P, P, I, P, P, P, I]),
+        "eor_emu_calibrate": (I, [P, P, P, I, D, P, P, I]),
+        "eor_emu_set_threshold": (I, [P, D]),
+        "eor_emu_likelihood": (I, [P, P, P, I, P, P, P, P, P, I]),
+        "eor_emu_last_error": (ctypes.c_char_p, [P]),
+        "eor_emu_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -320,6 +352,183 @@ class Context:
     basis_info = eor_basis_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count
+
+
+def emu_default_config(**overrides) -> EmuConfig:
+    cfg = EmuConfig()
+    load_library().eor_emu_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "z":
+            cfg.n_z = len(v)
+            for j, zv in enumerate(v):
+                cfg.z[j] = float(zv)
+        elif k in ("prior_lo", "prior_hi"):
+            for c in range(3):
+                getattr(cfg, k)[c] = float(v[c])
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Emulator:
+    """The power-spectrum surrogate (eor_emu_create ... eor_emu_destroy): numpy arrays are
+    host buffers, CUDA torch tensors device buffers."""
+
+    def __init__(self, cfg: EmuConfig | None = None, stream=None, **overrides):
+        self.lib = load_library()
+        self.cfg = cfg if cfg is not None else emu_default_config(**overrides)
+        handle = ctypes.c_void_p()
+        rc = self.lib.eor_emu_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream) if stream else None,
+                                     ctypes.byref(handle))
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_emu_last_error(None).decode())
+        self.handle = handle
+        self.members, self.n_z, self.n_bins = self.cfg.members, self.cfg.n_z, self.cfg.n_bins
+        self.n_params = int(self.lib.eor_emu_n_params(handle))
+
+    def _check(self, rc: int):
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_emu_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eor_emu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def eor_emu_set_data(self, params, d2):
+        pp, mem, kp = _arg(params, np.float64)
+        pd, mem2, _ = _arg(d2, np.float64)
+        if mem != mem2:
+            raise ValueError("params and d2 must both be host or both device")
+        self._check(self.lib.eor_emu_set_data(self.handle, pp, pd, int(kp.shape[0]), mem))
+
+    def eor_emu_train(self, steps: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
+        loss = np.zeros(self.members)
+        self._check(self.lib.eor_emu_train(self.handle, int(steps), int(batch), float(lr), int(seed),
+                                           loss.ctypes.data_as(ctypes.c_void_p)))
+        return loss
+
+    def eor_emu_forward(self, x) -> np.ndarray:
+        px, mem, kx = _arg(x, np.float32)
+        n = int(kx.shape[0])
+        y = np.empty((self.members, n, self.n_bins), dtype=np.float32)
+        if mem == EOR_DEVICE:
+            raise ValueError("host arrays only")
+        self._check(self.lib.eor_emu_forward(self.handle, px, n, y.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return y
+
+    def eor_emu_loss_grad(self, x, t):
+        px, _, kx = _arg(x, np.float32)
+        pt, _, _ = _arg(t, np.float32)
+        loss = np.zeros(self.members)
+        grad = np.empty((self.members, self.n_params), dtype=np.float32)
+        self._check(self.lib.eor_emu_loss_grad(self.handle, px, pt, int(kx.shape[0]),
+                                               loss.ctypes.data_as(ctypes.c_void_p),
+                                               grad.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return loss, grad
+
+    def eor_emu_train_batch(self, x, t, steps: int, lr: float) -> np.ndarray:
+        px, _, kx = _arg(x, np.float32)
+        pt, _, _ = _arg(t, np.float32)
+        loss = np.zeros(self.members)
+        self._check(self.lib.eor_emu_train_batch(self.handle, px, pt, int(kx.shape[0]), int(steps), float(lr),
+                                                 loss.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return loss
+
+    def eor_emu_get_weights(self) -> np.ndarray:
+        w = np.empty((self.members, self.n_params), dtype=np.float32)
+        self._check(self.lib.eor_emu_get_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return w
+
+    def eor_emu_set_weights(self, w):
+        pw, mem, _ = _arg(w, np.float32)
+        self._check(self.lib.eor_emu_set_weights(self.handle, pw, mem))
+
+    def eor_emu_get_normalization(self) -> np.ndarray:
+        out = np.empty((2, self.n_bins))
+        self._check(self.lib.eor_emu_get_normalization(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def eor_emu_set_normalization(self, mean_std):
+        a = np.ascontiguousarray(mean_std, dtype=np.float64)
+        self._check(self.lib.eor_emu_set_normalization(self.handle, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def eor_emu_predict(self, params):
+        """(log10 Delta^2 [n][n_z][n_bins], spread [n][n_z], fallback [n])."""
+        pp, mem, kp = _arg(params, np.float64)
+        n = int(kp.shape[0])
+        dev = mem == EOR_DEVICE
+        if dev:
+            import torch
+            pred = torch.empty((n, self.n_z, self.n_bins), dtype=torch.float64, device="cuda")
+            spread = torch.empty((n, self.n_z), dtype=torch.float64, device="cuda")
+            fb = torch.empty((n,), dtype=torch.int32, device="cuda")
+        else:
+            pred = np.empty((n, self.n_z, self.n_bins))
+            spread = np.empty((n, self.n_z))
+            fb = np.empty((n,), dtype=np.int32)
+        self._check(self.lib.eor_emu_predict(self.handle, pp, n, _arg(pred, np.float64)[0],
+                                             _arg(spread, np.float64)[0], _arg(fb, np.int32)[0], mem))
+        return pred, spread, fb
+
+    def eor_emu_calibrate(self, params, d2, recall: float = 0.99):
+        """(tau, fraction of these walkers sent to the simulation)."""
+        pp, mem, kp = _arg(params, np.float64)
+        pd, _, _ = _arg(d2, np.float64)
+        tau, frac = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.eor_emu_calibrate(self.handle, pp, pd, int(kp.shape[0]), float(recall),
+                                               ctypes.byref(tau), ctypes.byref(frac), mem))
+        return tau.value, frac.value
+
+    def eor_emu_set_threshold(self, tau: float):
+        self._check(self.lib.eor_emu_set_threshold(self.handle, float(tau)))
+
+    def eor_emu_likelihood(self, ctx: "Context", params, mock_d2, sigma, want_d2: bool = False):
+        """(chi2 [n], d2 [n][n_z][n_bins] or None, fallback [n])."""
+        pp, mem, kp = _arg(params, np.float64)
+        pm, _, km = _arg(mock_d2, np.float64)
+        ps, _, ks = _arg(sigma, np.float64)
+        n = int(kp.shape[0])
+        dev = mem == EOR_DEVICE
+        if dev:
+            import torch
+            chi2 = torch.empty((n,), dtype=torch.float64, device="cuda")
+            d2 = torch.empty((n, self.n_z, self.n_bins), dtype=torch.float64, device="cuda") if want_d2 else None
+            fb = torch.empty((n,), dtype=torch.int32, device="cuda")
+        else:
+            chi2 = np.empty((n,))
+            d2 = np.empty((n, self.n_z, self.n_bins)) if want_d2 else None
+            fb = np.empty((n,), dtype=np.int32)
+        self._check(self.lib.eor_emu_likelihood(self.handle, ctx.handle, pp, n, pm, ps, _arg(chi2, np.float64)[0],
+                                                None if d2 is None else _arg(d2, np.float64)[0],
+                                                _arg(fb, np.int32)[0], mem))
+        return chi2, d2, fb
+
+    set_data = eor_emu_set_data
+    train = eor_emu_train
+    forward = eor_emu_forward
+    loss_grad = eor_emu_loss_grad
+    train_batch = eor_emu_train_batch
+    get_weights = eor_emu_get_weights
+    set_weights = eor_emu_set_weights
+    get_normalization = eor_emu_get_normalization
+    set_normalization = eor_emu_set_normalization
+    predict = eor_emu_predict
+    calibrate = eor_emu_calibrate
+    set_threshold = eor_emu_set_threshold
+    likelihood = eor_emu_likelihood
 
 
 def box_power_spectrum_noalloc(n: int, box_mpc: float, box, d2, nmodes=None, n_bins: int = 14, k_lo: float = 0.1,
