@@ -156,10 +156,21 @@ int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* k
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
 
+/* Autotuner of the launch schedule (results do not depend on it): times eor_likelihood on
+ * these walkers (arguments as there, n_walkers <= max_walkers) with CUDA events on the
+ * context's stream, `reps` graph replays per candidate after one warm-up, over the
+ * candidates of the current method -- pairs in {4, 8, 16, 32} x plane_threads in {512, 1024}
+ * (128^3 grids; 512 otherwise), and for EOR_METHOD_DIRECT also group in {4, 8, 16} -- and
+ * keeps the fastest (eor_set_tuning). group, pairs, plane_threads and ms (mean milliseconds
+ * of one call) receive the choice; each optional. Tracing is off while it runs and is
+ * restored afterwards. */
+int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2, const double* sigma,
+                 int reps, int* group, int* pairs, int* plane_threads, double* ms, int mem);
+
 /* How the radius loop is evaluated (results agree to FP32 rounding; see the parity tests):
  * EOR_METHOD_BASIS (default): every walker's filtered fields are assembled from a small
  *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
- *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-9 on the grid's |k| for every R in
+ *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-6 on the grid's |k| for every R in
  *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
  *   that contraction, which runs on the tensor cores (tcgen05, TF32 split into hi + lo
  *   parts, three products per step, FP32 accumulation) when the basis has at most 32

@@ -301,7 +301,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->max_radii * c->kb) &&
          alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts) &&
          alloc_n(c, &c->d_ncols, 1);
-    if (ok && eor::basis_tc_fits(c->kb))
+    if (ok && eor::basis_tc_fits(c->basis_rank))
         ok = alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, Z)) &&
              alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
              alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
@@ -554,6 +554,88 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
         c->graph_exec = nullptr;
         c->graph_walkers = -1;
     }
+    return EOR_OK;
+}
+
+int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* mock_d2, const double* sigma,
+                 int reps, int* group, int* pairs, int* plane_threads, double* ms, int mem) {
+    if (!c) return EOR_EINVAL;
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (reps < 1 || reps > 1000) return fail(c, EOR_EINVAL, "reps outside 1..1000");
+    struct Cand { int group, pairs, threads; };
+    std::vector<Cand> cands;
+    const int groups_direct[] = {4, 8, 16};
+    const int pairs_list[] = {4, 8, 16, 32};
+    const bool direct = c->tune.method == eor::kMethodDirect;
+    for (int th : {512, 1024}) {
+        if (th == 1024 && c->n != 128) continue;
+        for (int p : pairs_list) {
+            if (direct)
+                for (int gsz : groups_direct) cands.push_back({gsz, p, th});
+            else
+                cands.push_back({c->tune.group, p, th});
+        }
+    }
+    const bool traced = c->trace_on;
+    c->trace_on = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        c->trace_on = traced;
+        return fail(c, EOR_ECUDA, "autotune events");
+    }
+    const Cand start{c->tune.group, c->tune.pairs, c->tune.plane_threads};
+    Cand best = start;
+    double best_ms = INFINITY;
+    std::vector<double> chi2_host;
+    double* chi2 = nullptr;   // chi^2 of the warm-up calls, where the caller's buffers live
+    if (mem == EOR_DEVICE) {
+        if (n_walkers >= 1 && !alloc_n(c, &chi2, (size_t)n_walkers)) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            c->trace_on = traced;
+            return fail(c, EOR_ENOMEM, "autotune buffer");
+        }
+    } else {
+        chi2_host.resize(n_walkers >= 1 ? (size_t)n_walkers : 1);
+        chi2 = chi2_host.data();
+    }
+    int r = EOR_OK;
+    for (const Cand& k : cands) {
+        if ((r = eor_set_tuning(c, k.group, k.pairs, k.threads)) != EOR_OK) break;
+        // warm-up: captures this schedule's graph and checks the arguments
+        if ((r = eor_likelihood(c, params, n_walkers, mock_d2, sigma, chi2, nullptr, mem)) != EOR_OK) break;
+        cudaEventRecord(e0, c->stream);
+        for (int i = 0; i < reps && r == EOR_OK; i++) {
+            cudaError_t e = cudaGraphLaunch(c->graph_exec, c->stream);
+            if (e != cudaSuccess) r = cuda_fail(c, e, "autotune replay");
+        }
+        cudaEventRecord(e1, c->stream);
+        if (r != EOR_OK) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { r = cuda_fail(c, e, "autotune timing"); break; }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        const double per = (double)t / reps;
+        if (per < best_ms) {
+            best_ms = per;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (mem == EOR_DEVICE) dev_free(c, chi2);
+    c->trace_on = traced;
+    if (r != EOR_OK) {
+        const std::string msg = c->err;
+        eor_set_tuning(c, start.group, start.pairs, start.threads);
+        return fail(c, r, "autotune: " + msg);
+    }
+    if ((r = eor_set_tuning(c, best.group, best.pairs, best.threads)) != EOR_OK) return r;
+    if (group) *group = best.group;
+    if (pairs) *pairs = best.pairs;
+    if (plane_threads) *plane_threads = best.threads;
+    if (ms) *ms = best_ms;
     return EOR_OK;
 }
 

@@ -18,7 +18,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kRhoCritH2 = 2.775e11;    // 3 H0^2 / (8 pi G) in h^2 Msun / Mpc^3
 constexpr int kBasisCand = 512;            // candidate radii of the filter basis
 constexpr int kBasisMax = 48;              // largest filter basis
-constexpr double kBasisTol = 1e-9;         // max |W - projection| over candidates and |k|
+constexpr double kBasisTol = 1e-6;         // max |W - projection| over candidates and |k| (FP32 level)
 constexpr int kCoefGrid = 8192;            // uniform R grid of the basis coefficient table
 
 // Device error word bits (set by kernels, read by the host).
@@ -181,7 +181,7 @@ int basis_cells_per_cta();
 
 // tcgen05.cu
 size_t basis_tc_smem();
-bool basis_tc_fits(int kb);
+bool basis_tc_fits(int rank);
 size_t basis_tc_a_bytes(long long n3, int n_z);
 size_t basis_tc_b_bytes(const eor_ctx* c);
 size_t basis_tc_column_slots(const eor_ctx* c);

@@ -110,16 +110,16 @@ static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0, "bulk copies move mult
 static_assert(kTcEpi == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
 static_assert(kTcN == 128 && kGroup == 32, "k_format_b: one block per chunk, one warp per group; 4 epilogue groups");
 
-// Basis fields -> the CTAs' A operands: [z][cta][hi/lo][tile][128 x 32 core-matrix layout],
-// K index kb holding the constant 1 (kb + 1 <= 32).
-__global__ void k_format_a(const float* F, int kb, long long n3, int n_z, unsigned char* out) {
+// Basis fields -> the CTAs' A operands: [z][cta][hi/lo][tile][128 x 32 core-matrix layout]:
+// the rank basis values, then at K index rank the constant 1 that carries the folded
+// threshold, then zeros (rank + 1 <= 32). F is [z][kb][n3] (kb >= rank).
+__global__ void k_format_a(const float* F, int kb, int rank, long long n3, int n_z, unsigned char* out) {
     const long long total = (long long)n_z * tc::kKMax * n3;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const long long cell = e % n3;
         const int b = (int)((e / n3) % tc::kKMax), zi = (int)(e / (n3 * tc::kKMax));
-        // basis values, then the constant 1 that carries the folded threshold, then zeros
-        const float v = b < kb ? F[((size_t)zi * kb + b) * n3 + cell] : (b == kb ? 1.0f : 0.0f);
+        const float v = b < rank ? F[((size_t)zi * kb + b) * n3 + cell] : (b == rank ? 1.0f : 0.0f);
         const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
         const long long cta = cell / kTcCells;
         const int c = (int)(cell % kTcCells);
@@ -132,13 +132,14 @@ __global__ void k_format_a(const float* F, int kb, long long n3, int n_z, unsign
 
 // Walker coefficients -> chunks of kTcN columns: [z][chunk][B hi | B lo | meta], one block
 // per chunk and one warp per group of kGroup columns. Column (walker w, radius j) holds
-// c_b(R_j) for b < kb and, at K index kb, minus its threshold, so that the contraction
+// c_b(R_j) for b < rank and, at K index rank, minus its threshold, so that the contraction
 // yields D = delta_R - threshold: delta_crit(R_j) (Eq. 1 flag test D >= 0) above R_cell,
 // delta_c at R_cell (where f_coll needs delta_c - delta_R). An infinite delta_crit (no
 // ionization possible) becomes kNever. Padding columns carry zero coefficients and
 // -kNever, so that D = -kNever there.
 __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* gmeta, const int* ncols,
-                                                   const float* coef, const PairInfo* pairs, int kb, int max_radii,
+                                                   const float* coef, const PairInfo* pairs, int kb, int rank,
+                                                   int max_radii,
                                                    int n_z, int chunks_per_z, float delta_c, unsigned char* out) {
     const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kTcN + row;
     const int nc = *ncols;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* g
         thr = j == pi.n_r - 1 ? delta_c : (isfinite(dcrit) ? dcrit : kNever);
     }
     for (int b = 0; b < tc::kKMax; b++) {
-        const float v = b < kb ? (src ? src[b] : 0.0f) : (b == kb ? -thr : 0.0f);
+        const float v = b < rank ? (src ? src[b] : 0.0f) : (b == rank ? -thr : 0.0f);
         const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
         *reinterpret_cast<uint32_t*>(chunk + tc::core_offset(row, b)) = hi;
         *reinterpret_cast<uint32_t*>(chunk + kBBytes / 2 + tc::core_offset(row, b)) = lo;
@@ -212,6 +213,7 @@ struct TcArgs {
     unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
     int* err;
     int n_z, chunks_per_z;
+    int ksteps;                 // MMA K steps of 8: (rank + 1) / 8 rounded up
     long long n3;
 };
 
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
             if (!ok) break;
             tc::fence_after_sync();
             // the tiles' accumulators alternate, so that consecutive MMAs are independent
-            for (int ks = 0; ks < tc::kKMax / 8; ks++) {
+            for (int ks = 0; ks < a.ksteps; ks++) {
                 const uint32_t ko = (uint32_t)ks * 2 * tc::kLBO;
                 const uint64_t bh = tc::smem_desc(tc::smem_addr(Bs + st * kBBytes) + ko, tc::kLBO, tc::kSBO);
                 const uint64_t bl = tc::smem_desc(tc::smem_addr(Bs + st * kBBytes + kBBytes / 2) + ko, tc::kLBO, tc::kSBO);
@@ -481,7 +483,7 @@ int tc_slots(const eor_ctx* c) {
 
 }  // namespace
 
-bool basis_tc_fits(int kb) { return kb + 1 <= tc::kKMax; }   // basis values plus the constant column
+bool basis_tc_fits(int rank) { return rank + 1 <= tc::kKMax; }   // basis values plus the constant column
 
 size_t basis_tc_smem() {
     return kABytes + kTcStages * (kBBytes + kMBytes) + (4 * kTcStages + 6) * sizeof(uint64_t) + 16;
@@ -497,7 +499,7 @@ cudaError_t prepare_basis_tc(eor_ctx* c) {
 
 cudaError_t format_basis_tc(eor_ctx* c) {
     trace_begin(c, kKOther);
-    k_format_a<<<2048, 256, 0, c->stream>>>(c->d_F, c->kb, (long long)c->n3, c->cfg.n_z, c->d_tcA);
+    k_format_a<<<2048, 256, 0, c->stream>>>(c->d_F, c->kb, c->basis_rank, (long long)c->n3, c->cfg.n_z, c->d_tcA);
     trace_end(c);
     return cudaGetLastError();
 }
@@ -509,7 +511,8 @@ cudaError_t build_columns(eor_ctx* c, int n_walkers) {
     const int chunks = tc_slots(c) / kTcN;
     trace_begin(c, kKTables);
     k_format_b<<<dim3(chunks, c->cfg.n_z), kTcN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
-                                                               c->d_pairs, c->kb, c->max_radii, c->cfg.n_z, chunks,
+                                                               c->d_pairs, c->kb, c->basis_rank, c->max_radii, c->cfg.n_z,
+                                                               chunks,
                                                                (float)c->cfg.delta_c, c->d_tcB);
     trace_end(c);
     return cudaGetLastError();
@@ -520,7 +523,7 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     cudaError_t e = cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * pairs, c->stream);
     if (e != cudaSuccess) return e;
     TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, c->d_delta, c->d_dtb, xhi_out, c->d_xq, c->d_err,
-             c->cfg.n_z, tc_slots(c) / kTcN, (long long)c->n3};
+             c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3};
     trace_begin(c, kKBasis);
     k_basis_ionize_tc<<<dim3((unsigned)(c->n3 / kTcCells), c->cfg.n_z), kTcThreads, basis_tc_smem(), c->stream>>>(a);
     trace_end(c);

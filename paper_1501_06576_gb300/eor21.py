@@ -21,7 +21,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 # names exported by include/eor21.h
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_method", "eor_basis_info", "eor_trace",
+           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
            "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
@@ -97,6 +97,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
         "eor_set_tuning": (I, [P, I, I, I]),
         "eor_set_method": (I, [P, I]),
+        "eor_autotune": (I, [P, P, I, P, P, I, P, P, P, P, I]),
         "eor_basis_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "eor_trace": (I, [P, I]),
         "eor_trace_read": (I, [P, P, P, I]),
@@ -311,6 +312,17 @@ class Context:
     def eor_set_tuning(self, group: int, pairs: int, plane_threads: int = 512):
         self._check(self.lib.eor_set_tuning(self.handle, int(group), int(pairs), int(plane_threads)))
 
+    def eor_autotune(self, params, mock_d2, sigma, reps: int = 3):
+        """Pick the fastest launch schedule for these walkers; returns (group, pairs,
+        plane_threads, ms per call)."""
+        pp, mem, kp = _arg(params, np.float64)
+        pm, _, km = _arg(mock_d2, np.float64)
+        ps, _, ks = _arg(sigma, np.float64)
+        g, p, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.eor_autotune(self.handle, pp, int(kp.shape[0]), pm, ps, int(reps), ctypes.byref(g),
+                                          ctypes.byref(p), ctypes.byref(t), ctypes.byref(ms), mem))
+        return g.value, p.value, t.value, ms.value
+
     def eor_set_method(self, method: int):
         self._check(self.lib.eor_set_method(self.handle, int(method)))
 
@@ -349,6 +361,7 @@ class Context:
     trace = eor_trace
     set_tuning = eor_set_tuning
     set_method = eor_set_method
+    autotune = eor_autotune
     basis_info = eor_basis_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count

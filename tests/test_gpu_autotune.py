@@ -1,0 +1,54 @@
+"""GPU test of the launch-schedule autotuner (eor_autotune): it picks one of its candidates,
+leaves the context usable, and the likelihood does not depend on the schedule."""
+import numpy as np
+import pytest
+
+from paper_1501_06576_gb300 import eor21, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT])
+def test_autotune_picks_a_candidate_and_keeps_results(method):
+    n, box, zs = 64, 100.0, (9.0, 10.0)
+    ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=8)
+    ctx.set_method(method)
+    ctx.init_boxes(synth.density_boxes(n, box, zs, seed=8))
+    params = synth.walker_params(8, seed=9)
+    mock = np.full((2, 14), 20.0)
+    sigma = 0.2 * mock
+    before, d2_before = ctx.likelihood(params, mock, sigma, want_d2=True)
+    g, p, t, ms = ctx.autotune(params, mock, sigma, reps=2)
+    assert p in (4, 8, 16, 32) and t == 512 and ms > 0
+    assert g in ((4, 8, 16) if method == eor21.EOR_METHOD_DIRECT else (8,))
+    after, d2_after = ctx.likelihood(params, mock, sigma, want_d2=True)
+    assert np.allclose(after, before, rtol=1e-9, atol=0)
+    assert np.allclose(d2_after, d2_before, rtol=1e-9, atol=0, equal_nan=True)
+    ctx.close()
+
+
+def test_autotune_device_buffers_and_errors():
+    torch = pytest.importorskip("torch")
+    ctx = eor21.Context(n=32, box_mpc=60.0, z=(9.0,), max_walkers=4)
+    with pytest.raises(eor21.EorError) as ei:
+        ctx.autotune(synth.walker_params(4, seed=1), np.ones((1, 14)), np.ones((1, 14)))
+    assert ei.value.code == eor21.EOR_ESTATE
+    ctx.init_boxes(synth.density_boxes(32, 60.0, (9.0,), seed=3))
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g, p, t, ms = ctx.autotune(d(synth.walker_params(4, seed=1)), d(np.full((1, 14), 5.0)), d(np.ones((1, 14))))
+    assert p in (4, 8, 16, 32)
+    with pytest.raises(eor21.EorError) as ei:
+        ctx.autotune(synth.walker_params(5, seed=1), np.ones((1, 14)), np.ones((1, 14)))   # > max_walkers
+    assert ei.value.code == eor21.EOR_EINVAL
+    # the context still works with the restored schedule
+    chi = ctx.likelihood(synth.walker_params(4, seed=1), np.full((1, 14), 5.0), np.ones((1, 14)))
+    assert np.all(np.isfinite(chi))
+    ctx.close()

@@ -256,9 +256,9 @@ def test_emulator_likelihood_routes_walkers():
     _, _, cnt = oracle.power_spectrum(box, 60.0, 8, 0.15, 1.5)
     for i in np.nonzero(emulated)[0]:
         d2_ref = 10.0 ** rp[i, 0]
-        want = oracle.chi2(d2_ref, cnt, mock, sigma, k_lo=0.15, k_hi=1.5)
-        r = (d2_ref - mock) / sigma
-        dr = d2_ref * (10.0 ** 1e-4 - 1.0) / sigma
+        want = oracle.chi2(d2_ref, cnt, mock[0], sigma[0], k_lo=0.15, k_hi=1.5)
+        r = (d2_ref - mock[0]) / sigma[0]
+        dr = d2_ref * (10.0 ** 1e-4 - 1.0) / sigma[0]
         used = (cnt > 0) & (np.sqrt(np.geomspace(0.15, 1.5, 9)[:-1] * np.geomspace(0.15, 1.5, 9)[1:]) <= 1.0)
         tol = np.sum(((2 * np.abs(r) + dr) * dr)[used]) + 1e-12
         assert abs(chi[i] - want) <= tol, (chi[i], want, tol)
