@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
-    ap.add_argument("--emu-steps", type=int, default=6000, help="Adam steps of the surrogate")
+    ap.add_argument("--emu-steps", type=int, default=16000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
     return ap.parse_args()
 
@@ -312,7 +312,7 @@ def time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args
     # accuracy on the timed walkers, against their simulated spectra
     pred, _, fb = emu.predict(test_p)
     truth = test_d2.cpu().numpy()
-    ok = np.isfinite(truth) & (truth > 1e-4)
+    ok = np.isfinite(truth) & (truth > emu.cfg.d2_floor)
     err = np.where(ok, np.abs(10.0 ** pred / np.where(ok, truth, 1.0) - 1.0), 0.0).max(axis=(1, 2))
     acc = fb == 0
     # device time of the prediction alone (features, 4 layers x 4 members, combination)

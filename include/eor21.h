@@ -267,7 +267,7 @@ typedef struct {
     int max_rows;                /* largest minibatch, and largest walkers x n_z of one prediction (16384) */
     int max_samples;             /* largest training set in samples = walkers x n_z (65536) */
     double prior_lo[3], prior_hi[3];   /* box of (zeta, R_mfp, log10 T_vir): (5, 5, 4) .. (100, 20, 6) */
-    double d2_floor;             /* Delta^2 floor before log10 [mK^2] (1e-4) */
+    double d2_floor;             /* Delta^2 floor before log10 [mK^2] (1e-2) */
     double err_tol;              /* per-bin relative error the fallback guards (0.05) */
     unsigned long long seed;     /* weight initialisation */
 } eor_emu_config;

@@ -81,8 +81,9 @@ __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(_
 
 template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads) k_emu_gemm(GemmArgs g) {
-    __shared__ float As[kGemmK][kGemmTile + 1];   // [k][m]
-    __shared__ float Bs[kGemmK][kGemmTile + 1];   // [k][n]
+    // rows padded to 68 floats: 16-byte aligned for the float4 reads below
+    __shared__ __align__(16) float As[kGemmK][kGemmTile + 4];   // [k][m]
+    __shared__ __align__(16) float Bs[kGemmK][kGemmTile + 4];   // [k][n]
     const int e = blockIdx.z, m0 = blockIdx.y * kGemmTile, n0 = blockIdx.x * kGemmTile;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const float* A = g.A + e * g.ae;
@@ -113,11 +114,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_emu_gemm(GemmArgs g) {
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kGemmK; kk++) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx * 4 + j];
+            const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -768,7 +767,7 @@ void eor_emu_default_config(eor_emu_config* cfg) {
     cfg->prior_hi[0] = 100.0;
     cfg->prior_hi[1] = 20.0;
     cfg->prior_hi[2] = 6.0;
-    cfg->d2_floor = 1e-4;
+    cfg->d2_floor = 1e-2;
     cfg->err_tol = 0.05;
     cfg->seed = 1;
 }

@@ -132,7 +132,7 @@ def test_training_is_deterministic_and_learns():
         last = emu.train(600, 256, 2e-3, seed=5)
         out.append((first, last, emu.get_weights()))
         norm = emu.get_normalization()
-        ref_t = em.targets(d2, 1e-4).reshape(-1, 14)
+        ref_t = em.targets(d2, emu.cfg.d2_floor).reshape(-1, 14)
         assert np.allclose(norm[0], ref_t.mean(axis=0), rtol=1e-12, atol=1e-12)
         assert np.allclose(norm[1], ref_t.std(axis=0), rtol=1e-10)
         emu.close()
@@ -144,7 +144,7 @@ def _pred_setup(members=3):
     emu = make_emu(members=members, max_rows=2048)
     w = seeded_weights(emu, seed=51)
     emu.set_weights(w)
-    norm = np.stack([synth.normals(9, 1, 14) + 1.0, 0.2 + synth.uniform01(9, 2, 14)])
+    norm = np.stack([synth.normals(9, 1, 14) + 2.0, 0.2 + synth.uniform01(9, 2, 14)])
     emu.set_normalization(norm)
     return emu, w, norm
 
@@ -225,7 +225,7 @@ def test_emulator_likelihood_routes_walkers():
     emu = make_emu(members=2, hidden=64, n_hidden=2, n_bins=8, zs=zs, max_rows=512)
     w = seeded_weights(emu, seed=61)
     emu.set_weights(w)
-    norm = np.stack([np.full(8, 1.5), np.full(8, 0.3)])
+    norm = np.stack([np.full(8, 2.0), np.full(8, 0.3)])
     emu.set_normalization(norm)
     params = synth.walker_params(150, seed=14)
     _, mock = ctx.likelihood(np.array([[30.0, 12.0, 4.7]]), np.ones((1, 8)), np.ones((1, 8)), want_d2=True)
@@ -325,12 +325,12 @@ def test_trained_surrogate_gain_over_simulation():
 
     emu = eor21.Emulator(z=zs, members=4, max_rows=2048, max_samples=8192, seed=3)
     emu.set_data(train_p, train_d2)
-    loss = emu.train(4000, 512, 2e-3, seed=11)
+    loss = emu.train(16000, 512, 2e-3, seed=11)
     tau, val_frac = emu.calibrate(val_p, val_d2, recall=0.99)
 
     pred, _, fb = emu.predict(test_p)
-    rel = np.abs(10.0 ** pred / test_d2 - 1.0)
-    has_modes = np.isfinite(test_d2) & (test_d2 > 1e-4)
+    has_modes = np.isfinite(test_d2) & (test_d2 > emu.cfg.d2_floor)
+    rel = np.abs(10.0 ** pred / np.where(has_modes, test_d2, 1.0) - 1.0)
     err = np.where(has_modes, rel, 0.0).max(axis=(1, 2))
     accepted = fb == 0
     miss = float(np.mean(err[accepted] > 0.05)) if accepted.any() else 0.0
@@ -350,7 +350,7 @@ def test_trained_surrogate_gain_over_simulation():
     assert np.array_equal(fb2, fb)
     assert np.array_equal(chi[fb == 1], test_chi[fb == 1])
     # the surrogate spares the simulation for most walkers and is rarely wrong on them
-    assert accepted.mean() >= 0.5
-    assert miss <= 0.03
+    assert accepted.mean() >= 0.6
+    assert miss <= 0.02
     emu.close()
     ctx.close()
