@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--walkers", type=int, default=128)
+    ap.add_argument("--nz", type=int, default=3, choices=[1, 2, 3],
+                    help="redshifts of the workload used (the first of z = 8, 9, 10); fewer only for small profiling cases")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-walkers", type=int, default=16, help="walkers timed one call each (plain path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,7 +354,9 @@ def time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args
 
 
 def main():
+    global ZS
     args = parse()
+    ZS = ZS[:args.nz]
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)

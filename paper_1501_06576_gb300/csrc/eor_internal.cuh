@@ -140,6 +140,7 @@ struct eor_ctx {
     unsigned long long* d_xq = nullptr;   // [pairs] fixed-point x_HI sums of the tensor-core path
     int* d_ncols = nullptr;          // [1] number of columns
     int n_ready_tables = 0;
+    int ps_planes = 0;               // kz planes holding a binned mode: kf kz < k_hi
 
     // state
     int stage = 0;                   // 0 created, 1 boxes, 2 params, 3 ionized, 4 spectra

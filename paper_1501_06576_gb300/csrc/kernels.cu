@@ -668,7 +668,7 @@ cudaError_t ps_from_boxes_n(eor_ctx* c) {
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
+        k_plane_ps<N, T><<<dim3(c->ps_planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
         trace_end(c);
     }
     return cudaGetLastError();
@@ -713,7 +713,7 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(NH, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
+        k_plane_ps<N, T><<<dim3(c->ps_planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
         trace_end(c);
     }
     return cudaGetLastError();

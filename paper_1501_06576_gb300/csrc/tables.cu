@@ -337,6 +337,9 @@ cudaError_t build_cosmology_tables(eor_ctx* c) {
     trace_end(c);
     cudaFreeAsync(d_z, c->stream);
     double kf = 2.0 * kPi / g.box_mpc;
+    // every mode of plane kz has |k| >= kf kz, so planes with kf kz >= k_hi hold no binned mode
+    c->ps_planes = 0;
+    while (c->ps_planes < c->nh && kf * c->ps_planes < g.k_hi) c->ps_planes++;
     trace_begin(c, kKOther);
     k_bin_table<<<(c->n_m2 + 255) / 256, 256, 0, c->stream>>>(c->n_m2, kf, g.k_lo, g.k_hi, g.n_bins,
                                                               c->d_bin_of_m2);

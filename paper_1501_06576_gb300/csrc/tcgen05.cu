@@ -87,22 +87,23 @@ extern "C" int eor_tensor_core_check(const float* a, const float* b, float* d, i
 namespace eor {
 namespace {
 
-constexpr int kTcTiles = 2;                            // M tiles of 128 cells per CTA
+constexpr int kTcTiles = 1;                            // M tiles of 128 cells per CTA (two CTAs per SM)
 constexpr int kTcCells = 128 * kTcTiles;               // cells per CTA
 constexpr int kTcN = 128;                              // (walker, radius) columns per chunk (MMA N)
-constexpr int kTcStages = 3;                           // coefficient chunks in flight
+constexpr int kTcStages = 2;                           // coefficient chunks in flight per CTA
 constexpr int kGroup = 32;                             // epilogue columns per tensor-memory read
 constexpr uint32_t kTileBytes = 128 * tc::kKMax * 4;   // one 128 x 32 TF32 tile (16 KB)
-constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (64 KB)
+constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (32 KB)
 constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chunk (32 KB)
 // chunk meta: one 16-byte record per group of kGroup columns: (walker << 2 | first << 1 |
 // last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0)
 constexpr int kGroupsPerChunk = kTcN / kGroup;
 constexpr uint32_t kMBytes = kGroupsPerChunk * 16;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
-constexpr uint32_t kTmemCols = 512;                       // 2 buffers x kTcTiles x kTcN columns
-constexpr int kTcThreads = 640;                           // warp 0 producer, warps 4-19 epilogue
-constexpr int kTcEpi = 512;                               // epilogue threads: 2 per cell
+constexpr uint32_t kTmemCols = 2 * kTcTiles * kTcN;       // 2 buffers x kTcTiles x kTcN columns (256)
+constexpr int kTcEpi = 2 * 128 * kTcTiles;               // epilogue threads: 2 per cell
+constexpr int kTcThreads = 128 + kTcEpi;                  // warps 0-3: MMA (thread 0), copies (thread 32); then epilogue
+constexpr int kTcCtasPerSm = 2;                          // shared memory and tensor memory allow two
 constexpr float kNever = 1.0e30f;                         // folded threshold that no delta_R reaches
 constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
 static_assert(2 * kTcTiles * kTcN <= (int)kTmemCols, "tensor memory");
@@ -217,24 +218,26 @@ struct TcArgs {
     long long n3;
 };
 
-// One CTA: 256 cells of one redshift (two 128-row tiles) against every (walker, radius)
-// column. The cells' basis values (A) and each 128-column chunk of coefficients (B) arrive by
-// bulk copy in the TF32 hi/lo core-matrix layout; thread 0 issues, per K step, product and
-// tile, hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation) into one of two tensor-memory
-// buffers, so D(cell, column) = sum_b F_b c_b - threshold = delta_R - threshold. Each
-// walker's columns start on a group of 32: its R_cell column first (D = delta_R - delta_c),
-// then its radii from R_mfp down, then padding. Warps 4-11 run the epilogue of the other
-// buffer meanwhile, two threads per cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag
-// of a walker, "D >= 0 (sign bit clear) at some radius above R_cell", is an AND of sign bits
-// over its columns; at its last group the thread forms x_HI and delta T_b (coalesced stores)
-// and the warp adds its exact fixed-point x_HI sum to the pair's total.
+// One CTA: 128 cells of one redshift (one M = 128 tile) against every (walker, radius)
+// column; two CTAs share an SM (97 KB of shared memory and 256 tensor-memory columns each),
+// so that one CTA's operand waits, pipeline fill and drain overlap the other's work. The
+// cells' basis values (A) and each 128-column chunk of coefficients (B) arrive by bulk copy
+// in the TF32 hi/lo core-matrix layout; thread 0 issues, per K step, hi*hi + hi*lo + lo*hi
+// (3xTF32, FP32 accumulation) into one of two tensor-memory buffers, so D(cell, column) =
+// sum_b F_b c_b - threshold = delta_R - threshold. Each walker's columns start on a group
+// of 32: its R_cell column first (D = delta_R - delta_c), then its radii from R_mfp down,
+// then padding. Warps 4-11 run the epilogue of the other buffer meanwhile, two threads per
+// cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag of a walker, "D >= 0 (sign bit
+// clear) at some radius above R_cell", is an AND of sign bits over its columns; at its last
+// group the thread forms x_HI and delta T_b (coalesced stores) and the warp adds its exact
+// fixed-point x_HI sum to the pair's total.
 // Roles: thread 32 issues the bulk copies, thread 0 the MMAs (it waits only for operands and
-// a free accumulator buffer, so the tensor pipe stays fed), warps 4-19 the epilogue.
-// Hand-offs: chunk c + 3 reuses chunk c's stage after MMA(c) (coefficients) and the
+// a free accumulator buffer, so the tensor pipe stays fed), warps 4-11 the epilogue.
+// Hand-offs: chunk c + 2 reuses chunk c's stage after MMA(c) (coefficients) and the
 // epilogue's read of chunk c's meta; MMA(c) reuses the tensor memory of chunk c - 2 after
 // its epilogue. Every wait is bounded; on a timeout the CTA sets kErrTimeout, waits for its
 // copies and MMAs in flight and frees its tensor memory.
-__global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* As = sm;                                // A hi tiles then lo tiles
     unsigned char* Bs = As + kABytes;                      // [kTcStages][kBBytes]
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_basis_ionize_tc(TcArgs a) {
         // (the quarter its warp index allows) of tile (e / 4) % 2, and groups 2 (e / 8) and
         // 2 (e / 8) + 1 of every chunk: one cell, half the columns. A walker never spans
         // the two halves (multi-group walkers start on an even group).
-        const int e = warp - 4, lq = warp & 3, q = (e >> 2) & 1, g0 = 2 * (e >> 3);
+        const int e = warp - 4, lq = warp & 3, q = (e >> 2) % kTcTiles, g0 = 2 * ((e >> 2) / kTcTiles);
         const long long cell = cell0 + q * 128 + lq * 32 + lane;
         const float dens = __ldg(a.delta + (size_t)zi * a.n3 + cell);
         for (int c = 0; c < nch; c++) {
@@ -494,7 +497,12 @@ size_t basis_tc_column_slots(const eor_ctx* c) { return (size_t)tc_slots(c); }
 
 cudaError_t prepare_basis_tc(eor_ctx* c) {
     (void)c;
-    return cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)basis_tc_smem());
+    cudaError_t e =
+        cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)basis_tc_smem());
+    if (e != cudaSuccess) return e;
+    // the largest shared-memory carve-out, so that kTcCtasPerSm CTAs fit on an SM
+    return cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t format_basis_tc(eor_ctx* c) {
