@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
+    ap.add_argument("--mcmc-steps", type=int, default=10)
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
     ap.add_argument("--emu-steps", type=int, default=16000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
@@ -353,6 +355,32 @@ def time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args
                     "likelihood calls of walkers_per_call walkers, device-resident inputs"}
 
 
+def time_mcmc(ctx, eor21, synth, torch, stream, mock, sigma, args):
+    """The device-side stretch-move sampler on the same boxes: an ensemble of twice the
+    context's walkers (each half is one batched likelihood call per step), timed with CUDA
+    events over args.mcmc_steps steps after two warm-up steps."""
+    w = 2 * ctx.cfg.max_walkers
+    smp = eor21.Sampler(ctx, n_walkers=w, seed=17)
+    x0 = synth.walker_params(w, seed=200, zeta=(20.0, 40.0), r_mfp=(10.0, 20.0), log10_tvir=(4.4, 5.0))
+    smp.start(x0, mock, sigma)
+    smp.run(2, want_chain=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    smp.run(args.mcmc_steps, want_chain=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, lnp, acc = smp.run(2)
+    smp.close()
+    return {"value": w * args.mcmc_steps / (ms / 1e3), "unit": "evals/s", "walkers": w,
+            "steps_per_s": args.mcmc_steps / (ms / 1e3), "ms_per_step": ms / args.mcmc_steps,
+            "acceptance_last_steps": float(acc.mean()),
+            "note": "stretch-move ensemble sampler on the device: per step two half-ensemble proposals, each "
+                    "evaluated by one batched likelihood graph replay, Metropolis decisions on the device; no host "
+                    "round trip between steps"}
+
+
 def main():
     global ZS
     args = parse()
@@ -473,6 +501,13 @@ def main():
         torch.cuda.synchronize()
         plain = pw / (p0.elapsed_time(p1) / 1e3)
 
+        # ---------------- the device-side ensemble sampler on the same likelihood
+        mcmc = None
+        if not args.no_mcmc and rank == 0:
+            ctx.trace(False)
+            mcmc = time_mcmc(ctx, eor21, synth, torch, stream, np.ascontiguousarray(mock),
+                             np.ascontiguousarray(sigma), args)
+
         # ---------------- the learned surrogate with simulation fallback (same boxes)
         emulator = None
         if not args.no_emulator and rank == 0:
@@ -552,7 +587,7 @@ def main():
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
                        "contraction": "tcgen05 3xTF32" if uses_tensor_cores else "FP32 FMA"},
             "basis_fp32_units": simt,
-            "direct_method": direct, "emulator": emulator, "cpu_baseline": cpu, "clocks": clk}
+            "direct_method": direct, "emulator": emulator, "mcmc": mcmc, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0
 

@@ -340,6 +340,52 @@ int eor_emu_likelihood(eor_emu* emu, eor_ctx* ctx, const double* params, int n_w
 const char* eor_emu_last_error(const eor_emu* emu);
 void eor_emu_destroy(eor_emu* emu);
 
+/* ------------------------------------------------------------------------------------
+ * Affine-invariant ensemble sampler on the device (Sec. 2.4: Goodman & Weare 2010, as in
+ * emcee / CosmoHammer), with the optional neutral-fraction prior of Sec. 3.3.
+ *
+ * One step updates the two halves of the ensemble in turn: walker k of the active half picks
+ * a partner j of the other half, draws z from g(z) ~ 1/sqrt(z) on [1/a, a], proposes
+ * Y = X_j + z (X_k - X_j) and accepts with probability min(1, z^2 p(Y) / p(X_k)), where
+ * log p = -chi^2 / 2 (eor_likelihood's chi^2 on the context) inside the flat prior box and,
+ * when xhi_prior_z >= 0, only where the mean neutral fraction at redshift index xhi_prior_z
+ * is >= xhi_prior_min; -infinity elsewhere. A half's proposals are evaluated as one batch by
+ * the context's captured likelihood graph; between steps nothing goes to the host.
+ * Random numbers: SplitMix64 keyed by seed; draw c (partner, stretch, accept) of walker k in
+ * half h of step s is output ((2 s + h) n_walkers + k) 3 + c, uniform = top 53 bits / 2^53.
+ * Without a context (ctx NULL) the target is the Gaussian log p = -(y - mean)^T P (y - mean)/2
+ * given in the config (gauss_target = 1): a check of the sampler itself.
+ * -------------------------------------------------------------------------------------- */
+typedef struct eor_mcmc eor_mcmc;   /* opaque, library-owned */
+
+typedef struct {
+    int n_walkers;                       /* even, >= 4; n_walkers / 2 <= the context's max_walkers */
+    double a;                            /* stretch scale > 1 (2) */
+    double prior_lo[3], prior_hi[3];     /* flat prior box of (zeta, R_mfp, log10 T_vir) */
+    int xhi_prior_z;                     /* redshift index of the neutral-fraction prior, -1: none */
+    double xhi_prior_min;                /* its lower limit (0.05, Sec. 3.3) */
+    unsigned long long seed;
+    int gauss_target;                    /* 1: Gaussian test target (ctx NULL) */
+    double gauss_mean[3], gauss_precision[9];
+} eor_mcmc_config;
+
+void eor_mcmc_default_config(eor_mcmc_config* cfg);   /* 128 walkers, a = 2, the workloads' prior box */
+/* ctx: the likelihood (boxes loaded); it must outlive the sampler, which runs on its stream. */
+int eor_mcmc_create(const eor_mcmc_config* cfg, eor_ctx* ctx, eor_mcmc** out);
+/* Starting walkers params double [n_walkers][3], mock and sigma as for eor_likelihood
+ * (ignored without a context); lnp (optional) double [n_walkers] receives their log
+ * posteriors. Resets the step count. */
+int eor_mcmc_start(eor_mcmc* m, const double* params, const double* mock_d2, const double* sigma, double* lnp,
+                   int mem);
+/* `steps` steps; each optional output gets one row per step after both halves moved:
+ * chain double [steps][n_walkers][3], lnp double [steps][n_walkers], accepted int
+ * [steps][n_walkers] (1 where the walker's last proposal was accepted). */
+int eor_mcmc_run(eor_mcmc* m, int steps, double* chain, double* lnp, int* accepted, int mem);
+/* Current walkers (double [n_walkers][3]) and their log posteriors, each optional. */
+int eor_mcmc_walkers(eor_mcmc* m, double* params, double* lnp, int mem);
+const char* eor_mcmc_last_error(const eor_mcmc* m);
+void eor_mcmc_destroy(eor_mcmc* m);
+
 /* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
 const char* eor_last_error(const eor_ctx* ctx);
 const char* eor_version(void);

@@ -28,7 +28,8 @@ EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params
            "eor_emu_forward", "eor_emu_loss_grad", "eor_emu_train_batch", "eor_emu_get_weights",
            "eor_emu_set_weights", "eor_emu_get_normalization", "eor_emu_set_normalization", "eor_emu_predict",
            "eor_emu_calibrate", "eor_emu_set_threshold", "eor_emu_likelihood", "eor_emu_last_error",
-           "eor_emu_destroy")
+           "eor_emu_destroy", "eor_mcmc_default_config", "eor_mcmc_create", "eor_mcmc_start", "eor_mcmc_run",
+           "eor_mcmc_walkers", "eor_mcmc_last_error", "eor_mcmc_destroy")
 EMU_MAX_HIDDEN, EMU_MAX_MEMBERS = 8, 8
 KERNEL_CLASSES = 8
 EOR_METHOD_BASIS, EOR_METHOD_DIRECT, EOR_METHOD_BASIS_SIMT = 0, 1, 2
@@ -55,6 +56,13 @@ class EmuConfig(ctypes.Structure):
                 ("max_rows", ctypes.c_int), ("max_samples", ctypes.c_int),
                 ("prior_lo", ctypes.c_double * 3), ("prior_hi", ctypes.c_double * 3),
                 ("d2_floor", ctypes.c_double), ("err_tol", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+class McmcConfig(ctypes.Structure):
+    _fields_ = [("n_walkers", ctypes.c_int), ("a", ctypes.c_double), ("prior_lo", ctypes.c_double * 3),
+                ("prior_hi", ctypes.c_double * 3), ("xhi_prior_z", ctypes.c_int), ("xhi_prior_min", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("gauss_target", ctypes.c_int), ("gauss_mean", ctypes.c_double * 3),
+                ("gauss_precision", ctypes.c_double * 9)]
 
 
 class EorError(RuntimeError):
@@ -126,6 +134,13 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_emu_likelihood": (I, [P, P, P, I, P, P, P, P, P, I]),
         "eor_emu_last_error": (ctypes.c_char_p, [P]),
         "eor_emu_destroy": (None, [P]),
+        "eor_mcmc_default_config": (None, [ctypes.POINTER(McmcConfig)]),
+        "eor_mcmc_create": (I, [ctypes.POINTER(McmcConfig), P, ctypes.POINTER(P)]),
+        "eor_mcmc_start": (I, [P, P, P, P, P, I]),
+        "eor_mcmc_run": (I, [P, I, P, P, P, I]),
+        "eor_mcmc_walkers": (I, [P, P, P, I]),
+        "eor_mcmc_last_error": (ctypes.c_char_p, [P]),
+        "eor_mcmc_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -542,6 +557,84 @@ class Emulator:
     calibrate = eor_emu_calibrate
     set_threshold = eor_emu_set_threshold
     likelihood = eor_emu_likelihood
+
+
+def mcmc_default_config(**overrides) -> McmcConfig:
+    cfg = McmcConfig()
+    load_library().eor_mcmc_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k in ("prior_lo", "prior_hi", "gauss_mean", "gauss_precision"):
+            arr = getattr(cfg, k)
+            for i, x in enumerate(np.ravel(v)):
+                arr[i] = float(x)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Sampler:
+    """The device-side ensemble sampler (eor_mcmc_create ... eor_mcmc_destroy) on a Context
+    (or, with ctx None and gauss_target=1, on a Gaussian test target)."""
+
+    def __init__(self, ctx: "Context | None", cfg: McmcConfig | None = None, **overrides):
+        self.lib = load_library()
+        self.cfg = cfg if cfg is not None else mcmc_default_config(**overrides)
+        self.ctx = ctx   # keeps the context alive
+        handle = ctypes.c_void_p()
+        rc = self.lib.eor_mcmc_create(ctypes.byref(self.cfg), None if ctx is None else ctx.handle,
+                                      ctypes.byref(handle))
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_mcmc_last_error(None).decode())
+        self.handle = handle
+        self.n_walkers = self.cfg.n_walkers
+
+    def _check(self, rc: int):
+        if rc != EOR_OK:
+            raise EorError(rc, self.lib.eor_mcmc_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eor_mcmc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eor_mcmc_start(self, params, mock_d2=None, sigma=None) -> np.ndarray:
+        pp, mem, _ = _arg(params, np.float64)
+        pm, _, km = _arg(mock_d2, np.float64)
+        ps, _, ks = _arg(sigma, np.float64)
+        lnp = np.empty(self.n_walkers)
+        if mem == EOR_DEVICE:
+            raise ValueError("host arrays only")
+        self._check(self.lib.eor_mcmc_start(self.handle, pp, pm, ps, lnp.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return lnp
+
+    def eor_mcmc_run(self, steps: int, want_chain: bool = True):
+        """(chain [steps][W][3], lnp [steps][W], accepted [steps][W]) as numpy arrays."""
+        w = self.n_walkers
+        chain = np.empty((steps, w, 3)) if want_chain else None
+        lnp = np.empty((steps, w)) if want_chain else None
+        acc = np.empty((steps, w), dtype=np.int32) if want_chain else None
+        self._check(self.lib.eor_mcmc_run(self.handle, int(steps),
+                                          None if chain is None else chain.ctypes.data_as(ctypes.c_void_p),
+                                          None if lnp is None else lnp.ctypes.data_as(ctypes.c_void_p),
+                                          None if acc is None else acc.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return chain, lnp, acc
+
+    def eor_mcmc_walkers(self):
+        x = np.empty((self.n_walkers, 3))
+        lnp = np.empty(self.n_walkers)
+        self._check(self.lib.eor_mcmc_walkers(self.handle, x.ctypes.data_as(ctypes.c_void_p),
+                                              lnp.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return x, lnp
+
+    start = eor_mcmc_start
+    run = eor_mcmc_run
+    walkers = eor_mcmc_walkers
 
 
 def box_power_spectrum_noalloc(n: int, box_mpc: float, box, d2, nmodes=None, n_bins: int = 14, k_lo: float = 0.1,
