@@ -97,14 +97,20 @@ int finish(eor_ctx* c, int mem) {
 }
 
 int check_device_error(eor_ctx* c) {
-    int err = 0;
-    cudaError_t e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    int words[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(words, c->d_err, sizeof(words), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "read error word");
+    const int err = words[0];
     if (err & eor::kErrParam) return fail(c, EOR_EINVAL, "walker parameter non-finite or out of range "
                                                          "(zeta > 0, 0 < R_mfp <= r_mfp_max, 0 < log10 T_vir < 12)");
     if (err & eor::kErrLadder) return fail(c, EOR_EINVAL, "radius ladder longer than the tables (raise r_mfp_max)");
     if (err & eor::kErrSigmaRange) return fail(c, EOR_EINVAL, "radius or halo mass outside the sigma^2 table range");
-    if (err & eor::kErrTimeout) return fail(c, EOR_ETIMEOUT, "a bounded tensor-core wait ran out");
+    if (err & eor::kErrTimeout) {
+        char where[96];
+        snprintf(where, sizeof(where), " (first: role %d, barrier %d, chunk %d)", (words[1] >> 28) & 15,
+                 (words[1] >> 20) & 255, words[1] & 0xFFFFF);
+        return fail(c, EOR_ETIMEOUT, std::string("a bounded tensor-core wait ran out") + where);
+    }
     return EOR_OK;
 }
 
@@ -281,13 +287,13 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_kd_m2, c->n_m2) && alloc_n(c, &c->d_m2_to_kd, c->n_m2) &&
               alloc_n(c, &c->d_basis, (size_t)eor::kBasisMax * c->n_m2) &&
               alloc_n(c, &c->d_coef_tab, (size_t)eor::kBasisMax * eor::kCoefGrid) &&
-              alloc_n(c, &c->d_phi_m2, (size_t)eor::kBasisMax * c->n_m2) && alloc_n(c, &c->d_err, 1);
+              alloc_n(c, &c->d_phi_m2, (size_t)eor::kBasisMax * c->n_m2) && alloc_n(c, &c->d_err, 2);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed");
     }
     cudaError_t e = eor::prepare_kernels(c->n);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = eor::build_cosmology_tables(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = eor::build_basis(c);
@@ -352,7 +358,7 @@ int eor_set_params(eor_ctx* c, const double* params, int n_walkers, int mem) {
         return fail(c, EOR_EINVAL, "params NULL, bad mem or n_walkers outside 1..max_walkers");
     int r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem);
     if (r) return r;
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream), "memset");
     c->n_walkers = n_walkers;
     CK(eor::build_walker_tables(c, n_walkers), "walker tables");
     CK(cudaStreamSynchronize(c->stream), "walker tables");
@@ -435,7 +441,7 @@ int eor_likelihood(eor_ctx* c, const double* params, int n_walkers, const double
     if ((r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem))) return r;
     if ((r = copy_in(c, c->d_mock, mock_d2, sizeof(double) * zb, mem))) return r;
     if ((r = copy_in(c, c->d_mock + zb, sigma, sizeof(double) * zb, mem))) return r;
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream), "memset");
     c->n_walkers = n_walkers;
     if (c->graph_walkers != n_walkers || c->graph_traced != c->trace_on) {
         if (c->graph_exec) {

@@ -37,9 +37,7 @@ struct Plane {
     static constexpr int LPT = UNITS / THREADS;            // lines per thread per pass
     static constexpr int NB = R1 / R2;                     // stage-B DFTs per unit
     static constexpr size_t SMEM = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 64 * sizeof(double);
-    static constexpr int NM2 = 3 * (N / 2) * (N / 2) + 1;  // |m|^2 values of the grid (bin table entries)
-    static constexpr size_t SMEM_PS = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 16 * THREADS * sizeof(float) +
-                                      (size_t)(NM2 + 15) / 16 * 16;
+    static constexpr size_t SMEM_PS = (size_t)N * S * sizeof(float2) + N * sizeof(float2) + 16 * THREADS * sizeof(float);
 };
 
 // 2D FFT of an n x n complex plane. load(r, c) gives the natural-order input; on return
@@ -219,13 +217,11 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
     float2* buf = smem;
     float2* tw = smem + N * P::S;
     float* priv = reinterpret_cast<float*>(tw + N);          // [kPrivBins][THREADS]
-    signed char* sbin = reinterpret_cast<signed char*>(priv + kPrivBins * P::THREADS);   // [NM2] bin of |m|^2
     __shared__ double s_bins[EOR21_MAX_BINS];
     const int kz = blockIdx.x, slot = blockIdx.y;
     const int pair = a.pair0 + slot;
     if (pair >= a.n_pairs) return;
     fill_twiddles<N>(tw);
-    for (int e = threadIdx.x; e < P::NM2; e += P::THREADS) sbin[e] = a.bin_of_m2[e];
     for (int e = threadIdx.x; e < kPrivBins * P::THREADS; e += P::THREADS) priv[e] = 0.0f;
     for (int e = threadIdx.x; e < EOR21_MAX_BINS; e += P::THREADS) s_bins[e] = 0.0;
     __syncthreads();
@@ -245,7 +241,7 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
             for (int k2 = 0; k2 < P::R2; k2++) {
                 const int my = signed_index(plane_col<N, T>(l, q, k2), N);
                 const int m2 = mx * mx + my * my + mz2;
-                const int b = sbin[m2];
+                const int b = a.bin_of_m2[m2];
                 if (b >= 0) {
                     const float2 v = hold[l][q][k2];
                     const float fm2 = (float)m2;

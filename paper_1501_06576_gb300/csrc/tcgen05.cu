@@ -9,7 +9,15 @@
 namespace eor {
 namespace {
 
-constexpr uint32_t kWaitTries = 1u << 22;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s of GPU time per bounded wait
+
+// A bounded wait ran out: set kErrTimeout and keep the first record of where,
+// err[1] = role << 28 | barrier << 20 | chunk (roles 1 copy, 2 MMA, 3 epilogue; barriers
+// 1 A, 2 B full, 3 B empty, 4 meta full, 5 meta empty, 6 accumulator full, 7 accumulator free).
+__device__ __forceinline__ void record_timeout(int* err, int role, int bar, int chunk) {
+    atomicOr(err, kErrTimeout);
+    atomicCAS(err + 1, 0, (role << 28) | (bar << 20) | (chunk & 0xFFFFF));
+}
 
 __global__ void __launch_bounds__(128) k_tc_check(const float* A, const float* B, float* D, int n, uint32_t ncols,
                                                    int* err) {
@@ -39,8 +47,8 @@ __global__ void __launch_bounds__(128) k_tc_check(const float* A, const float* B
         }
         tc::mma_commit(bar);
     }
-    bool ok = tc::mbar_wait(bar, 0, kWaitTries);
-    if (!ok) ok = tc::mbar_wait(bar, 0, kWaitTries);   // let an MMA in flight finish before freeing its memory
+    bool ok = tc::mbar_wait(bar, 0, kWaitNs);
+    if (!ok) ok = tc::mbar_wait(bar, 0, kWaitNs);   // let an MMA in flight finish before freeing its memory
     tc::fence_after_sync();
     if (ok) {
         for (int c0 = 0; c0 < n; c0 += 16) {
@@ -87,23 +95,23 @@ extern "C" int eor_tensor_core_check(const float* a, const float* b, float* d, i
 namespace eor {
 namespace {
 
-constexpr int kTcTiles = 1;                            // M tiles of 128 cells per CTA (two CTAs per SM)
+constexpr int kTcTiles = 2;                            // M tiles of 128 cells per CTA
 constexpr int kTcCells = 128 * kTcTiles;               // cells per CTA
 constexpr int kTcN = 128;                              // (walker, radius) columns per chunk (MMA N)
-constexpr int kTcStages = 2;                           // coefficient chunks in flight per CTA
+constexpr int kTcStages = 3;                           // coefficient chunks in flight
 constexpr int kGroup = 32;                             // epilogue columns per tensor-memory read
 constexpr uint32_t kTileBytes = 128 * tc::kKMax * 4;   // one 128 x 32 TF32 tile (16 KB)
-constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (32 KB)
+constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (64 KB)
 constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chunk (32 KB)
 // chunk meta: one 16-byte record per group of kGroup columns: (walker << 2 | first << 1 |
 // last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0)
 constexpr int kGroupsPerChunk = kTcN / kGroup;
 constexpr uint32_t kMBytes = kGroupsPerChunk * 16;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
-constexpr uint32_t kTmemCols = 2 * kTcTiles * kTcN;       // 2 buffers x kTcTiles x kTcN columns (256)
+constexpr uint32_t kTmemCols = 2 * kTcTiles * kTcN;       // 2 buffers x kTcTiles x kTcN columns (512)
 constexpr int kTcEpi = 2 * 128 * kTcTiles;               // epilogue threads: 2 per cell
 constexpr int kTcThreads = 128 + kTcEpi;                  // warps 0-3: MMA (thread 0), copies (thread 32); then epilogue
-constexpr int kTcCtasPerSm = 2;                          // shared memory and tensor memory allow two
+constexpr int kTcCtasPerSm = 1;                          // one CTA holds all tensor memory of an SM
 constexpr float kNever = 1.0e30f;                         // folded threshold that no delta_R reaches
 constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
 static_assert(2 * kTcTiles * kTcN <= (int)kTmemCols, "tensor memory");
@@ -218,25 +226,23 @@ struct TcArgs {
     long long n3;
 };
 
-// One CTA: 128 cells of one redshift (one M = 128 tile) against every (walker, radius)
-// column; two CTAs share an SM (97 KB of shared memory and 256 tensor-memory columns each),
-// so that one CTA's operand waits, pipeline fill and drain overlap the other's work. The
-// cells' basis values (A) and each 128-column chunk of coefficients (B) arrive by bulk copy
-// in the TF32 hi/lo core-matrix layout; thread 0 issues, per K step, hi*hi + hi*lo + lo*hi
-// (3xTF32, FP32 accumulation) into one of two tensor-memory buffers, so D(cell, column) =
-// sum_b F_b c_b - threshold = delta_R - threshold. Each walker's columns start on a group
-// of 32: its R_cell column first (D = delta_R - delta_c), then its radii from R_mfp down,
-// then padding. Warps 4-11 run the epilogue of the other buffer meanwhile, two threads per
-// cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag of a walker, "D >= 0 (sign bit
-// clear) at some radius above R_cell", is an AND of sign bits over its columns; at its last
-// group the thread forms x_HI and delta T_b (coalesced stores) and the warp adds its exact
-// fixed-point x_HI sum to the pair's total.
+// One CTA: 256 cells of one redshift (two 128-row tiles) against every (walker, radius)
+// column. The cells' basis values (A) and each 128-column chunk of coefficients (B) arrive by
+// bulk copy in the TF32 hi/lo core-matrix layout; thread 0 issues, per K step, product and
+// tile, hi*hi + hi*lo + lo*hi (3xTF32, FP32 accumulation) into one of two tensor-memory
+// buffers, so D(cell, column) = sum_b F_b c_b - threshold = delta_R - threshold. Each
+// walker's columns start on a group of 32: its R_cell column first (D = delta_R - delta_c),
+// then its radii from R_mfp down, then padding. Warps 4-19 run the epilogue of the other
+// buffer meanwhile, two threads per cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag
+// of a walker, "D >= 0 (sign bit clear) at some radius above R_cell", is an AND of sign bits
+// over its columns; at its last group the thread forms x_HI and delta T_b (coalesced stores)
+// and the warp adds its exact fixed-point x_HI sum to the pair's total.
 // Roles: thread 32 issues the bulk copies, thread 0 the MMAs (it waits only for operands and
-// a free accumulator buffer, so the tensor pipe stays fed), warps 4-11 the epilogue.
-// Hand-offs: chunk c + 2 reuses chunk c's stage after MMA(c) (coefficients) and the
+// a free accumulator buffer, so the tensor pipe stays fed), warps 4-19 the epilogue.
+// Hand-offs: chunk c + 3 reuses chunk c's stage after MMA(c) (coefficients) and the
 // epilogue's read of chunk c's meta; MMA(c) reuses the tensor memory of chunk c - 2 after
-// its epilogue. Every wait is bounded; on a timeout the CTA sets kErrTimeout, waits for its
-// copies and MMAs in flight and frees its tensor memory.
+// its epilogue. Every wait is bounded in GPU time; on a timeout the CTA records where, sets
+// kErrTimeout, waits for its copies and MMAs in flight and frees its tensor memory.
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* As = sm;                                // A hi tiles then lo tiles
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t kTries = 1u << 24;
+    constexpr uint64_t kTries = kWaitNs;   // time limit of every wait below
     // copy-thread bookkeeping: parity of the phase each copy barrier still owes, or -1
     int owedA = -1, owedB[kTcStages], owedM[kTcStages];
 #pragma unroll
@@ -299,30 +305,29 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             const int st = c % kTcStages;
             const uint32_t use = (uint32_t)(c / kTcStages);   // how many chunks used the stage before
             if (use > 0) ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kTries, abort);
-            if (!ok) break;
+            if (!ok) { record_timeout(a.err, 1, 3, c); break; }
             tc::mbar_expect_tx(barB + st, kBBytes);
             tc::bulk_g2s(Bs + st * kBBytes, Bg + (size_t)c * kChunkBytes, kBBytes, barB + st);
             owedB[st] = (int)(use & 1u);
             if (use > 0) ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kTries, abort);
-            if (!ok) break;
+            if (!ok) { record_timeout(a.err, 1, 5, c); break; }
             tc::mbar_expect_tx(barM + st, kMBytes);
             tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, kMBytes, barM + st);
             owedM[st] = (int)(use & 1u);
         }
-        if (!ok) {
-            *abort = 1;
-            atomicOr(a.err, kErrTimeout);
-        }
+        if (!ok) *abort = 1;
     } else if (t == 0 && nch > 0) {
         // ---------------- MMA thread: waits only for operands and a free accumulator buffer
         bool ok = tc::mbar_wait_or_abort(barA, 0, kTries, abort);
+        if (!ok) record_timeout(a.err, 2, 1, 0);
         const uint32_t idesc = tc::idesc_tf32(128, kTcN);
         for (int c = 0; c < nch && ok; c++) {
             const int st = c % kTcStages, tb = c & 1;
             ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
-            if (ok && c >= 2)   // the epilogue of chunk c - 2 has released tensor-memory buffer tb
+            if (!ok) { record_timeout(a.err, 2, 2, c); break; }
+            if (c >= 2)   // the epilogue of chunk c - 2 has released tensor-memory buffer tb
                 ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - 2) >> 1) & 1u, kTries, abort);
-            if (!ok) break;
+            if (!ok) { record_timeout(a.err, 2, 7, c); break; }
             tc::fence_after_sync();
             // the tiles' accumulators alternate, so that consecutive MMAs are independent
             for (int ks = 0; ks < a.ksteps; ks++) {
@@ -348,10 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             tc::mma_commit(barD + tb);    // accumulators ready for the epilogue
             tc::mma_commit(barBe + st);   // coefficient stage free for the copy thread
         }
-        if (!ok) {
-            *abort = 1;
-            atomicOr(a.err, kErrTimeout);
-        }
+        if (!ok) *abort = 1;
     } else if (warp >= 4 && nch > 0) {
         // ---------------- epilogue warps: warp 4 + e owns tensor-memory lanes 32 (e % 4) .. + 31
         // (the quarter its warp index allows) of tile (e / 4) % 2, and groups 2 (e / 8) and
@@ -362,9 +364,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
         const float dens = __ldg(a.delta + (size_t)zi * a.n3 + cell);
         for (int c = 0; c < nch; c++) {
             const int st = c % kTcStages, tb = c & 1;
-            if (!tc::mbar_wait_or_abort(barD + tb, (uint32_t)(c >> 1) & 1u, kTries, abort) ||
-                !tc::mbar_wait_or_abort(barM + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort)) {
-                if (lane == 0) atomicOr(a.err, kErrTimeout);
+            const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(c >> 1) & 1u, kTries, abort);
+            const bool okM = okD && tc::mbar_wait_or_abort(barM + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
+            if (!okM) {
+                if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, c);
                 *abort = 1;
                 break;
             }
@@ -499,10 +502,7 @@ cudaError_t prepare_basis_tc(eor_ctx* c) {
     (void)c;
     cudaError_t e =
         cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)basis_tc_smem());
-    if (e != cudaSuccess) return e;
-    // the largest shared-memory carve-out, so that kTcCtasPerSm CTAs fit on an SM
-    return cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 cudaError_t format_basis_tc(eor_ctx* c) {
