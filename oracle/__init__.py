@@ -72,6 +72,8 @@ def _load():
         "or_tophat_w": (_D, [_D]),
         "or_sigma2": (_D, [ctypes.POINTER(_Cosmo), _D]),
         "or_growth": (_D, [ctypes.POINTER(_Cosmo), _D]),
+        "or_growth_rate": (_D, [ctypes.POINTER(_Cosmo), _D]),
+        "or_los_gradient": (None, [_I, _D, _P, _P]),
         "or_rho_mean": (_D, [ctypes.POINTER(_Cosmo)]),
         "or_mass_to_radius": (_D, [ctypes.POINTER(_Cosmo), _D]),
         "or_mmin": (_D, [ctypes.POINTER(_Cosmo), _D, _D, _D]),
@@ -154,6 +156,9 @@ class Oracle:
     def growth(self, z: float) -> float:
         return self.lib.or_growth(ctypes.byref(self._c), float(z))
 
+    def growth_rate(self, z: float) -> float:
+        return self.lib.or_growth_rate(ctypes.byref(self._c), float(z))
+
     def rho_mean(self) -> float:
         return self.lib.or_rho_mean(ctypes.byref(self._c))
 
@@ -187,8 +192,19 @@ class Oracle:
         self.lib.or_filter_box(n, float(box_mpc), _ptr(d), float(r), _ptr(out))
         return out
 
+    def rsd_weight(self, delta: np.ndarray, box_mpc: float, z: float, max_dvdr: float) -> np.ndarray:
+        """(1 + delta) H / (dv_r/dr + H) with linear velocities along the last axis:
+        dv_r/dr / H = -f IDFT(k_z^2/k^2 delta_hat), clipped to [-max_dvdr, max_dvdr] (Sec. 2.2's
+        velocity-gradient factor; the clip is a reading: the paper is silent where it diverges)."""
+        d = np.ascontiguousarray(delta, dtype=np.float32)
+        n = d.shape[0]
+        g = np.empty(d.shape, dtype=np.float64)
+        self.lib.or_los_gradient(n, float(box_mpc), _ptr(d), _ptr(g))
+        dvdr = np.clip(-self.growth_rate(z) * g, -max_dvdr, max_dvdr)
+        return (1.0 + d.astype(np.float64)) / (1.0 + dvdr)
+
     def ionize(self, delta: np.ndarray, box_mpc: float, z: float, zeta: float, r_mfp: float,
-               log10_tvir: float) -> dict:
+               log10_tvir: float, rsd_max_dvdr: float | None = None) -> dict:
         d = np.ascontiguousarray(delta, dtype=np.float32)
         n = d.shape[0]
         xhi = np.empty(d.shape, dtype=np.float64)
@@ -198,6 +214,9 @@ class Oracle:
         nr = self.lib.or_ionize(ctypes.byref(self._c), ctypes.byref(self._ion), n, float(box_mpc),
                                 float(z), _ptr(d), float(zeta), float(r_mfp), float(log10_tvir),
                                 _ptr(xhi), _ptr(flag), _ptr(dtb), _ptr(mean))
+        if rsd_max_dvdr is not None:
+            # delta T_b = T0 x_HI (1 + delta) H / (dv_r/dr + H) (Sec. 2.2)
+            dtb = self.t0_mk(z) * xhi * self.rsd_weight(d, box_mpc, z, rsd_max_dvdr)
         return {"xhi": xhi, "flag": flag, "dtb": dtb, "xhi_mean": float(mean[0]), "n_radii": nr}
 
 

@@ -256,6 +256,16 @@ double or_growth(const or_cosmo* c, double z) {
     return growth_unnorm(c, 1.0 / (1.0 + z)) / growth_unnorm(c, 1.0);
 }
 
+/* Growth rate f = d ln D / d ln a of D(a) = E(a) I(a), I(a) = Int_0^a da'/(a' E(a'))^3:
+ * a D'/D = d ln E / d ln a + 1 / (a^2 E^3 I), with d ln E / d ln a = -1.5 Omega_m / (a^3 E^2)
+ * for flat LCDM. */
+double or_growth_rate(const or_cosmo* c, double z) {
+    double a = 1.0 / (1.0 + z);
+    double e = hubble_e(c, a);
+    double i_a = growth_unnorm(c, a) / e;
+    return -1.5 * c->omega_m / (a * a * a * e * e) + 1.0 / (a * a * e * e * e * i_a);
+}
+
 double or_rho_mean(const or_cosmo* c) { return c->omega_m * OR_RHO_CRIT_H2 * c->h * c->h; }
 
 double or_mass_to_radius(const or_cosmo* c, double m) {
@@ -341,6 +351,33 @@ static void filter_from_spectrum(int n, double box_mpc, const double* spec, doub
     or_fft3d(work, n, +1);
 #pragma omp parallel for schedule(static)
     for (long long i = 0; i < (long long)n3; i++) out[i] = work[2 * i] / (double)n3;
+}
+
+/* Line-of-sight (last axis) second derivative field: out = IDFT(k_z^2 / k^2 DFT(delta)) / n^3,
+ * zero at k = 0. In linear theory dv_r/dr = -f H out. */
+void or_los_gradient(int n, double box_mpc, const float* delta, double* out) {
+    size_t n3 = (size_t)n * n * n;
+    double* spec = forward_spectrum(n, delta);
+    (void)box_mpc;   /* the ratio k_z^2 / k^2 does not depend on the box size */
+#pragma omp parallel for schedule(static)
+    for (long long ix = 0; ix < n; ix++) {
+        double mx = freq_index((int)ix, n);
+        for (int iy = 0; iy < n; iy++) {
+            double my = freq_index(iy, n);
+            for (int iz = 0; iz < n; iz++) {
+                double mz = freq_index(iz, n);
+                double m2 = mx * mx + my * my + mz * mz;
+                double w = m2 > 0.0 ? mz * mz / m2 : 0.0;
+                size_t idx = ((size_t)ix * n + iy) * n + iz;
+                spec[2 * idx] *= w;
+                spec[2 * idx + 1] *= w;
+            }
+        }
+    }
+    or_fft3d(spec, n, +1);
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)n3; i++) out[i] = spec[2 * i] / (double)n3;
+    free(spec);
 }
 
 void or_filter_box(int n, double box_mpc, const float* delta, double r, double* out) {

@@ -19,6 +19,10 @@
  *                            scipy quadrature of j1 for n_s = 1, sigma(8/h) = sigma8
  *   or_growth                Einstein-de Sitter limit D = 1/(1+z); Carroll-Press-Turner
  *                            growth suppression within 1 %
+ *   or_growth_rate           Einstein-de Sitter f = 1; the numerical derivative of ln D;
+ *                            Linder's Omega_m(z)^0.55 within 1 %
+ *   or_los_gradient          plane waves: along the line of sight the field itself, across
+ *                            it zero, at 45 degrees half of it
  *   or_mmin                  the three halo masses printed in Sec. 3.1 / 4.1 (10^8.06,
  *                            10^8.78, 10^9.11 Msun at z = 8), tests/golden/mmin_paper.txt
  *   or_t0_mk                 27 mK at (1+z)/10 = 1, Omega_m h^2 = 0.15, Omega_b h^2 = 0.023
@@ -67,6 +71,7 @@ double or_pk(const or_cosmo* c, double k);               /* linear P(k) at z = 0
 double or_tophat_w(double x);                            /* 3 (sin x - x cos x) / x^3 */
 double or_sigma2(const or_cosmo* c, double r);           /* sigma^2 of the top-hat radius r at z = 0 */
 double or_growth(const or_cosmo* c, double z);           /* D(z), D(0) = 1 */
+double or_growth_rate(const or_cosmo* c, double z);      /* f = d ln D / d ln a */
 double or_rho_mean(const or_cosmo* c);                   /* mean matter density, Msun / Mpc^3 */
 double or_mass_to_radius(const or_cosmo* c, double m);
 double or_mmin(const or_cosmo* c, double tvir, double z, double mu);
@@ -81,6 +86,10 @@ double or_fcoll(double delta_r, double sigma2_min, double sigma2_r, double delta
 
 /* delta_R = IDFT(W(kR) DFT(delta)) / n^3 for one radius; out: n^3 doubles. */
 void   or_filter_box(int n, double box_mpc, const float* delta, double r, double* out);
+
+/* IDFT(k_z^2/k^2 DFT(delta)) / n^3 along the last axis (line of sight); out: n^3 doubles.
+ * Linear theory: dv_r/dr = -f H times this field (velocity-gradient term of delta T_b). */
+void   or_los_gradient(int n, double box_mpc, const float* delta, double* out);
 
 /* Excursion-set ionization of one box at redshift z for parameters (zeta, R_mfp, log10 T_vir).
  * Any output pointer may be NULL. Returns the ladder length. */
