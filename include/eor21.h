@@ -79,12 +79,20 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* user);
     void (*dev_free)(void* ptr, void* user);
     void* alloc_user;
+    /* Velocity-gradient factor of delta T_b (Sec. 2.2): 1 multiplies delta T_b by
+     * H / (dv_r/dr + H) with linear peculiar velocities along the last box axis,
+     * dv_r/dr / H = -f IDFT(k_z^2/k^2 delta_hat) (f = d ln D / d ln a), clipped to
+     * [-rsd_max_dvdr, rsd_max_dvdr]; 0 (default) leaves the factor at 1. The factor is a
+     * per-box field, formed once at eor_init_boxes. */
+    int rsd;
+    double rsd_max_dvdr;         /* 0.2 */
 } eor_config;
 
 /* Defaults: n = 128, L = 250 Mpc, z = {8, 9, 10}, (h, Omega_m, Omega_b, n_s, sigma_8) =
  * (0.68, 0.31, 0.02254/0.68^2, 0.96, 0.82), r_factor 1.1, r_cell_rule 0, delta_c 1.686,
  * mu 0.6 (the value that reproduces the halo masses printed in Sec. 3.1 and 4.1),
- * 14 bins on [0.1, 1.5), chi^2 bins 0.15..1.0 (Sec. 2.5), max_walkers 1, r_mfp_max 20. */
+ * 14 bins on [0.1, 1.5), chi^2 bins 0.15..1.0 (Sec. 2.5), max_walkers 1, r_mfp_max 20,
+ * rsd 0 (rsd_max_dvdr 0.2). */
 void eor_default_config(eor_config* cfg);
 
 /* Create a context on the current CUDA device, ordered on `cuda_stream` (a cudaStream_t;

@@ -196,6 +196,8 @@ void eor_default_config(eor_config* cfg) {
     cfg->chi2_k_lo = 0.15; cfg->chi2_k_hi = 1.0;
     cfg->max_walkers = 1;
     cfg->r_mfp_max = 20.0;
+    cfg->rsd = 0;
+    cfg->rsd_max_dvdr = 0.2;
 }
 
 const char* eor_version(void) { return kVersion; }
@@ -209,7 +211,7 @@ void eor_destroy(eor_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (cudaEvent_t e : c->trace_events) cudaEventDestroy(e);
-    void* bufs[] = {c->d_delta, c->d_spec, c->d_lnsig, c->d_growth, c->d_cosmo_amp, c->d_bin_of_m2,
+    void* bufs[] = {c->d_delta, c->d_bright, c->d_spec, c->d_lnsig, c->d_growth, c->d_cosmo_amp, c->d_bin_of_m2,
                     c->d_nmodes, c->d_ksum, c->d_params, c->d_walkers, c->d_pairs, c->d_wtab, c->d_inter,
                     c->d_flags, c->d_psinter, c->d_ps_sum, c->d_xhi_sum, c->d_chi2, c->d_mock, c->d_d2,
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
@@ -241,6 +243,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     if (g.max_walkers < 1 || !(g.r_mfp_max > 0.0)) return fail(nullptr, EOR_EINVAL, "max_walkers/r_mfp_max");
     if ((g.dev_alloc == nullptr) != (g.dev_free == nullptr))
         return fail(nullptr, EOR_EINVAL, "dev_alloc and dev_free come together");
+    if ((g.rsd != 0 && g.rsd != 1) || (g.rsd && !(g.rsd_max_dvdr > 0.0 && g.rsd_max_dvdr < 1.0)))
+        return fail(nullptr, EOR_EINVAL, "rsd must be 0 or 1, with 0 < rsd_max_dvdr < 1");
 
     eor_ctx* c = new (std::nothrow) eor_ctx();
     if (!c) return fail(nullptr, EOR_ENOMEM, "host allocation");
@@ -271,7 +275,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     const size_t pairs = (size_t)W * Z;
     c->flag_words = eor::flag_words_per_pair(g.n);
     bool ok = alloc_n(c, &c->d_delta, (size_t)Z * c->n3) && alloc_n(c, &c->d_spec, (size_t)Z * c->nspec) &&
-              alloc_n(c, &c->d_lnsig, eor::kSigmaTable + 1) && alloc_n(c, &c->d_growth, Z) &&
+              alloc_n(c, &c->d_lnsig, eor::kSigmaTable + 1) && alloc_n(c, &c->d_growth, 2 * (size_t)Z) &&
               alloc_n(c, &c->d_cosmo_amp, 1) && alloc_n(c, &c->d_bin_of_m2, c->n_m2) &&
               alloc_n(c, &c->d_nmodes, B) && alloc_n(c, &c->d_ksum, B) && alloc_n(c, &c->d_params, 3 * W) &&
               alloc_n(c, &c->d_walkers, W) && alloc_n(c, &c->d_pairs, pairs) &&
@@ -312,6 +316,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
              alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
              alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
              alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
+    if (ok && g.rsd) ok = alloc_n(c, &c->d_bright, (size_t)Z * c->n3);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");
@@ -335,6 +340,8 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
     for (int zi = 0; zi < c->cfg.n_z; zi++) {
         cudaError_t e = eor::launch_forward_spectrum(c, zi);
         if (e != cudaSuccess) return cuda_fail(c, e, "forward spectrum");
+        if (c->cfg.rsd && (e = eor::launch_brightness_weight(c, zi)) != cudaSuccess)
+            return cuda_fail(c, e, "velocity-gradient factor");
         // basis fields F_b = IDFT(phi_b delta_hat) of this box
         for (int b = 0; b < c->kb; b++) {
             e = eor::launch_filtered_density(c, zi, c->d_F + ((size_t)zi * c->kb + b) * c->n3,

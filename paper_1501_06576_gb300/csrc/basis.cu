@@ -486,7 +486,7 @@ cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
     if (c->tune.method == kMethodBasis && basis_tc_fits(c->basis_rank)) return launch_basis_ionize_tc(c, xhi_out);
-    BasisArgs a{c->d_F, c->d_coef, c->d_pairs, c->d_delta, c->d_dtb, xhi_out, c->d_xpart, c->n_walkers, n_z,
+    BasisArgs a{c->d_F, c->d_coef, c->d_pairs, brightness_base(c), c->d_dtb, xhi_out, c->d_xpart, c->n_walkers, n_z,
                 c->max_radii, (long long)c->n3, (float)c->cfg.delta_c};
     const size_t smem = basis_ionize_smem(c->kb, c->max_radii);
     const int parts = (int)(c->n3 / kTC);

@@ -88,9 +88,10 @@ struct eor_ctx {
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]
+    float* d_bright = nullptr;       // [n_z][n^3] (1 + delta) H/(dv_r/dr + H) - 1 when cfg.rsd, else unused
     float2* d_spec = nullptr;        // [n_z][nh][n][n]
     double* d_lnsig = nullptr;       // ln sigma^2(R) at z = 0 on the ln R grid
-    double* d_growth = nullptr;      // [n_z]
+    double* d_growth = nullptr;      // [2][n_z]: D(z), then f = d ln D / d ln a
     double* d_cosmo_amp = nullptr;   // [1] P(k) amplitude
     signed char* d_bin_of_m2 = nullptr;   // [n_m2] bin of |m|^2 or -1
     signed char* d_chi2_use = nullptr;    // [n_bins] 1 where the bin enters chi^2
@@ -208,6 +209,9 @@ cudaError_t launch_chi2(eor_ctx* c);
 cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab);
 cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab);
 cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box);
+cudaError_t launch_brightness_weight(eor_ctx* c, int zi);
+// the field multiplying T0 x_HI in delta T_b, minus 1: delta, or the velocity-weighted form
+inline const float* brightness_base(const eor_ctx* c) { return c->cfg.rsd ? c->d_bright : c->d_delta; }
 bool grid_supported(int n);
 
 }  // namespace eor

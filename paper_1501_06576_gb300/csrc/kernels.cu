@@ -704,7 +704,7 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
             trace_begin(c, kKFilterPlane);
             k_plane_filter_inverse<N, T><<<dim3(NH, G, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
             trace_end(c);
-            Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, c->d_delta, xhi_out,
+            Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, brightness_base(c), xhi_out,
                          c->d_xhi_sum, c->d_psinter, pair0, n_pairs, g * G, G, (float)c->cfg.delta_c};
             trace_begin(c, kKPencil);
             k_pencil_ionize<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(a2);
@@ -731,6 +731,52 @@ cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab
         return e;
     Pass1Args a1{c->d_spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
     trace_begin(c, kKFilterPlane);
+    k_plane_filter_inverse<N, T><<<dim3(NH, 1, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
+    trace_end(c);
+    trace_begin(c, kKOther);
+    k_pencil_density<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(c->d_inter, out);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+// delta_hat k_z^2 / k^2 (0 at k = 0) of a half spectrum [kz][kx][ky]: the Fourier transform of
+// the line-of-sight second derivative field that gives linear dv_r/dr (last box axis).
+__global__ void k_los_weight(const float2* spec, int n, float2* out) {
+    const long long total = (long long)(n / 2 + 1) * n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(e / ((long long)n * n)), kx = (int)((e / n) % n), ky = (int)(e % n);
+        const int mx = signed_index(kx, n), my = signed_index(ky, n);
+        const int m2 = mx * mx + my * my + kz * kz;
+        const float w = m2 > 0 ? (float)(kz * kz) / (float)m2 : 0.0f;
+        const float2 v = spec[e];
+        out[e] = make_float2(v.x * w, v.y * w);
+    }
+}
+
+// (1 + delta) H / (dv_r/dr + H) - 1 with dv_r/dr / H = -f g clipped to [-max_dvdr, max_dvdr].
+__global__ void k_rsd_weight(const float* delta, const float* g, const double* f, float max_dvdr, long long n3,
+                             float* out) {
+    const float fz = (float)*f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const float dvdr = fminf(fmaxf(-fz * g[i], -max_dvdr), max_dvdr);
+        out[i] = (1.0f + delta[i]) / (1.0f + dvdr) - 1.0f;
+    }
+}
+
+// Real box of a half spectrum held at spec ([kz][kx][ky], one box) through the plane and
+// pencil inverse passes with the unit window at wtab; normalised by 1/n^3.
+template <int N, int T>
+cudaError_t spectrum_to_box_n(eor_ctx* c, const float2* spec, float* out, const float* wtab) {
+    constexpr int NH = N / 2 + 1;
+    cudaError_t e;
+    PairInfo pi{};
+    pi.w = 0; pi.zi = 0; pi.n_r = 1;
+    if ((e = cudaMemcpyAsync(c->d_diag_pair, &pi, sizeof(PairInfo), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
+        return e;
+    Pass1Args a1{spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
+    trace_begin(c, kKOther);
     k_plane_filter_inverse<N, T><<<dim3(NH, 1, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
     trace_end(c);
     trace_begin(c, kKOther);
@@ -802,6 +848,35 @@ cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signe
         case 128: return box_ps_raw_n<128, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// The velocity-weighted brightness field of box zi (Sec. 2.2): k_z^2/k^2 delta_hat -> real
+// field g (scratch box) -> (1 + delta) / (1 + clip(-f g)) - 1 into d_bright.
+cudaError_t launch_brightness_weight(eor_ctx* c, int zi) {
+    cudaError_t e;
+    trace_begin(c, kKOther);
+    k_los_weight<<<1024, 256, 0, c->stream>>>(c->d_spec + (size_t)zi * c->nspec, c->n, c->d_psinter);
+    trace_end(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_window_table(c, 0.0, c->d_diag_wtab)) != cudaSuccess) return e;   // W(0) = 1 everywhere
+    switch (c->n) {
+        case 16: e = spectrum_to_box_n<16, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab); break;
+        case 32: e = spectrum_to_box_n<32, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab); break;
+        case 64: e = spectrum_to_box_n<64, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab); break;
+        case 128:
+            e = c->tune.plane_threads >= 1024
+                    ? spectrum_to_box_n<128, 1024>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab)
+                    : spectrum_to_box_n<128, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_rsd_weight<<<1024, 256, 0, c->stream>>>(c->d_delta + (size_t)zi * c->n3, c->d_scratch_box,
+                                              c->d_growth + c->cfg.n_z + zi, (float)c->cfg.rsd_max_dvdr,
+                                              (long long)c->n3, c->d_bright + (size_t)zi * c->n3);
+    trace_end(c);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box) { EOR_DISPATCH(c, box_power_spectrum_n, c, box) }

@@ -119,14 +119,15 @@ __global__ void k_sigma2_normalise(double* shape, int n_table, double sigma8, do
     if (threadIdx.x == 0) amp_out[0] = amp;
 }
 
-// Linear growth D(z) = E(a) Int_0^a da'/(a' E(a'))^3 / (same at a = 1), flat LCDM;
+// Linear growth D(z) = E(a) Int_0^a da'/(a' E(a'))^3 / (same at a = 1), flat LCDM, and its
+// rate f = d ln D / d ln a into out[n_z + j];
 // substituting a' = u^2 makes the integrand smooth at 0. One block per redshift.
 __global__ void k_growth(const double* zs, int n_z, double om, double ol, double* out) {
     __shared__ double gx[kGL], gw[kGL], red[32];
     gauss_legendre(gx, gw);
     __syncthreads();
     const int panels = 256;
-    double res[2];
+    double res[2], integ0 = 0.0;
     for (int which = 0; which < 2; which++) {
         double a = which == 0 ? 1.0 / (1.0 + zs[blockIdx.x]) : 1.0;
         double umax = sqrt(a), h = umax / panels, acc = 0.0;
@@ -141,8 +142,15 @@ __global__ void k_growth(const double* zs, int n_z, double om, double ol, double
         }
         double s = block_sum(acc, red);
         res[which] = sqrt(om / (a * a * a) + ol) * s;
+        if (which == 0) integ0 = s;
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = res[0] / res[1];
+    if (threadIdx.x == 0) {
+        out[blockIdx.x] = res[0] / res[1];
+        // f = d ln D / d ln a = d ln E / d ln a + 1 / (a^2 E^3 I), d ln E / d ln a = -1.5 Om / (a^3 E^2)
+        const double a = 1.0 / (1.0 + zs[blockIdx.x]);
+        const double e = sqrt(om / (a * a * a) + ol);
+        out[n_z + blockIdx.x] = -1.5 * om / (a * a * a * e * e) + 1.0 / (a * a * e * e * e * integ0);
+    }
 }
 
 // Bin of every |m|^2 = mx^2 + my^2 + mz^2 (FP64 decision, -1 outside [k_lo, k_hi) or k = 0).

@@ -530,7 +530,7 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     const int pairs = c->n_walkers * c->cfg.n_z;
     cudaError_t e = cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * pairs, c->stream);
     if (e != cudaSuccess) return e;
-    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, c->d_delta, c->d_dtb, xhi_out, c->d_xq, c->d_err,
+    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, brightness_base(c), c->d_dtb, xhi_out, c->d_xq, c->d_err,
              c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3};
     trace_begin(c, kKBasis);
     k_basis_ionize_tc<<<dim3((unsigned)(c->n3 / kTcCells), c->cfg.n_z), kTcThreads, basis_tc_smem(), c->stream>>>(a);

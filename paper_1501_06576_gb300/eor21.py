@@ -47,7 +47,8 @@ class EorConfig(ctypes.Structure):
                 ("mu", ctypes.c_double), ("n_bins", ctypes.c_int), ("k_lo", ctypes.c_double),
                 ("k_hi", ctypes.c_double), ("chi2_k_lo", ctypes.c_double), ("chi2_k_hi", ctypes.c_double),
                 ("max_walkers", ctypes.c_int), ("r_mfp_max", ctypes.c_double),
-                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p)]
+                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p),
+                ("rsd", ctypes.c_int), ("rsd_max_dvdr", ctypes.c_double)]
 
 
 class EmuConfig(ctypes.Structure):
