@@ -157,6 +157,16 @@ int eor_walker_ladder(eor_ctx* ctx, int walker, double* radii, int* n_radii);
 int eor_box_power_spectrum(eor_ctx* ctx, const float* box, double* d2, double* kmean, long long* nmodes,
                            int mem);
 
+/* Total uncertainty of mock spectra per bin (Sec. 2.4's T+S equation, Sec. 2.5's modelling
+ * error): sigma_b^2 = (sum over the bin's modes i of 1 / (N_i + mock_b)^2)^-1
+ * + (model_frac mock_b)^2, over the modes of the full grid (k != 0) in the context's bins.
+ * mock_d2 double [n_z][n_bins]; thermal (optional, NULL = no thermal noise) float
+ * [n_z][n/2 + 1][n][n]: the per-mode thermal noise Delta^2_N in the half-spectrum layout
+ * [kz][kx][ky], shared by each mode's conjugate; sigma double [n_z][n_bins], NaN where a bin
+ * has no mode. Uses only the context's grid and bins (needs only eor_create). */
+int eor_noise_sigma(eor_ctx* ctx, const double* mock_d2, const float* thermal, double model_frac, double* sigma,
+                    int mem);
+
 /* Launch schedule of eor_run_ionization / eor_likelihood (results do not depend on it):
  * group = radii per pencil launch (1..16), pairs = (walker, redshift) pairs in flight
  * (1..64; scratch memory grows with group * pairs), plane_threads = CTA size of the

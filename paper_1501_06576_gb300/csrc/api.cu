@@ -540,6 +540,36 @@ int eor_box_power_spectrum(eor_ctx* c, const float* box, double* d2, double* kme
     return finish(c, mem);
 }
 
+int eor_noise_sigma(eor_ctx* c, const double* mock_d2, const float* thermal, double model_frac, double* sigma,
+                    int mem) {
+    if (!c) return EOR_EINVAL;
+    if (!mock_d2 || !sigma || !valid_mem(mem) || !(model_frac >= 0.0) || !isfinite(model_frac))
+        return fail(c, EOR_EINVAL, "mock_d2/sigma NULL, bad mem or model_frac < 0");
+    const size_t zb = (size_t)c->cfg.n_z * c->cfg.n_bins;
+    double* buf = nullptr;     // mock, sums, sigma
+    float* th = nullptr;
+    if (!alloc_n(c, &buf, 3 * zb)) return fail(c, EOR_ENOMEM, "noise buffers");
+    int r = copy_in(c, buf, mock_d2, sizeof(double) * zb, mem);
+    if (!r && thermal) {
+        if (mem == EOR_DEVICE) {
+            th = const_cast<float*>(thermal);
+        } else if (!alloc_n(c, &th, (size_t)c->cfg.n_z * c->nspec)) {
+            r = fail(c, EOR_ENOMEM, "thermal noise buffer");
+        } else {
+            r = copy_in(c, th, thermal, sizeof(float) * c->cfg.n_z * c->nspec, mem);
+        }
+    }
+    if (!r) {
+        cudaError_t e = eor::launch_noise_sigma(c, buf, th, model_frac, buf + zb, buf + 2 * zb);
+        if (e != cudaSuccess) r = cuda_fail(c, e, "noise sigma");
+    }
+    if (!r) r = copy_out(c, sigma, buf + 2 * zb, sizeof(double) * zb, mem);
+    if (!r) r = finish(c, EOR_HOST);   // the scratch is freed below
+    if (thermal && mem == EOR_HOST) dev_free(c, th);
+    dev_free(c, buf);
+    return r;
+}
+
 int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     if (!c) return EOR_EINVAL;
     if (group < 1 || group > 16 || pairs < 1 || pairs > 64 || (plane_threads != 512 && plane_threads != 1024))

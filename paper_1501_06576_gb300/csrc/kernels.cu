@@ -814,6 +814,42 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     return cudaGetLastError();
 }
 
+// Inverse-weighted mode sums of the T+S equation: sums[z][b] += w / (N_i + mock[z][b])^2 over
+// the half-spectrum modes of bin b (w = 2 for 0 < kz < n/2: the conjugate mode, else 1).
+// Block-private FP64 bins in shared memory, then one global add per bin and block.
+__global__ void __launch_bounds__(256) k_noise_sums(int n, const signed char* bin, int n_bins, const double* mock,
+                                                    const float* thermal, double* sums) {
+    __shared__ double s[EOR21_MAX_BINS];
+    const int zi = blockIdx.y;
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) s[b] = 0.0;
+    __syncthreads();
+    const int nh = n / 2 + 1;
+    const long long total = (long long)nh * n * n;
+    const float* th = thermal ? thermal + (size_t)zi * total : nullptr;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(e / ((long long)n * n)), kx = (int)((e / n) % n), ky = (int)(e % n);
+        const int mx = signed_index(kx, n), my = signed_index(ky, n);
+        const int b = bin[mx * mx + my * my + kz * kz];
+        if (b < 0) continue;
+        const double w = (kz == 0 || kz == n / 2) ? 1.0 : 2.0;
+        const double d = (th ? (double)th[e] : 0.0) + mock[(size_t)zi * n_bins + b];
+        atomicAdd(&s[b], w / (d * d));
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x)
+        if (s[b] != 0.0) atomicAdd(&sums[(size_t)zi * n_bins + b], s[b]);
+}
+
+__global__ void k_noise_finish(const double* sums, const double* mock, const long long* nmodes, int n_bins, int count,
+                               double model_frac, double* sigma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int b = i % n_bins;
+    const double m = model_frac * mock[i];
+    sigma[i] = nmodes[b] > 0 ? sqrt(1.0 / sums[i] + m * m) : (double)NAN;
+}
+
 // Grid-size dispatch; the 128^3 plane kernels come in 512- and 1024-thread CTAs.
 #define EOR_DISPATCH(c, FN, ...)                                                            \
     switch ((c)->n) {                                                                       \
@@ -848,6 +884,22 @@ cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signe
         case 128: return box_ps_raw_n<128, 512>(box, spec, bins, sums, n_bins, kf3, pair_info, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_noise_sigma(eor_ctx* c, const double* mock, const float* thermal, double model_frac, double* sums,
+                               double* sigma) {
+    const int nb = c->cfg.n_bins, nz = c->cfg.n_z;
+    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * nz * nb, c->stream);
+    if (e != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_noise_sums<<<dim3(256, nz), 256, 0, c->stream>>>(c->n, c->d_bin_of_m2, nb, mock, thermal, sums);
+    trace_end(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_noise_finish<<<(nz * nb + 127) / 128, 128, 0, c->stream>>>(sums, mock, c->d_nmodes, nb, nz * nb, model_frac,
+                                                                 sigma);
+    trace_end(c);
+    return cudaGetLastError();
 }
 
 // The velocity-weighted brightness field of box zi (Sec. 2.2): k_z^2/k^2 delta_hat -> real

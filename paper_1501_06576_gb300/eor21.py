@@ -21,7 +21,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 # names exported by include/eor21.h
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_set_method", "eor_basis_info", "eor_trace",
+           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
            "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
@@ -107,6 +107,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_set_tuning": (I, [P, I, I, I]),
         "eor_set_method": (I, [P, I]),
         "eor_autotune": (I, [P, P, I, P, P, I, P, P, P, P, I]),
+        "eor_noise_sigma": (I, [P, P, P, D, P, I]),
         "eor_basis_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "eor_trace": (I, [P, I]),
         "eor_trace_read": (I, [P, P, P, I]),
@@ -339,6 +340,14 @@ class Context:
                                           ctypes.byref(p), ctypes.byref(t), ctypes.byref(ms), mem))
         return g.value, p.value, t.value, ms.value
 
+    def eor_noise_sigma(self, mock_d2, thermal=None, model_frac: float = 0.25) -> np.ndarray:
+        """Total uncertainty [n_z][n_bins] of mock spectra: T+S mode sum plus modelling error."""
+        pm, mem, _ = _arg(mock_d2, np.float64)
+        pt, _, kt = _arg(thermal, np.float32)
+        out = self._out(mem == EOR_DEVICE, (self.n_z, self.n_bins), np.float64)
+        self._check(self.lib.eor_noise_sigma(self.handle, pm, pt, float(model_frac), _arg(out, np.float64)[0], mem))
+        return out
+
     def eor_set_method(self, method: int):
         self._check(self.lib.eor_set_method(self.handle, int(method)))
 
@@ -378,6 +387,7 @@ class Context:
     set_tuning = eor_set_tuning
     set_method = eor_set_method
     autotune = eor_autotune
+    noise_sigma = eor_noise_sigma
     basis_info = eor_basis_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count
