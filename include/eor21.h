@@ -355,6 +355,15 @@ int eor_emu_set_threshold(eor_emu* emu, double tau);
 int eor_emu_likelihood(eor_emu* emu, eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2,
                        const double* sigma, double* chi2, double* d2, int* fallback, int mem);
 
+/* Where predictions (eor_emu_predict, eor_emu_calibrate, eor_emu_likelihood) run: 1 = the
+ * 5th-generation tensor cores (tcgen05 BF16 x BF16, FP32 accumulation; every layer input,
+ * activations included, rounded to BF16), the default when the network has 3 hidden layers
+ * of 256 and at most 16 bins; 0 = the FP32 units (BF16-rounded weights, FP32 activations,
+ * the arithmetic of training). EOR_ENOTSUP for 1 with another shape. eor_emu_inference
+ * gives the current choice. */
+int eor_emu_set_inference(eor_emu* emu, int tensor_cores);
+int eor_emu_inference(const eor_emu* emu);
+
 const char* eor_emu_last_error(const eor_emu* emu);
 void eor_emu_destroy(eor_emu* emu);
 

@@ -22,8 +22,11 @@
 #include <vector>
 
 #include "eor_internal.cuh"
+#include "tc.cuh"
 
 namespace {
+
+namespace tc = eor::tc;
 
 constexpr int kIn = 4;                                 // zeta, R_mfp, log10 T_vir, z
 constexpr int kMaxLayers = EOR21_EMU_MAX_HIDDEN + 1;
@@ -501,6 +504,202 @@ __global__ void k_emu_chi2(const double* pred, const int* fallback, int n_walker
     chi2[w] = acc;
 }
 
+// ------------------------------------------------------------------ tensor-core inference
+//
+// The 256-wide hidden layers as BF16 x BF16 tcgen05 MMAs (kind::f16, FP32 accumulation in
+// tensor memory): one CTA carries 128 rows of one member through the whole network, the
+// activations staying in shared memory as the next layer's A operand and the weights of
+// one layer at a time arriving by bulk copy. Operands are K-major without swizzle: an
+// 8-row x 16-byte core matrix holds 8 BF16 values along K; core (g, kc) of a 256-wide
+// operand sits at g * 4096 + kc * 128 bytes. Every layer input is rounded to BF16 (the
+// first, the four features, too), the products and sums are FP32.
+constexpr int kTcHidden = 256;                          // the only width this path serves
+constexpr uint32_t kTcSbo16 = (kTcHidden / 8) * 128;    // bytes between 8-row groups (4096)
+constexpr uint32_t kTcActBytes = 128 * kTcHidden * 2;   // activations of a tile (64 KB)
+constexpr uint32_t kTcWBytes = kTcHidden * kTcHidden * 2;  // one hidden layer's weights (128 KB)
+constexpr int kTcOutN = 16;                             // MMA N of the output layer (>= n_bins)
+constexpr uint32_t kTcW3Bytes = kTcOutN * kTcHidden * 2;   // output layer's weights (8 KB)
+constexpr uint32_t kTcMemberBytes = 2 * kTcWBytes + kTcW3Bytes;
+constexpr uint64_t kTcWaitNs = 2000000000ull;           // 2 s of GPU time per bounded wait
+
+__device__ __forceinline__ uint32_t core16(int row, int k) {
+    return (uint32_t)((row >> 3) * kTcSbo16 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Instruction descriptor of kind::f16 with BF16 operands and FP32 accumulation, K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+
+// Weights of hidden layers 1, 2 and the output layer of every member in the BF16 core-matrix
+// layout: [member][W1 | W2 | W3 padded to kTcOutN rows with zeros].
+__global__ void k_emu_format_tc(const float* wq, Layout lay, int members, unsigned char* out) {
+    const long long per = (long long)(2 * kTcHidden + kTcOutN) * kTcHidden;
+    const long long total = per * members;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(i / per);
+        const long long r = i % per;
+        const int layer = r < (long long)kTcHidden * kTcHidden ? 1 : (r < 2LL * kTcHidden * kTcHidden ? 2 : 3);
+        const long long rl = r - (long long)(layer - 1) * kTcHidden * kTcHidden;
+        const int o = (int)(rl / kTcHidden), k = (int)(rl % kTcHidden);
+        float v = 0.0f;
+        if (o < lay.fout[layer]) v = wq[(size_t)e * lay.n_params + lay.off_w[layer] + (size_t)o * kTcHidden + k];
+        unsigned char* base = out + (size_t)e * kTcMemberBytes + (size_t)(layer - 1) * kTcWBytes;
+        *reinterpret_cast<__nv_bfloat16*>(base + core16(o, k)) = __float2bfloat16_rn(v);
+    }
+}
+
+// Forward pass of 128 rows (blockIdx.x) of member blockIdx.y: layer 0 (4 inputs) on the FP32
+// units, hidden layers 1-2 and the output layer on the tensor cores. y [member][rows][n_out].
+__global__ void __launch_bounds__(128, 1) k_emu_infer_tc(const float* x, int rows, const float* wq, Layout lay,
+                                                         const unsigned char* wfmt, int n_out, float* y,
+                                                         long long ye, int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* As = sm;                        // activations, 64 KB
+    unsigned char* Bs = sm + kTcActBytes;          // weights of the current layer, 128 KB
+    uint64_t* barW = reinterpret_cast<uint64_t*>(Bs + kTcWBytes);
+    uint64_t* barD = barW + 1;
+    uint64_t* barF = barW + 2;   // final drain on the failure path
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(barW + 3);
+    const int t = threadIdx.x, warp = t >> 5, e = blockIdx.y;
+    const int row = blockIdx.x * 128 + t;
+    const float* w = wq + (size_t)e * lay.n_params;
+    const unsigned char* wm = wfmt + (size_t)e * kTcMemberBytes;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    if (t == 0) {
+        tc::mbar_init(barW, 1);
+        tc::mbar_init(barD, 1);
+        tc::mbar_init(barF, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    int owed = -1;   // thread 0: barW phase of a weight copy not yet seen to land
+    if (t == 0) {    // layer 1's weights arrive while layer 0 runs
+        tc::mbar_expect_tx(barW, kTcWBytes);
+        tc::bulk_g2s(Bs, wm, kTcWBytes, barW);
+        owed = 0;
+    }
+    // layer 0 on the FP32 units: h = GELU(W0 bf16(x) + b0), stored as BF16 (row t of the tile)
+    {
+        float xin[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            xin[c] = row < rows ? __bfloat162float(__float2bfloat16_rn(x[(size_t)row * 4 + c])) : 0.0f;
+        const float* w0 = w + lay.off_w[0];
+        const float* b0 = w + lay.off_b[0];
+        for (int o0 = 0; o0 < kTcHidden; o0 += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                float hv[2];
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    const int o = o0 + 2 * q + u;
+                    float z = b0[o];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) z = fmaf(w0[o * 4 + c], xin[c], z);
+                    hv[u] = gelu_f(z);
+                }
+                pk[q] = pack_bf16(hv[0], hv[1]);
+            }
+            *reinterpret_cast<uint4*>(As + core16(t, o0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int layer = 1; layer <= 3; layer++) {
+        const int n = layer == 3 ? kTcOutN : kTcHidden;
+        if (t == 0) {
+            ok = ok && tc::mbar_wait(barW, phase, kTcWaitNs);
+            if (ok) owed = -1;
+            if (ok) {
+                tc::fence_after_sync();
+                const uint32_t idesc = idesc_bf16(128, n);
+                for (int ks = 0; ks < kTcHidden / 16; ks++) {
+                    const uint64_t ad = tc::smem_desc(tc::smem_addr(As) + ks * 256, 128, kTcSbo16);
+                    const uint64_t bd = tc::smem_desc(tc::smem_addr(Bs) + ks * 256, 128, kTcSbo16);
+                    mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(barD);   // also when skipped: completes once the MMAs issued so far are done
+        }
+        const bool done = tc::mbar_wait(barD, phase, kTcWaitNs);
+        tc::fence_after_sync();
+        phase ^= 1u;
+        const bool good = __syncthreads_and(done && (t != 0 || ok));
+        if (!good) {
+            if (t == 0) atomicOr(err, 1);
+            break;
+        }
+        if (t == 0 && layer < 3) {   // the MMAs are done with B: the next layer's weights
+            const uint32_t bytes = layer == 1 ? kTcWBytes : kTcW3Bytes;
+            tc::mbar_expect_tx(barW, bytes);
+            tc::bulk_g2s(Bs, wm + (size_t)layer * kTcWBytes, bytes, barW);
+            owed = (int)phase;
+        }
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const float* bias = w + lay.off_b[layer];
+        if (layer < 3) {
+            for (int c0 = 0; c0 < kTcHidden; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_base + (uint32_t)c0, v);
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        pk[q] = pack_bf16(gelu_f(v[8 * g + 2 * q] + bias[c0 + 8 * g + 2 * q]),
+                                          gelu_f(v[8 * g + 2 * q + 1] + bias[c0 + 8 * g + 2 * q + 1]));
+                    *reinterpret_cast<uint4*>(As + core16(t, c0 + 8 * g)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        } else {
+            float v[16];
+            tc::tmem_ld16(lane_base, v);
+            if (row < rows)
+                for (int b = 0; b < n_out; b++) y[(size_t)e * ye + (size_t)row * n_out + b] = v[b] + bias[b];
+        }
+    }
+    // failure path: no MMA may run and no copy may land after the CTA is gone
+    if (t == 0) {
+        if (owed >= 0) tc::mbar_wait(barW, (uint32_t)owed, kTcWaitNs);
+        tc::mma_commit(barF);
+        tc::mbar_wait(barF, 0, kTcWaitNs);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+size_t emu_tc_smem() { return kTcActBytes + kTcWBytes + 3 * sizeof(uint64_t) + 16; }
+
 }  // namespace
 
 struct eor_emu {
@@ -531,6 +730,10 @@ struct eor_emu {
     cudaGraphExec_t step_graph = nullptr;
     int graph_batch = -1;
     cudaEvent_t ev_emu = nullptr, ev_sim = nullptr;
+    bool tc_ok = false;                  // the network's shape fits the tensor-core inference
+    bool use_tc = false;                 // predictions on the tensor cores (else the FP32 units)
+    unsigned char* d_wfmt = nullptr;     // BF16 core-matrix weights of every member
+    int* d_flag = nullptr;               // bit 0: a bounded tensor-core wait ran out
     std::string err;
 };
 
@@ -727,7 +930,20 @@ cudaError_t predict_device(eor_emu* m, int n_walkers) {
     const int rows = n_walkers * m->Z;
     k_emu_features<<<grid_for(rows, 128), 128, 0, m->stream>>>(m->d_params, n_walkers, m->fm, m->d_x);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward(m, m->d_x, 0, rows);
+    if (e == cudaSuccess) {
+        if (m->use_tc) {
+            const long long total = (long long)(2 * kTcHidden + kTcOutN) * kTcHidden * m->E;
+            k_emu_format_tc<<<grid_for(total, 256), 256, 0, m->stream>>>(m->d_wq, m->lay, m->E, m->d_wfmt);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                k_emu_infer_tc<<<dim3(grid_for(rows, 128), m->E), 128, emu_tc_smem(), m->stream>>>(
+                    m->d_x, rows, m->d_wq, m->lay, m->d_wfmt, m->B, m->d_y, out_stride(m), m->d_flag);
+                e = cudaGetLastError();
+            }
+        } else {
+            e = forward(m, m->d_x, 0, rows);
+        }
+    }
     if (e == cudaSuccess) {
         k_emu_combine<<<grid_for(n_walkers, 128), 128, 0, m->stream>>>(
             m->d_y, out_stride(m), m->E, n_walkers, m->Z, m->B, m->d_norm, m->d_params, m->fm,
@@ -782,7 +998,7 @@ void eor_emu_destroy(eor_emu* m) {
                     m->d_dy, m->d_da, m->d_db, m->d_loss, m->d_data_x, m->d_data_t, m->d_data_raw, m->d_norm,
                     m->d_state, m->d_params, m->d_d2in, m->d_pred, m->d_spread, m->d_score, m->d_err,
                     m->d_fallback, m->d_list, m->d_count, m->d_mock, m->d_chi2, m->d_d2out, m->d_fparams,
-                    m->d_fchi2, m->d_fd2};
+                    m->d_fchi2, m->d_fd2, m->d_wfmt, m->d_flag};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -866,6 +1082,18 @@ int eor_emu_create(const eor_emu_config* cfg, void* cuda_stream, eor_emu** out) 
     if (!ok) {
         eor_emu_destroy(m);
         return efail(nullptr, EOR_ENOMEM, "device allocation failed");
+    }
+    m->tc_ok = g.hidden == kTcHidden && g.n_hidden == 3 && g.n_bins <= kTcOutN;
+    if (m->tc_ok) {
+        if (!ealloc(&m->d_wfmt, (size_t)m->E * kTcMemberBytes) || !ealloc(&m->d_flag, 1) ||
+            cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream) != cudaSuccess ||
+            cudaFuncSetAttribute(k_emu_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu_tc_smem()) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            eor_emu_destroy(m);
+            return efail(nullptr, EOR_ENOMEM, "tensor-core inference buffers");
+        }
+        m->use_tc = true;
     }
     if (cudaEventCreateWithFlags(&m->ev_emu, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_sim, cudaEventDisableTiming) != cudaSuccess) {
@@ -1067,8 +1295,22 @@ int eor_emu_predict(eor_emu* m, const double* params, int n_walkers, double* log
     if (spread) EK(cudaMemcpyAsync(spread, m->d_spread, sizeof(double) * rows, kind_out(mem), m->stream), "copy");
     if (fallback)
         EK(cudaMemcpyAsync(fallback, m->d_fallback, sizeof(int) * n_walkers, kind_out(mem), m->stream), "copy");
-    return finish(m, mem);
+    r = finish(m, mem);
+    if (r || !m->use_tc || mem != EOR_HOST) return r;
+    int flag = 0;
+    EK(cudaMemcpy(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "flag");
+    return flag ? efail(m, EOR_ETIMEOUT, "a bounded tensor-core wait of the inference ran out") : EOR_OK;
 }
+
+int eor_emu_set_inference(eor_emu* m, int tensor_cores) {
+    if (!m) return EOR_EINVAL;
+    if (tensor_cores && !m->tc_ok)
+        return efail(m, EOR_ENOTSUP, "tensor-core inference needs 3 hidden layers of 256 and at most 16 bins");
+    m->use_tc = tensor_cores != 0;
+    return EOR_OK;
+}
+
+int eor_emu_inference(const eor_emu* m) { return m ? (m->use_tc ? 1 : 0) : -1; }
 
 int eor_emu_set_threshold(eor_emu* m, double tau) {
     if (!m) return EOR_EINVAL;

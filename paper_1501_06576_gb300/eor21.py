@@ -27,7 +27,8 @@ EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
            "eor_emu_forward", "eor_emu_loss_grad", "eor_emu_train_batch", "eor_emu_get_weights",
            "eor_emu_set_weights", "eor_emu_get_normalization", "eor_emu_set_normalization", "eor_emu_predict",
-           "eor_emu_calibrate", "eor_emu_set_threshold", "eor_emu_likelihood", "eor_emu_last_error",
+           "eor_emu_calibrate", "eor_emu_set_threshold", "eor_emu_likelihood", "eor_emu_set_inference",
+           "eor_emu_inference", "eor_emu_last_error",
            "eor_emu_destroy", "eor_mcmc_default_config", "eor_mcmc_create", "eor_mcmc_start", "eor_mcmc_run",
            "eor_mcmc_walkers", "eor_mcmc_last_error", "eor_mcmc_destroy")
 EMU_MAX_HIDDEN, EMU_MAX_MEMBERS = 8, 8
@@ -134,6 +135,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_emu_calibrate": (I, [P, P, P, I, D, P, P, I]),
         "eor_emu_set_threshold": (I, [P, D]),
         "eor_emu_likelihood": (I, [P, P, P, I, P, P, P, P, P, I]),
+        "eor_emu_set_inference": (I, [P, I]),
+        "eor_emu_inference": (I, [P]),
         "eor_emu_last_error": (ctypes.c_char_p, [P]),
         "eor_emu_destroy": (None, [P]),
         "eor_mcmc_default_config": (None, [ctypes.POINTER(McmcConfig)]),
@@ -555,6 +558,14 @@ class Emulator:
                                                 _arg(fb, np.int32)[0], mem))
         return chi2, d2, fb
 
+    def eor_emu_set_inference(self, tensor_cores: bool):
+        self._check(self.lib.eor_emu_set_inference(self.handle, 1 if tensor_cores else 0))
+
+    def eor_emu_inference(self) -> int:
+        return int(self.lib.eor_emu_inference(self.handle))
+
+    set_inference = eor_emu_set_inference
+    inference = eor_emu_inference
     set_data = eor_emu_set_data
     train = eor_emu_train
     forward = eor_emu_forward
