@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
     ap.add_argument("--mcmc-steps", type=int, default=10)
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
-    ap.add_argument("--emu-steps", type=int, default=16000, help="Adam steps of the surrogate")
+    ap.add_argument("--emu-steps", type=int, default=32000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
     return ap.parse_args()
 
