@@ -95,7 +95,7 @@ extern "C" int eor_tensor_core_check(const float* a, const float* b, float* d, i
 namespace eor {
 namespace {
 
-constexpr int kTcTiles = 2;                            // M tiles of 128 cells per CTA
+constexpr int kTcTiles = 2;                            // M tiles of 128 cells per CTA (their MMAs alternate)
 constexpr int kTcCells = 128 * kTcTiles;               // cells per CTA
 constexpr int kTcN = 128;                              // (walker, radius) columns per chunk (MMA N)
 constexpr int kTcStages = 3;                           // coefficient chunks in flight
@@ -108,15 +108,19 @@ constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chun
 constexpr int kGroupsPerChunk = kTcN / kGroup;
 constexpr uint32_t kMBytes = kGroupsPerChunk * 16;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
-constexpr uint32_t kTmemCols = 2 * kTcTiles * kTcN;       // 2 buffers x kTcTiles x kTcN columns (512)
-constexpr int kTcEpi = 2 * 128 * kTcTiles;               // epilogue threads: 2 per cell
+constexpr int kTmemBufs = 2;                              // accumulator buffers in tensor memory
+constexpr uint32_t kTmemCols = kTmemBufs * kTcTiles * kTcN;   // 2 buffers x kTcTiles x kTcN columns (512)
+constexpr int kEpiSets = 1;                               // epilogue warp sets, alternating chunks
+constexpr int kTcEpiSet = 2 * 128 * kTcTiles;             // threads of a set: 2 per cell
+constexpr int kTcEpi = kEpiSets * kTcEpiSet;              // epilogue threads
 constexpr int kTcThreads = 128 + kTcEpi;                  // warps 0-3: MMA (thread 0), copies (thread 32); then epilogue
 constexpr int kTcCtasPerSm = 1;                          // one CTA holds all tensor memory of an SM
 constexpr float kNever = 1.0e30f;                         // folded threshold that no delta_R reaches
 constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
-static_assert(2 * kTcTiles * kTcN <= (int)kTmemCols, "tensor memory");
+static_assert(kTmemCols <= 512, "tensor memory");
+static_assert(kTmemBufs % kEpiSets == 0, "a set always meets the same buffers");
 static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-static_assert(kTcEpi == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
+static_assert(kTcEpiSet == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
 static_assert(kTcN == 128 && kGroup == 32, "k_format_b: one block per chunk, one warp per group; 4 epilogue groups");
 
 // Basis fields -> the CTAs' A operands: [z][cta][hi/lo][tile][128 x 32 core-matrix layout]:
@@ -233,7 +237,8 @@ struct TcArgs {
 // buffers, so D(cell, column) = sum_b F_b c_b - threshold = delta_R - threshold. Each
 // walker's columns start on a group of 32: its R_cell column first (D = delta_R - delta_c),
 // then its radii from R_mfp down, then padding. Warps 4-19 run the epilogue of the other
-// buffer meanwhile, two threads per cell (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag
+// buffer meanwhile (kEpiSets = 1: one set takes every chunk), two threads per cell
+// (groups 0-1 and 2-3 of the chunk): the Eq. 1 flag
 // of a walker, "D >= 0 (sign bit clear) at some radius above R_cell", is an AND of sign bits
 // over its columns; at its last group the thread forms x_HI and delta T_b (coalesced stores)
 // and the warp adds its exact fixed-point x_HI sum to the pair's total.
@@ -254,9 +259,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
     uint64_t* barBe = barB + kTcStages;         // [kTcStages] its MMAs are done: stage free
     uint64_t* barM = barBe + kTcStages;         // [kTcStages] meta landed
     uint64_t* barMe = barM + kTcStages;         // [kTcStages] the epilogue has read it: stage free
-    uint64_t* barD = barMe + kTcStages;         // [2] MMAs into tensor-memory buffer done
-    uint64_t* barE = barD + 2;                  // [2] epilogue released the buffer
-    uint64_t* barF = barE + 2;                  // MMAs drained (abort path)
+    uint64_t* barD = barMe + kTcStages;         // [kTmemBufs] MMAs into tensor-memory buffer done
+    uint64_t* barE = barD + kTmemBufs;          // [kTmemBufs] epilogue released the buffer
+    uint64_t* barF = barE + kTmemBufs;          // MMAs drained (abort path)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(barF + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -274,11 +279,11 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             tc::mbar_init(barB + s, 1);
             tc::mbar_init(barBe + s, 1);
             tc::mbar_init(barM + s, 1);
-            tc::mbar_init(barMe + s, kTcEpi);
+            tc::mbar_init(barMe + s, kTcEpiSet);
         }
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < kTmemBufs; s++) {
             tc::mbar_init(barD + s, 1);
-            tc::mbar_init(barE + s, kTcEpi);
+            tc::mbar_init(barE + s, kTcEpiSet);
         }
         *abort = 0;
     }
@@ -322,11 +327,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
         if (!ok) record_timeout(a.err, 2, 1, 0);
         const uint32_t idesc = tc::idesc_tf32(128, kTcN);
         for (int c = 0; c < nch && ok; c++) {
-            const int st = c % kTcStages, tb = c & 1;
+            const int st = c % kTcStages, tb = c % kTmemBufs;
             ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
             if (!ok) { record_timeout(a.err, 2, 2, c); break; }
-            if (c >= 2)   // the epilogue of chunk c - 2 has released tensor-memory buffer tb
-                ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - 2) >> 1) & 1u, kTries, abort);
+            if (c >= kTmemBufs)   // the epilogue of chunk c - kTmemBufs has released buffer tb
+                ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - kTmemBufs) / kTmemBufs) & 1u, kTries,
+                                            abort);
             if (!ok) { record_timeout(a.err, 2, 7, c); break; }
             tc::fence_after_sync();
             // the tiles' accumulators alternate, so that consecutive MMAs are independent
@@ -355,16 +361,18 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
         }
         if (!ok) *abort = 1;
     } else if (warp >= 4 && nch > 0) {
-        // ---------------- epilogue warps: warp 4 + e owns tensor-memory lanes 32 (e % 4) .. + 31
-        // (the quarter its warp index allows) of tile (e / 4) % 2, and groups 2 (e / 8) and
-        // 2 (e / 8) + 1 of every chunk: one cell, half the columns. A walker never spans
-        // the two halves (multi-group walkers start on an even group).
-        const int e = warp - 4, lq = warp & 3, q = (e >> 2) % kTcTiles, g0 = 2 * ((e >> 2) / kTcTiles);
+        // ---------------- epilogue warps: set `set` (8 kTcTiles warps) takes the chunks
+        // c = set (mod kEpiSets); within it warp 4 + e owns tensor-memory lanes 32 (e % 4) ..
+        // + 31 (the quarter its warp index allows) of tile (ei / 4) % kTcTiles, and groups g0
+        // and g0 + 1 of its chunks: one cell, half the columns. A walker never spans the two
+        // halves (multi-group walkers start on an even group).
+        const int e = warp - 4, set = e / (8 * kTcTiles), ei = e % (8 * kTcTiles);
+        const int lq = warp & 3, q = (ei >> 2) % kTcTiles, g0 = 2 * ((ei >> 2) / kTcTiles);
         const long long cell = cell0 + q * 128 + lq * 32 + lane;
         const float dens = __ldg(a.delta + (size_t)zi * a.n3 + cell);
-        for (int c = 0; c < nch; c++) {
-            const int st = c % kTcStages, tb = c & 1;
-            const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(c >> 1) & 1u, kTries, abort);
+        for (int c = set; c < nch; c += kEpiSets) {
+            const int st = c % kTcStages, tb = c % kTmemBufs;
+            const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(c / kTmemBufs) & 1u, kTries, abort);
             const bool okM = okD && tc::mbar_wait_or_abort(barM + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
             if (!okM) {
                 if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, c);
@@ -492,7 +500,7 @@ int tc_slots(const eor_ctx* c) {
 bool basis_tc_fits(int rank) { return rank + 1 <= tc::kKMax; }   // basis values plus the constant column
 
 size_t basis_tc_smem() {
-    return kABytes + kTcStages * (kBBytes + kMBytes) + (4 * kTcStages + 6) * sizeof(uint64_t) + 16;
+    return kABytes + kTcStages * (kBBytes + kMBytes) + (4 * kTcStages + 2 * kTmemBufs + 2) * sizeof(uint64_t) + 16;
 }
 size_t basis_tc_a_bytes(long long n3, int n_z) { return (size_t)n_z * (size_t)(n3 / kTcCells) * kABytes; }
 size_t basis_tc_b_bytes(const eor_ctx* c) { return (size_t)c->cfg.n_z * (size_t)(tc_slots(c) / kTcN) * kChunkBytes; }
