@@ -86,6 +86,12 @@ typedef struct {
      * per-box field, formed once at eor_init_boxes. */
     int rsd;
     double rsd_max_dvdr;         /* 0.2 */
+    /* 1: eor_init_boxes takes its boxes as linear density fields and evolves each with the
+     * Zel'dovich approximation (Sec. 2.1): one unit-mass particle per cell displaced by
+     * psi = IDFT(i k / k^2 delta_hat) and deposited back by cloud-in-cell weights (FP32
+     * atomics: the evolved box can differ between loads in the last bits); the excursion set
+     * and delta T_b then use the evolved field. 0 (default): the boxes are used as given. */
+    int zeldovich;
 } eor_config;
 
 /* Defaults: n = 128, L = 250 Mpc, z = {8, 9, 10}, (h, Omega_m, Omega_b, n_s, sigma_8) =
@@ -149,6 +155,9 @@ int eor_likelihood(eor_ctx* ctx, const double* params, int n_walkers, const doub
  * up to EOR21_MAX_RADII) and their count, after eor_set_params. */
 int eor_filtered_density(eor_ctx* ctx, int z_index, double r_mpc, float* out, int mem);
 int eor_density_spectrum(eor_ctx* ctx, int z_index, float* out, int mem);
+/* The density box z_index the likelihood uses (the evolved one with zeldovich = 1),
+ * float [n][n][n]. */
+int eor_density_box(eor_ctx* ctx, int z_index, float* out, int mem);
 int eor_walker_ladder(eor_ctx* ctx, int walker, double* radii, int* n_radii);
 
 /* Power spectrum of any real box on the context's grid (Sec. 2.2 definition, the same

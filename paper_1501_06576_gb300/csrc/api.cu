@@ -198,6 +198,7 @@ void eor_default_config(eor_config* cfg) {
     cfg->r_mfp_max = 20.0;
     cfg->rsd = 0;
     cfg->rsd_max_dvdr = 0.2;
+    cfg->zeldovich = 0;
 }
 
 const char* eor_version(void) { return kVersion; }
@@ -245,6 +246,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
         return fail(nullptr, EOR_EINVAL, "dev_alloc and dev_free come together");
     if ((g.rsd != 0 && g.rsd != 1) || (g.rsd && !(g.rsd_max_dvdr > 0.0 && g.rsd_max_dvdr < 1.0)))
         return fail(nullptr, EOR_EINVAL, "rsd must be 0 or 1, with 0 < rsd_max_dvdr < 1");
+    if (g.zeldovich != 0 && g.zeldovich != 1) return fail(nullptr, EOR_EINVAL, "zeldovich must be 0 or 1");
 
     eor_ctx* c = new (std::nothrow) eor_ctx();
     if (!c) return fail(nullptr, EOR_ENOMEM, "host allocation");
@@ -337,20 +339,44 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
     if (!delta || !valid_mem(mem)) return fail(c, EOR_EINVAL, "delta is NULL or bad mem");
     int r = copy_in(c, c->d_delta, delta, sizeof(float) * c->cfg.n_z * c->n3, mem);
     if (r) return r;
+    float* zwork = nullptr;   // Zel'dovich displacement fields and deposit
+    if (c->cfg.zeldovich && !alloc_n(c, &zwork, 4 * c->n3)) return fail(c, EOR_ENOMEM, "Zel'dovich work space");
     for (int zi = 0; zi < c->cfg.n_z; zi++) {
-        cudaError_t e = eor::launch_forward_spectrum(c, zi);
-        if (e != cudaSuccess) return cuda_fail(c, e, "forward spectrum");
+        cudaError_t e;
+        if (c->cfg.zeldovich) {
+            // linear spectrum -> displaced particles -> evolved box, then its spectrum below
+            if ((e = eor::launch_forward_spectrum(c, zi)) != cudaSuccess ||
+                (e = eor::launch_zeldovich(c, zi, zwork)) != cudaSuccess) {
+                dev_free(c, zwork);
+                return cuda_fail(c, e, "Zel'dovich evolution");
+            }
+        }
+        e = eor::launch_forward_spectrum(c, zi);
+        if (e != cudaSuccess) { dev_free(c, zwork); return cuda_fail(c, e, "forward spectrum"); }
         if (c->cfg.rsd && (e = eor::launch_brightness_weight(c, zi)) != cudaSuccess)
+        {
+            dev_free(c, zwork);
             return cuda_fail(c, e, "velocity-gradient factor");
+        }
         // basis fields F_b = IDFT(phi_b delta_hat) of this box
         for (int b = 0; b < c->kb; b++) {
             e = eor::launch_filtered_density(c, zi, c->d_F + ((size_t)zi * c->kb + b) * c->n3,
                                              c->d_phi_m2 + (size_t)b * c->n_m2);
-            if (e != cudaSuccess) return cuda_fail(c, e, "basis fields");
+            if (e != cudaSuccess) {
+                dev_free(c, zwork);
+                return cuda_fail(c, e, "basis fields");
+            }
         }
     }
-    if (c->d_tcA) CK(eor::format_basis_tc(c), "tensor-core operands");
+    if (c->d_tcA) {
+        cudaError_t e = eor::format_basis_tc(c);
+        if (e != cudaSuccess) {
+            dev_free(c, zwork);
+            return cuda_fail(c, e, "tensor-core operands");
+        }
+    }
     r = finish(c, EOR_HOST);
+    dev_free(c, zwork);
     if (r) return r;
     c->stage = 1;
     return EOR_OK;
@@ -505,6 +531,15 @@ int eor_density_spectrum(eor_ctx* c, int z_index, float* out, int mem) {
     if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
     if (!out || !valid_mem(mem) || z_index < 0 || z_index >= c->cfg.n_z) return fail(c, EOR_EINVAL, "bad argument");
     int r = copy_out(c, out, c->d_spec + (size_t)z_index * c->nspec, sizeof(float2) * c->nspec, mem);
+    if (r) return r;
+    return finish(c, mem);
+}
+
+int eor_density_box(eor_ctx* c, int z_index, float* out, int mem) {
+    if (!c) return EOR_EINVAL;
+    if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
+    if (!out || !valid_mem(mem) || z_index < 0 || z_index >= c->cfg.n_z) return fail(c, EOR_EINVAL, "bad argument");
+    int r = copy_out(c, out, c->d_delta + (size_t)z_index * c->n3, sizeof(float) * c->n3, mem);
     if (r) return r;
     return finish(c, mem);
 }

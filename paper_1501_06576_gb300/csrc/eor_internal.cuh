@@ -210,6 +210,7 @@ cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float*
 cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab);
 cudaError_t launch_box_power_spectrum(eor_ctx* c, const float* box);
 cudaError_t launch_brightness_weight(eor_ctx* c, int zi);
+cudaError_t launch_zeldovich(eor_ctx* c, int zi, float* work);
 cudaError_t launch_noise_sigma(eor_ctx* c, const double* mock, const float* thermal, double model_frac, double* sums,
                                double* sigma);
 // the field multiplying T0 x_HI in delta T_b, minus 1: delta, or the velocity-weighted form

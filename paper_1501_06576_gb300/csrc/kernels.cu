@@ -902,6 +902,89 @@ cudaError_t launch_noise_sigma(eor_ctx* c, const double* mock, const float* ther
     return cudaGetLastError();
 }
 
+// Zel'dovich displacement along axis j of box zi in cells: i m_j / (kf |m|^2) delta_hat / dx, the
+// Nyquist index of axis j set to zero (an odd derivative has no Nyquist value).
+__global__ void k_za_weight(const float2* spec, int n, int axis, float inv_kf_dx, float2* out) {
+    const long long total = (long long)(n / 2 + 1) * n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(e / ((long long)n * n)), kx = (int)((e / n) % n), ky = (int)(e % n);
+        const int mx = signed_index(kx, n), my = signed_index(ky, n);
+        const int m2 = mx * mx + my * my + kz * kz;
+        const int mj = axis == 0 ? mx : (axis == 1 ? my : kz);
+        const bool nyq = axis == 2 ? kz == n / 2 : mj == -n / 2;
+        const float w = (m2 > 0 && !nyq) ? (float)mj * inv_kf_dx / (float)m2 : 0.0f;
+        const float2 v = spec[e];
+        out[e] = make_float2(-v.y * w, v.x * w);   // i w delta_hat
+    }
+}
+
+// Cloud-in-cell deposit of the unit-mass particle of every cell, displaced by psi [3][n^3]
+// (cells), periodic; rho must start at zero.
+__global__ void k_za_deposit(const float* psi, int n, float* rho) {
+    const long long n3 = (long long)n * n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const int qx = (int)(i / ((long long)n * n)), qy = (int)((i / n) % n), qz = (int)(i % n);
+        const float px = qx + psi[i], py = qy + psi[n3 + i], pz = qz + psi[2 * n3 + i];
+        const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+        const float tx = px - fx, ty = py - fy, tz = pz - fz;
+        const int ix = (((int)fx % n) + n) % n, iy = (((int)fy % n) + n) % n, iz = (((int)fz % n) + n) % n;
+#pragma unroll
+        for (int cx = 0; cx < 2; cx++)
+#pragma unroll
+            for (int cy = 0; cy < 2; cy++)
+#pragma unroll
+                for (int cz = 0; cz < 2; cz++) {
+                    const float w = (cx ? tx : 1.0f - tx) * (cy ? ty : 1.0f - ty) * (cz ? tz : 1.0f - tz);
+                    const long long j = ((long long)((ix + cx) % n) * n + (iy + cy) % n) * n + (iz + cz) % n;
+                    atomicAdd(rho + j, w);
+                }
+    }
+}
+
+__global__ void k_za_finish(const float* rho, long long n3, float* delta) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+        delta[i] = rho[i] - 1.0f;
+}
+
+// Zel'dovich evolution of box zi in place (its linear spectrum must be in d_spec): the three
+// displacement fields, the deposit, delta = rho - 1. work: 4 n^3 floats.
+cudaError_t launch_zeldovich(eor_ctx* c, int zi, float* work) {
+    cudaError_t e;
+    const size_t n3 = c->n3;
+    const double dx = c->cfg.box_mpc / c->n, kf = 2.0 * kPi / c->cfg.box_mpc;
+    if ((e = launch_window_table(c, 0.0, c->d_diag_wtab)) != cudaSuccess) return e;   // unit window
+    for (int axis = 0; axis < 3; axis++) {
+        trace_begin(c, kKOther);
+        k_za_weight<<<1024, 256, 0, c->stream>>>(c->d_spec + (size_t)zi * c->nspec, c->n, axis,
+                                                 (float)(1.0 / (kf * dx)), c->d_psinter);
+        trace_end(c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        float* out = work + (size_t)axis * n3;
+        switch (c->n) {
+            case 16: e = spectrum_to_box_n<16, 512>(c, c->d_psinter, out, c->d_diag_wtab); break;
+            case 32: e = spectrum_to_box_n<32, 512>(c, c->d_psinter, out, c->d_diag_wtab); break;
+            case 64: e = spectrum_to_box_n<64, 512>(c, c->d_psinter, out, c->d_diag_wtab); break;
+            case 128:
+                e = c->tune.plane_threads >= 1024 ? spectrum_to_box_n<128, 1024>(c, c->d_psinter, out, c->d_diag_wtab)
+                                                  : spectrum_to_box_n<128, 512>(c, c->d_psinter, out, c->d_diag_wtab);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    float* rho = work + 3 * n3;
+    if ((e = cudaMemsetAsync(rho, 0, sizeof(float) * n3, c->stream)) != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_za_deposit<<<2048, 256, 0, c->stream>>>(work, c->n, rho);
+    trace_end(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_za_finish<<<1024, 256, 0, c->stream>>>(rho, (long long)n3, c->d_delta + (size_t)zi * n3);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
 // The velocity-weighted brightness field of box zi (Sec. 2.2): k_z^2/k^2 delta_hat -> real
 // field g (scratch box) -> (1 + delta) / (1 + clip(-f g)) - 1 into d_bright.
 cudaError_t launch_brightness_weight(eor_ctx* c, int zi) {

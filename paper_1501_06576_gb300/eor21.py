@@ -21,7 +21,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 # names exported by include/eor21.h
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_trace",
+           "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
            "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
@@ -49,7 +49,7 @@ class EorConfig(ctypes.Structure):
                 ("k_hi", ctypes.c_double), ("chi2_k_lo", ctypes.c_double), ("chi2_k_hi", ctypes.c_double),
                 ("max_walkers", ctypes.c_int), ("r_mfp_max", ctypes.c_double),
                 ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p),
-                ("rsd", ctypes.c_int), ("rsd_max_dvdr", ctypes.c_double)]
+                ("rsd", ctypes.c_int), ("rsd_max_dvdr", ctypes.c_double), ("zeldovich", ctypes.c_int)]
 
 
 class EmuConfig(ctypes.Structure):
@@ -103,6 +103,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_likelihood": (I, [P, P, I, P, P, P, P, I]),
         "eor_filtered_density": (I, [P, I, D, P, I]),
         "eor_density_spectrum": (I, [P, I, P, I]),
+        "eor_density_box": (I, [P, I, P, I]),
         "eor_walker_ladder": (I, [P, I, P, ctypes.POINTER(I)]),
         "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
         "eor_set_tuning": (I, [P, I, I, I]),
@@ -312,6 +313,11 @@ class Context:
                                                   EOR_HOST))
         return out
 
+    def eor_density_box(self, z_index: int) -> np.ndarray:
+        out = np.empty((self.n,) * 3, dtype=np.float32)
+        self._check(self.lib.eor_density_box(self.handle, int(z_index), out.ctypes.data_as(ctypes.c_void_p), EOR_HOST))
+        return out
+
     def eor_walker_ladder(self, walker: int) -> np.ndarray:
         radii = np.zeros(MAX_RADII, dtype=np.float64)
         cnt = ctypes.c_int()
@@ -385,6 +391,7 @@ class Context:
     filtered_density = eor_filtered_density
     density_spectrum = eor_density_spectrum
     walker_ladder = eor_walker_ladder
+    density_box = eor_density_box
     box_power_spectrum = eor_box_power_spectrum
     trace = eor_trace
     set_tuning = eor_set_tuning
