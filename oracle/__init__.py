@@ -86,6 +86,13 @@ def _load():
                            _D, _D, _D, _P, _P, _P, _P]),
         "or_power_spectrum": (None, [_I, _D, _P, _I, _D, _D, _P, _P, _P]),
         "or_chi2": (_D, [_I, _D, _D, _D, _D, _P, _P, _P, _P]),
+        "or_dsigma2_dlnr": (_D, [ctypes.POINTER(_Cosmo), _D]),
+        "or_var_table_new": (_P, [ctypes.POINTER(_Cosmo), _D, _D, _D, _D]),
+        "or_var_table_free": (None, [_P]),
+        "or_var_s": (_D, [_P, _D, _P]),
+        "or_fcoll_pops": (_D, [_P, _P, _I, _D, _D, _D]),
+        "or_ionize_pops": (_I, [ctypes.POINTER(_Cosmo), ctypes.POINTER(_IonCfg), _I, _D, _D, _P, _P, _I,
+                                _D, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +225,70 @@ class Oracle:
             # delta T_b = T0 x_HI (1 + delta) H / (dv_r/dr + H) (Sec. 2.2)
             dtb = self.t0_mk(z) * xhi * self.rsd_weight(d, box_mpc, z, rsd_max_dvdr)
         return {"xhi": xhi, "flag": flag, "dtb": dtb, "xhi_mean": float(mean[0]), "n_radii": nr}
+
+    # mass-dependent efficiency (Sec. 5)
+    def dsigma2_dlnr(self, r: float) -> float:
+        return self.lib.or_dsigma2_dlnr(ctypes.byref(self._c), float(r))
+
+    def var_table(self, growth: float, m_lo: float, m_hi: float, dlnm: float = 0.03) -> "VarTable":
+        return VarTable(self, growth, m_lo, m_hi, dlnm)
+
+    def populations(self, model: int, params, extra, z: float) -> np.ndarray:
+        """Populations [n][5] = (zeta0, m_pivot, slope, m_lo, m_hi) of an efficiency model at z.
+        model 1: two populations zeta_i0 (M / 1e10 Msun)^alpha_i above their own M_min(T_vir,i):
+                 params = (zeta_10, R_mfp, log10 T_vir,1), extra = (alpha_1, zeta_20, alpha_2, log10 T_vir,2).
+        model 2: Sec. 5's feedback form in T_vir, zeta0 (T/T_F)^alpha for 10^4 K <= T < T_F and
+                 zeta0 (T/T_F)^beta above T_F; at fixed z T_vir ~ M^(2/3), so the mass slopes are
+                 2 alpha / 3 and 2 beta / 3: params = (zeta0, R_mfp, log10 T_F), extra = (alpha, beta, -, -)."""
+        if model == 1:
+            return np.array([[params[0], 1e10, extra[0], self.mmin(10.0 ** params[2], z), 0.0],
+                             [extra[1], 1e10, extra[2], self.mmin(10.0 ** extra[3], z), 0.0]], dtype=np.float64)
+        if model == 2:
+            m_f = self.mmin(10.0 ** params[2], z)
+            m_cool = self.mmin(1e4, z)
+            pops = []
+            if m_cool < m_f:
+                pops.append([params[0], m_f, 2.0 * extra[0] / 3.0, m_cool, m_f])
+            pops.append([params[0], m_f, 2.0 * extra[1] / 3.0, max(m_f, m_cool), 0.0])
+            return np.array(pops, dtype=np.float64)
+        raise ValueError("model must be 1 or 2")
+
+    def ionize_pops(self, delta: np.ndarray, box_mpc: float, z: float, pops: np.ndarray, r_mfp: float) -> dict:
+        d = np.ascontiguousarray(delta, dtype=np.float32)
+        p = np.ascontiguousarray(pops, dtype=np.float64).reshape(-1, 5)
+        n = d.shape[0]
+        xhi = np.empty(d.shape, dtype=np.float64)
+        flag = np.empty(d.shape, dtype=np.uint8)
+        dtb = np.empty(d.shape, dtype=np.float64)
+        mean = np.zeros(1, dtype=np.float64)
+        nr = self.lib.or_ionize_pops(ctypes.byref(self._c), ctypes.byref(self._ion), n, float(box_mpc), float(z),
+                                     _ptr(d), _ptr(p), p.shape[0], float(r_mfp), _ptr(xhi), _ptr(flag), _ptr(dtb),
+                                     _ptr(mean))
+        return {"xhi": xhi, "flag": flag, "dtb": dtb, "xhi_mean": float(mean[0]), "n_radii": nr}
+
+
+class VarTable:
+    """S(M) = D^2 sigma^2(R(M)) on a ln M grid (cubic Hermite) and the populations' collapsed
+    fraction over it (or_fcoll_pops)."""
+
+    def __init__(self, oracle: Oracle, growth: float, m_lo: float, m_hi: float, dlnm: float):
+        self._lib = oracle.lib
+        self._t = oracle.lib.or_var_table_new(ctypes.byref(oracle._c), float(growth), float(m_lo), float(m_hi),
+                                              float(dlnm))
+
+    def __del__(self):
+        if getattr(self, "_t", None):
+            self._lib.or_var_table_free(self._t)
+            self._t = None
+
+    def s(self, m: float) -> tuple[float, float]:
+        ds = np.zeros(1)
+        v = self._lib.or_var_s(self._t, float(np.log(m)), _ptr(ds))
+        return v, float(ds[0])
+
+    def fcoll(self, pops, m_r: float, delta_r: float, delta_c: float = 1.686) -> float:
+        p = np.ascontiguousarray(pops, dtype=np.float64).reshape(-1, 5)
+        return self._lib.or_fcoll_pops(self._t, _ptr(p), p.shape[0], float(m_r), float(delta_r), float(delta_c))
 
 
 # ---------------------------------------------------------------- free functions

@@ -169,6 +169,27 @@ static double integrate(or_fn f, const void* ctx, double a, double b, int panels
     return total;
 }
 
+/* Adaptive Simpson on [a, b] that also stops where a panel's estimate changes by less than
+ * rel of itself (so that rounding in a narrow peak cannot drive the recursion to its depth). */
+static double simpson_rel(or_fn f, const void* ctx, double a, double b, double fa, double fm, double fb,
+                          double whole, double eps, double rel, int depth) {
+    double m = 0.5 * (a + b);
+    double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = f(lm, ctx), frm = f(rm, ctx);
+    double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+    double delta = left + right - whole;
+    if (depth <= 0 || fabs(delta) <= 15.0 * eps || fabs(delta) <= rel * fabs(left + right))
+        return left + right + delta / 15.0;
+    return simpson_rel(f, ctx, a, m, fa, flm, fm, left, 0.5 * eps, rel, depth - 1) +
+           simpson_rel(f, ctx, m, b, fm, frm, fb, right, 0.5 * eps, rel, depth - 1);
+}
+
+static double integrate_rel(or_fn f, const void* ctx, double a, double b, double eps, double rel) {
+    double m = 0.5 * (a + b), fa = f(a, ctx), fm = f(m, ctx), fb = f(b, ctx);
+    return simpson_rel(f, ctx, a, b, fa, fm, fb, (b - a) / 6.0 * (fa + 4.0 * fm + fb), eps, rel, 40);
+}
+
 /* ---------------------------------------------------------------- cosmology */
 
 /* Bardeen, Bond, Kaiser & Szalay (1986), App. G: adiabatic CDM transfer function. */
@@ -320,6 +341,146 @@ double or_fcoll(double delta_r, double sigma2_min, double sigma2_r, double delta
     return erfc((delta_c - delta_r) / sqrt(2.0 * s2));
 }
 
+/* ------------------------------------------ mass-dependent efficiency (Sec. 5) */
+
+/* dW/dx of the top-hat transform: 3 (x^2 sin x - 3 sin x + 3 x cos x) / x^4. */
+static double tophat_dw(double x) {
+    if (fabs(x) < 0.05) {
+        double x2 = x * x;
+        return x * (-1.0 / 5.0 + x2 / 70.0 - x2 * x2 / 2520.0);
+    }
+    double s = sin(x), c = cos(x);
+    return 3.0 * (x * x * s - 3.0 * s + 3.0 * x * c) / (x * x * x * x);
+}
+
+/* d sigma^2 / d ln R integrand: k^3 P(k) 2 W(kR) W'(kR) kR / (2 pi^2), P without amplitude. */
+static double dsigma2_integrand(double lnk, const void* vctx) {
+    const sig_ctx* s = (const sig_ctx*)vctx;
+    double k = exp(lnk), x = k * s->r;
+    return k * k * k * pk_shape(s->c, k) * 2.0 * or_tophat_w(x) * tophat_dw(x) * x / (2.0 * OR_PI * OR_PI);
+}
+
+double or_dsigma2_dlnr(const or_cosmo* c, double r) {
+    sig_ctx s = {c, r};
+    const double a = log(1e-6), b = log(1e4);
+    double coarse = 0.0;   /* integral of |integrand| sets the absolute tolerance */
+    const int m = 4000;
+    for (int i = 0; i <= m; i++) {
+        double w = (i == 0 || i == m) ? 1.0 : (i % 2 ? 4.0 : 2.0);
+        coarse += w * fabs(dsigma2_integrand(a + (b - a) * i / m, &s));
+    }
+    coarse *= (b - a) / m / 3.0;
+    return c->amp * integrate(dsigma2_integrand, &s, a, b, 64, 1e-11 * coarse);
+}
+
+/* S(M) = D^2 sigma^2(R(M)) and dS/dln M = D^2 (d sigma^2/d ln R) / 3 on a uniform ln M grid,
+ * each node by the two quadratures above; or_var_s interpolates with cubic Hermite
+ * polynomials through the values and the derivatives. */
+or_var_table* or_var_table_new(const or_cosmo* c, double growth, double m_lo, double m_hi, double dlnm) {
+    or_var_table* t = (or_var_table*)calloc(1, sizeof(or_var_table));
+    t->lnm0 = log(m_lo);
+    t->n = (int)ceil((log(m_hi) - t->lnm0) / dlnm) + 1;
+    if (t->n < 2) t->n = 2;
+    t->dlnm = (log(m_hi) - t->lnm0) / (t->n - 1);
+    t->s = (double*)malloc(sizeof(double) * t->n);
+    t->ds = (double*)malloc(sizeof(double) * t->n);
+    double g2 = growth * growth;
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < t->n; i++) {
+        double r = or_mass_to_radius(c, exp(t->lnm0 + i * t->dlnm));
+        t->s[i] = g2 * or_sigma2(c, r);
+        t->ds[i] = g2 * or_dsigma2_dlnr(c, r) / 3.0;
+    }
+    return t;
+}
+
+void or_var_table_free(or_var_table* t) {
+    if (!t) return;
+    free(t->s);
+    free(t->ds);
+    free(t);
+}
+
+double or_var_s(const or_var_table* t, double lnm, double* dsdlnm) {
+    double u = (lnm - t->lnm0) / t->dlnm;
+    int i = (int)floor(u);
+    if (i < 0) i = 0;
+    if (i > t->n - 2) i = t->n - 2;
+    double x = u - i, h = t->dlnm;
+    double p0 = t->s[i], p1 = t->s[i + 1], m0 = t->ds[i] * h, m1 = t->ds[i + 1] * h;
+    double x2 = x * x, x3 = x2 * x;
+    if (dsdlnm)
+        *dsdlnm = ((6.0 * x2 - 6.0 * x) * p0 + (3.0 * x2 - 4.0 * x + 1.0) * m0 + (-6.0 * x2 + 6.0 * x) * p1 +
+                   (3.0 * x2 - 2.0 * x) * m1) / h;
+    return (2.0 * x3 - 3.0 * x2 + 1.0) * p0 + (x3 - 2.0 * x2 + x) * m0 + (-2.0 * x3 + 3.0 * x2) * p1 +
+           (x3 - x2) * m1;
+}
+
+/* S(lb - gap) - S(lb) for gap >= 0 without cancellation: for gaps below a quarter of the grid
+ * step both points use the cubic of lb's cell, whose Hermite basis differences factor as
+ * (u - v) = -gap / h times a polynomial; larger gaps subtract directly. */
+static double var_diff(const or_var_table* t, double lb, double gap) {
+    double h = t->dlnm;
+    if (gap >= 0.25 * h) return or_var_s(t, lb - gap, NULL) - or_var_s(t, lb, NULL);
+    int i = (int)floor((lb - t->lnm0) / h);
+    i = i < 0 ? 0 : (i > t->n - 2 ? t->n - 2 : i);
+    double x0 = t->lnm0 + i * h;
+    double v = (lb - x0) / h, u = v - gap / h;
+    double p0 = t->s[i], p1 = t->s[i + 1], m0 = t->ds[i] * h, m1 = t->ds[i + 1] * h;
+    double q = u * u + u * v + v * v, l = u + v;
+    return (-gap / h) * (p0 * (2.0 * q - 3.0 * l) + m0 * (q - 2.0 * l + 1.0) + p1 * (-2.0 * q + 3.0 * l) +
+                         m1 * (q - l));
+}
+
+static double pop_zeta(const or_pop* p, double m) { return p->zeta0 * pow(m / p->m_pivot, p->slope); }
+
+typedef struct {
+    const or_var_table* t;
+    const or_pop* p;
+    double top_lnm;   /* ln of the upper end of the mass range */
+    double lnm_r;     /* ln M_R, or 0 without a region (S_R = 0) */
+    double nu;        /* delta_c - delta_R > 0 */
+} pops_ctx;
+
+/* In x = ln(top / M): zeta(M) f(S(M) | delta_R, S_R) (-dS/d ln M), with the first-crossing
+ * distribution f(S) = nu / sqrt(2 pi) (S - S_R)^(-3/2) exp(-nu^2 / (2 (S - S_R))) of the
+ * extended Press-Schechter conditional mass function (Lacey & Cole 1993). */
+static double pops_integrand(double x, const void* v) {
+    const pops_ctx* c = (const pops_ctx*)v;
+    double lnm = c->top_lnm - x, ds;
+    double s = or_var_s(c->t, lnm, &ds);
+    double d = c->lnm_r != 0.0 ? var_diff(c->t, c->lnm_r, (c->lnm_r - c->top_lnm) + x) : s;
+    if (d <= 0.0) return 0.0;
+    double f = c->nu / sqrt(2.0 * OR_PI) * pow(d, -1.5) * exp(-c->nu * c->nu / (2.0 * d));
+    return pop_zeta(c->p, exp(lnm)) * f * (-ds);
+}
+
+double or_fcoll_pops(const or_var_table* t, const or_pop* pops, int n_pops, double m_r, double delta_r,
+                     double delta_c) {
+    double nu = delta_c - delta_r, total = 0.0;
+    for (int i = 0; i < n_pops; i++) {
+        const or_pop* p = &pops[i];
+        double hi = p->m_hi > 0.0 ? p->m_hi : exp(t->lnm0 + (t->n - 1) * t->dlnm);
+        if (nu <= 0.0) {   /* region collapsed into one halo of mass M_R */
+            if (m_r > 0.0 && m_r >= p->m_lo && (p->m_hi <= 0.0 || m_r < p->m_hi)) total += pop_zeta(p, m_r);
+            continue;
+        }
+        double top = m_r > 0.0 ? fmin(hi, m_r) : hi;
+        if (top <= p->m_lo) continue;
+        pops_ctx c = {t, p, log(top), m_r > 0.0 ? log(m_r) : 0.0, nu};
+        double span = log(top / p->m_lo);
+        double eps = 1e-12 * (pop_zeta(p, p->m_lo) + pop_zeta(p, top));
+        /* panels halving towards x = 0 (M -> top), where the integrand narrows as nu -> 0 */
+        double b = span;
+        for (int k = 0; k < 50; k++) {
+            double a = 0.5 * b;
+            total += integrate_rel(pops_integrand, &c, a, b, eps / 50.0, 1e-11);
+            b = a;
+        }
+    }
+    return total;
+}
+
 static double* forward_spectrum(int n, const float* delta) {
     size_t n3 = (size_t)n * n * n;
     double* spec = (double*)malloc(sizeof(double) * 2 * n3);
@@ -434,6 +595,98 @@ int or_ionize(const or_cosmo* c, const or_ion_cfg* cfg, int n, double box_mpc, d
     if (xhi_mean) *xhi_mean = sum / (double)n3;
 
     free(ion); free(f_cell); free(dr); free(work); free(spec); free(radii);
+    return nr;
+}
+
+/* Overdensities where zeta f_coll crosses 1 for one radius: a scan of nu = delta_c - delta_R
+ * from nu_max down (geometric, 400 points, then nu = 0, where F is the collapsed value),
+ * each sign change of F - 1 refined by bisection. Returns the count (<= cap), roots as
+ * delta values in increasing order of nu, i.e. decreasing delta. */
+static int pops_roots(const or_var_table* t, const or_pop* pops, int n_pops, double m_r, double delta_c,
+                      double nu_max, double* roots, int cap) {
+    const int m = 400;
+    int count = 0;
+    double nu_prev = nu_max;
+    double g_prev = or_fcoll_pops(t, pops, n_pops, m_r, delta_c - nu_prev, delta_c) - 1.0;
+    for (int k = 1; k <= m + 1; k++) {
+        double nu = k <= m ? nu_max * pow(1e-10, (double)k / m) : 0.0;
+        double g = or_fcoll_pops(t, pops, n_pops, m_r, delta_c - nu, delta_c) - 1.0;
+        if ((g >= 0.0) != (g_prev >= 0.0)) {
+            double lo = nu, hi = nu_prev;   /* g(lo) and g(hi) differ in sign */
+            double glo = g;
+            for (int it = 0; it < 200 && hi - lo > 1e-15 * (1.0 + hi); it++) {
+                double mid = 0.5 * (lo + hi);
+                double gm = or_fcoll_pops(t, pops, n_pops, m_r, delta_c - mid, delta_c) - 1.0;
+                if ((gm >= 0.0) == (glo >= 0.0)) { lo = mid; glo = gm; } else hi = mid;
+            }
+            if (count < cap) roots[count] = delta_c - 0.5 * (lo + hi);
+            count++;
+        }
+        nu_prev = nu;
+        g_prev = g;
+    }
+    return count;
+}
+
+int or_ionize_pops(const or_cosmo* c, const or_ion_cfg* cfg, int n, double box_mpc, double z,
+                   const float* delta, const or_pop* pops, int n_pops, double r_mfp,
+                   double* xhi, uint8_t* flag, double* dtb, double* xhi_mean) {
+    size_t n3 = (size_t)n * n * n;
+    int nr = or_radius_ladder(cfg, n, box_mpc, r_mfp, NULL, 0);
+    double* radii = (double*)malloc(sizeof(double) * nr);
+    or_radius_ladder(cfg, n, box_mpc, r_mfp, radii, nr);
+    double g = or_growth(c, z);
+    double rho = or_rho_mean(c);
+    double m_lo = INFINITY;
+    for (int i = 0; i < n_pops; i++) m_lo = fmin(m_lo, pops[i].m_lo);
+    double m_top = 4.0 / 3.0 * OR_PI * radii[0] * radii[0] * radii[0] * rho;
+    or_var_table* t = or_var_table_new(c, g, 0.25 * m_lo, 4.0 * m_top, 0.03);
+
+    double* spec = forward_spectrum(n, delta);
+    double* work = (double*)malloc(sizeof(double) * 2 * n3);
+    double* dr = (double*)malloc(sizeof(double) * n3);
+    uint8_t* ion = (uint8_t*)calloc(n3, 1);
+    double roots[64];
+
+    for (int j = 0; j < nr; j++) {
+        double r = radii[j];
+        double m_r = 4.0 / 3.0 * OR_PI * r * r * r * rho;
+        filter_from_spectrum(n, box_mpc, spec, r, work, dr);
+        double s_r = or_var_s(t, log(m_r), NULL);
+        double ds = or_var_s(t, log(m_lo), NULL) - s_r;
+        double nu_max = ds > 0.0 ? 12.0 * sqrt(2.0 * ds) : 1.0;
+        int nroot = pops_roots(t, pops, n_pops, m_r, cfg->delta_c, nu_max, roots, 64);
+        if (nroot > 64) nroot = 64;
+        double f_top = or_fcoll_pops(t, pops, n_pops, m_r, cfg->delta_c, cfg->delta_c);
+        int last = (j == nr - 1);
+        /* Eq. 1 per cell: zeta f_coll >= 1, i.e. an odd number of crossings at or above delta_R */
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)n3; i++) {
+            int on;
+            if (dr[i] >= cfg->delta_c) {
+                on = f_top >= 1.0;
+            } else {
+                int above = 0;
+                for (int q = 0; q < nroot; q++) above += roots[q] <= dr[i];
+                on = above & 1;
+            }
+            if (on) ion[i] = 1;
+            if (last) work[i] = ion[i] ? 1.0 : fmin(1.0, or_fcoll_pops(t, pops, n_pops, m_r, dr[i], cfg->delta_c));
+        }
+    }
+
+    double t0 = or_t0_mk(c, z);
+    double sum = 0.0;
+    for (size_t i = 0; i < n3; i++) {
+        double x = 1.0 - work[i];   /* partial ionization at R_cell, 1 where flagged */
+        if (xhi) xhi[i] = x;
+        if (flag) flag[i] = ion[i];
+        if (dtb) dtb[i] = t0 * x * (1.0 + (double)delta[i]);
+        sum += x;
+    }
+    if (xhi_mean) *xhi_mean = sum / (double)n3;
+    or_var_table_free(t);
+    free(ion); free(dr); free(work); free(spec); free(radii);
     return nr;
 }
 

@@ -30,6 +30,12 @@
  *                            plane-wave closed form, x_HI in [0,1], monotone in zeta and T_vir
  *   or_power_spectrum        plane-wave single-bin closed form, Parseval, GRF P(k) recovery
  *   or_chi2                  closed-form bin selection (bins 2..11) and unit contributions
+ *   or_dsigma2_dlnr          central differences of or_sigma2
+ *   or_var_table / or_var_s  exact or_sigma2 at off-grid masses
+ *   or_fcoll_pops            slope 0: zeta erfc (or_fcoll); a split mass range adds up to the
+ *                            whole; delta_R -> delta_c: zeta(M_R); a pure power-law spectrum
+ *                            without a region: the incomplete-gamma closed form
+ *   or_ionize_pops           one slope-0 population: or_ionize's flags and x_HI
  *   or_bbks_transfer         parity unpinned beyond its q -> 0 limit: the coefficients are
  *                            Bardeen et al. (1986) App. G, which the paper does not print.
  */
@@ -83,6 +89,40 @@ double or_r_cell(const or_ion_cfg* cfg, int n, double box_mpc);
 
 /* Conditional collapsed fraction of Eq. 1 for one smoothed overdensity. */
 double or_fcoll(double delta_r, double sigma2_min, double sigma2_r, double delta_c);
+
+/* Mass-dependent ionizing efficiency (Sec. 5): a population of sources with
+ * zeta(M) = zeta0 (M / m_pivot)^slope for m_lo <= M < m_hi (m_hi <= 0: no upper limit). */
+typedef struct {
+    double zeta0, m_pivot, slope, m_lo, m_hi;
+} or_pop;
+
+/* S(M) = D^2 sigma^2(R(M)) and dS/d ln M on a uniform ln M grid at one redshift (growth D),
+ * interpolated by cubic Hermite polynomials. */
+typedef struct {
+    int n;
+    double lnm0, dlnm;
+    double* s;
+    double* ds;
+} or_var_table;
+
+double or_dsigma2_dlnr(const or_cosmo* c, double r);      /* d sigma^2 / d ln R at z = 0 */
+or_var_table* or_var_table_new(const or_cosmo* c, double growth, double m_lo, double m_hi, double dlnm);
+void   or_var_table_free(or_var_table* t);
+double or_var_s(const or_var_table* t, double lnm, double* dsdlnm);
+
+/* sum_i Int zeta_i(M) dn/dM(M | delta_R, M_R) M / rho dM over population i's mass range below
+ * M_R, with the extended Press-Schechter conditional mass function (first-crossing form);
+ * delta_R >= delta_c gives sum_i zeta_i(M_R) over populations whose range holds M_R.
+ * m_r <= 0: no region (S_R = 0; the unconditional fraction, delta_R < delta_c only). */
+double or_fcoll_pops(const or_var_table* t, const or_pop* pops, int n_pops, double m_r, double delta_r,
+                     double delta_c);
+
+/* or_ionize with the populations' efficiency: flagged where the efficiency-weighted
+ * collapsed fraction reaches 1 at some radius; partial ionization min(1, that fraction) at
+ * R_cell. */
+int    or_ionize_pops(const or_cosmo* c, const or_ion_cfg* cfg, int n, double box_mpc, double z,
+                      const float* delta, const or_pop* pops, int n_pops, double r_mfp,
+                      double* xhi, uint8_t* flag, double* dtb, double* xhi_mean);
 
 /* delta_R = IDFT(W(kR) DFT(delta)) / n^3 for one radius; out: n^3 doubles. */
 void   or_filter_box(int n, double box_mpc, const float* delta, double r, double* out);
