@@ -92,6 +92,22 @@ typedef struct {
      * atomics: the evolved box can differ between loads in the last bits); the excursion set
      * and delta T_b then use the evolved field. 0 (default): the boxes are used as given. */
     int zeldovich;
+    /* Ionizing efficiency. 0 (default): the step function of Sec. 3, zeta for every halo
+     * above M_min(T_vir). 1 and 2: a mass-dependent efficiency (Sec. 5), Eq. 1 applied to
+     * the efficiency-weighted collapsed fraction
+     *     F(delta_R) = sum_i Int zeta_i(M) dn/dM(M | delta_R, R) M / rho dM
+     * over each population's mass range below M_R = 4 pi R^3 rho / 3, with the extended
+     * Press-Schechter conditional mass function (first-crossing form; F = sum_i zeta_i(M_R)
+     * once delta_R >= delta_c); x_HII = min(1, F) at R_cell. Per walker the params of
+     * eor_set_params and four numbers q of eor_set_efficiency:
+     *   1: two populations zeta_i0 (M / 1e10 Msun)^alpha_i above M_min(T_vir,i):
+     *      params (zeta_10, R_mfp, log10 T_vir,1), q (alpha_1, zeta_20, alpha_2, log10 T_vir,2);
+     *   2: Sec. 5's feedback form zeta0 (T_vir / T_F)^alpha for 10^4 K <= T_vir < T_F and
+     *      zeta0 (T_vir / T_F)^beta above T_F, mass slopes 2 alpha / 3 and 2 beta / 3 (T_vir ~
+     *      M^(2/3) at fixed z): params (zeta0, R_mfp, log10 T_F), q (alpha, beta, 0, 0).
+     * Per (walker, redshift, radius) FP64 on the GPU: the delta_R where F = 1 (Eq. 1 holds on
+     * the interval between them), and at R_cell a table of F in delta_R. */
+    int efficiency_model;
 } eor_config;
 
 /* Defaults: n = 128, L = 250 Mpc, z = {8, 9, 10}, (h, Omega_m, Omega_b, n_s, sigma_8) =
@@ -119,6 +135,13 @@ int eor_init_boxes(eor_ctx* ctx, const float* delta, int mem);
  * the overdensity at which zeta f_coll = 1 (Eq. 1); and per radius the FP32 top-hat
  * window W(kR) on the grid. */
 int eor_set_params(eor_ctx* ctx, const double* params, int n_walkers, int mem);
+
+/* Efficiency parameters of the walkers (efficiency_model 1 or 2; EOR_ESTATE otherwise):
+ * q double [n_walkers][4] as eor_config.efficiency_model describes, host (mem EOR_HOST) or
+ * device memory; copied. They stay in force for later eor_set_params / eor_likelihood calls
+ * of up to n_walkers walkers (EOR_ESTATE for more). EOR_EINVAL for non-finite values,
+ * |alpha| > 10, zeta_20 < 0 or log10 T_vir,2 outside (0, 12). */
+int eor_set_efficiency(eor_ctx* ctx, const double* q, int n_walkers, int mem);
 
 /* Excursion-set ionization (Eq. 1 and the partial ionization at R_cell of Sec. 2.1) of
  * every (walker, redshift): for each radius, filter the density spectrum with W(kR),

@@ -105,6 +105,9 @@ int check_device_error(eor_ctx* c) {
                                                          "(zeta > 0, 0 < R_mfp <= r_mfp_max, 0 < log10 T_vir < 12)");
     if (err & eor::kErrLadder) return fail(c, EOR_EINVAL, "radius ladder longer than the tables (raise r_mfp_max)");
     if (err & eor::kErrSigmaRange) return fail(c, EOR_EINVAL, "radius or halo mass outside the sigma^2 table range");
+    if (err & eor::kErrShape)
+        return fail(c, EOR_ENOTSUP, "mass-dependent efficiency: zeta f_coll crosses 1 more than twice in delta_R "
+                                    "(Eq. 1 is then not one interval; not supported)");
     if (err & eor::kErrTimeout) {
         char where[96];
         snprintf(where, sizeof(where), " (first: role %d, barrier %d, chunk %d)", (words[1] >> 28) & 15,
@@ -199,6 +202,7 @@ void eor_default_config(eor_config* cfg) {
     cfg->rsd = 0;
     cfg->rsd_max_dvdr = 0.2;
     cfg->zeldovich = 0;
+    cfg->efficiency_model = 0;
 }
 
 const char* eor_version(void) { return kVersion; }
@@ -247,6 +251,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     if ((g.rsd != 0 && g.rsd != 1) || (g.rsd && !(g.rsd_max_dvdr > 0.0 && g.rsd_max_dvdr < 1.0)))
         return fail(nullptr, EOR_EINVAL, "rsd must be 0 or 1, with 0 < rsd_max_dvdr < 1");
     if (g.zeldovich != 0 && g.zeldovich != 1) return fail(nullptr, EOR_EINVAL, "zeldovich must be 0 or 1");
+    if (g.efficiency_model < 0 || g.efficiency_model > 2)
+        return fail(nullptr, EOR_EINVAL, "efficiency_model must be 0, 1 or 2");
 
     eor_ctx* c = new (std::nothrow) eor_ctx();
     if (!c) return fail(nullptr, EOR_ENOMEM, "host allocation");
@@ -319,6 +325,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
              alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
              alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
     if (ok && g.rsd) ok = alloc_n(c, &c->d_bright, (size_t)Z * c->n3);
+    if (ok && g.efficiency_model)
+        ok = alloc_n(c, &c->d_effp, 4 * (size_t)W) && alloc_n(c, &c->d_ftab, pairs * eor::kFTab);
     if (!ok) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");
@@ -382,6 +390,29 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
     return EOR_OK;
 }
 
+int eor_set_efficiency(eor_ctx* c, const double* q, int n_walkers, int mem) {
+    if (!c) return EOR_EINVAL;
+    if (!c->cfg.efficiency_model) return fail(c, EOR_ESTATE, "efficiency_model is 0: no efficiency parameters");
+    if (!q || !valid_mem(mem) || n_walkers < 1 || n_walkers > c->cfg.max_walkers)
+        return fail(c, EOR_EINVAL, "q NULL, bad mem or n_walkers outside 1..max_walkers");
+    if (mem == EOR_HOST) {
+        for (int w = 0; w < n_walkers; w++) {
+            const double* v = q + 4 * w;
+            bool ok = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]) && fabs(v[0]) <= 10.0;
+            if (c->cfg.efficiency_model == 1) ok = ok && fabs(v[2]) <= 10.0 && v[1] >= 0.0 && v[3] > 0.0 && v[3] < 12.0;
+            else ok = ok && fabs(v[1]) <= 10.0;
+            if (!ok)
+                return fail(c, EOR_EINVAL, "efficiency parameter non-finite or out of range (|alpha| <= 10, "
+                                           "zeta_20 >= 0, 0 < log10 T_vir,2 < 12)");
+        }
+    }
+    int r = copy_in(c, c->d_effp, q, sizeof(double) * 4 * n_walkers, mem);
+    if (r) return r;
+    c->eff_walkers = n_walkers;
+    if (c->stage > 1) c->stage = 1;   // the tables follow at the next eor_set_params
+    return EOR_OK;
+}
+
 int eor_set_params(eor_ctx* c, const double* params, int n_walkers, int mem) {
     if (!c) return EOR_EINVAL;
     trace_reset(c);
@@ -389,6 +420,8 @@ int eor_set_params(eor_ctx* c, const double* params, int n_walkers, int mem) {
     if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
     if (!params || !valid_mem(mem) || n_walkers < 1 || n_walkers > c->cfg.max_walkers)
         return fail(c, EOR_EINVAL, "params NULL, bad mem or n_walkers outside 1..max_walkers");
+    if (c->cfg.efficiency_model && n_walkers > c->eff_walkers)
+        return fail(c, EOR_ESTATE, "eor_set_efficiency for these walkers first");
     int r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem);
     if (r) return r;
     CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream), "memset");
@@ -469,6 +502,8 @@ int eor_likelihood(eor_ctx* c, const double* params, int n_walkers, const double
     if (!params || !mock_d2 || !sigma || !chi2 || !valid_mem(mem) || n_walkers < 1 ||
         n_walkers > c->cfg.max_walkers)
         return fail(c, EOR_EINVAL, "NULL argument, bad mem or n_walkers outside 1..max_walkers");
+    if (c->cfg.efficiency_model && n_walkers > c->eff_walkers)
+        return fail(c, EOR_ESTATE, "eor_set_efficiency for these walkers first");
     const size_t zb = (size_t)c->cfg.n_z * c->cfg.n_bins;
     int r;
     if ((r = copy_in(c, c->d_params, params, sizeof(double) * 3 * n_walkers, mem))) return r;

@@ -222,6 +222,7 @@ struct BasisArgs {
     float* dtb;                 // [pair][n3]
     float* xhi_out;             // optional [pair][n3]
     float* xpart;               // [pair][n3 / kTC] per-CTA neutral-fraction sums
+    const float* ftab;          // [pair][kFTab] with a mass-dependent efficiency, else nullptr
     int n_walkers, n_z, max_radii;
     long long n3;
     float delta_c;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kBThreads) k_basis_ionize(BasisArgs a) {
         }
         if (t < nw) {
             const PairInfo& pi = a.pairs[(size_t)(w0 + t) * a.n_z + zi];
-            Wc[t] = WalkerConst{pi.zeta, pi.t0, pi.inv_sqrt2s2_cell, pi.cell_ok};
+            Wc[t] = WalkerConst{pi.zeta, pi.t0, a.ftab ? pi.f_inv_h : pi.inv_sqrt2s2_cell, pi.cell_ok};
         }
         __syncthreads();
         const int ncols = Off[nw];
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kBThreads) k_basis_ionize(BasisArgs a) {
             rec[KB] = a.pairs[(size_t)(w0 + wl) * a.n_z + zi].delta_crit[j];
             rec[KB + 1] = (j == n_r - 1) ? 1.0f : 0.0f;
             rec[KB + 2] = (float)wl;
-            rec[KB + 3] = 0.0f;
+            rec[KB + 3] = a.pairs[(size_t)(w0 + wl) * a.n_z + zi].delta_hi[j];
         }
         __syncthreads();
         bool fl[kCPL] = {false, false};
@@ -312,17 +313,19 @@ __global__ void __launch_bounds__(kBThreads) k_basis_ionize(BasisArgs a) {
             }
 #pragma unroll
             for (int ci = 0; ci < kCPL; ci++) acc[ci] += acc2[ci];
-            const float4 tail = *reinterpret_cast<const float4*>(rec + KB);   // threshold, last, slot
+            const float4 tail = *reinterpret_cast<const float4*>(rec + KB);   // threshold, last, slot, upper
 #pragma unroll
-            for (int ci = 0; ci < kCPL; ci++) fl[ci] |= acc[ci] >= tail.x;
+            for (int ci = 0; ci < kCPL; ci++) fl[ci] |= acc[ci] >= tail.x && acc[ci] <= tail.w;
             if (tail.y != 0.0f) {   // R_cell of walker `slot`: same column for the whole block
                 const int wl = (int)tail.z;
                 const WalkerConst w = Wc[wl];
+                const float* tab = a.ftab ? a.ftab + ((size_t)(w0 + wl) * a.n_z + zi) * kFTab : nullptr;
                 float xh[kCPL], xsum = 0.0f;
 #pragma unroll
                 for (int ci = 0; ci < kCPL; ci++) {
                     float fc = 0.0f;
-                    if (w.cell_ok > 0.5f) fc = acc[ci] >= a.delta_c ? 1.0f : erfcf((a.delta_c - acc[ci]) * w.inv);
+                    if (tab) fc = pop_table_f(tab, a.delta_c - acc[ci], w.inv);   // efficiency-weighted f_coll
+                    else if (w.cell_ok > 0.5f) fc = acc[ci] >= a.delta_c ? 1.0f : erfcf((a.delta_c - acc[ci]) * w.inv);
                     xh[ci] = fl[ci] ? 0.0f : 1.0f - fminf(1.0f, w.zeta * fc);
                     xsum += xh[ci];
                     fl[ci] = false;
@@ -486,7 +489,7 @@ cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
     if (c->tune.method == kMethodBasis && basis_tc_fits(c->basis_rank)) return launch_basis_ionize_tc(c, xhi_out);
-    BasisArgs a{c->d_F, c->d_coef, c->d_pairs, brightness_base(c), c->d_dtb, xhi_out, c->d_xpart, c->n_walkers, n_z,
+    BasisArgs a{c->d_F, c->d_coef, c->d_pairs, brightness_base(c), c->d_dtb, xhi_out, c->d_xpart, pop_tables(c), c->n_walkers, n_z,
                 c->max_radii, (long long)c->n3, (float)c->cfg.delta_c};
     const size_t smem = basis_ionize_smem(c->kb, c->max_radii);
     const int parts = (int)(c->n3 / kTC);

@@ -20,6 +20,7 @@ constexpr int kBasisCand = 512;            // candidate radii of the filter basi
 constexpr int kBasisMax = 48;              // largest filter basis
 constexpr double kBasisTol = 1e-6;         // max |W - projection| over candidates and |k| (FP32 level)
 constexpr int kCoefGrid = 8192;            // uniform R grid of the basis coefficient table
+constexpr int kFTab = 2048;                // entries of a walker's partial-ionization table in nu
 
 // Device error word bits (set by kernels, read by the host).
 enum : int {
@@ -27,6 +28,7 @@ enum : int {
     kErrSigmaRange = 2,   // a radius outside the sigma^2 table
     kErrParam = 4,        // non-finite or out-of-range walker parameter
     kErrTimeout = 8,      // a bounded tensor-core wait ran out
+    kErrShape = 16,       // a mass-dependent efficiency whose zeta f_coll crosses 1 more than twice
 };
 
 // Per (walker, redshift): everything the fused kernels need.
@@ -36,8 +38,22 @@ struct PairInfo {
     float t0;                // brightness prefactor T0(z) [mK]
     float inv_sqrt2s2_cell;  // 1 / sqrt(2 (sigma^2_min - sigma^2(R_cell))) or 0 when <= 0
     float cell_ok;           // 1 when R_cell's mass exceeds M_min, else 0
+    float f_inv_h;           // > 0: partial ionization from the pair's table in nu (step 1 / f_inv_h)
+    float pad2[3];
     float delta_crit[kMaxRadii];   // delta_R >= delta_crit  <=>  zeta f_coll >= 1 (+inf: never)
+    float delta_hi[kMaxRadii];     // ... and delta_R <= delta_hi (+inf except for a falling efficiency)
 };
+
+// Efficiency-weighted collapsed fraction at nu = delta_c - delta_R from a pair's table
+// (kFTab values at nu = i / inv_h; nu <= 0: the collapsed-region value in entry 0).
+__device__ __forceinline__ float pop_table_f(const float* tab, float nu, float inv_h) {
+    if (!(nu > 0.0f)) return __ldg(tab);
+    const float x = nu * inv_h;
+    if (x >= (float)(kFTab - 1)) return __ldg(tab + kFTab - 1);
+    const int i = (int)x;
+    const float a = __ldg(tab + i), b = __ldg(tab + i + 1);
+    return fmaf(x - (float)i, b - a, a);
+}
 
 // Per walker (FP64 ladder, kept for diagnostics).
 struct WalkerInfo {
@@ -98,6 +114,9 @@ struct eor_ctx {
     long long* d_nmodes = nullptr;   // [n_bins]
     double* d_ksum = nullptr;        // [n_bins]
     double* d_params = nullptr;      // [max_walkers][3]
+    double* d_effp = nullptr;        // [max_walkers][4] efficiency-model parameters (eor_set_efficiency)
+    float* d_ftab = nullptr;         // [max_walkers][n_z][kFTab] partial-ionization tables (models 1, 2)
+    int eff_walkers = 0;             // walkers whose efficiency parameters are set
     eor::WalkerInfo* d_walkers = nullptr;
     eor::PairInfo* d_pairs = nullptr;
     float* d_wtab = nullptr;         // [max_walkers][max_radii][n_m2]
@@ -172,6 +191,8 @@ size_t estimate_launches(const eor_ctx* c);
 // tables.cu
 cudaError_t build_cosmology_tables(eor_ctx* c);
 cudaError_t build_walker_tables(eor_ctx* c, int n_walkers);
+// the partial-ionization tables when a mass-dependent efficiency is on, else nullptr
+inline const float* pop_tables(const eor_ctx* c) { return c->cfg.efficiency_model ? c->d_ftab : nullptr; }
 
 // basis.cu
 cudaError_t build_basis(eor_ctx* c);

@@ -422,6 +422,7 @@ struct Pass2Args {
     float* xhi_out;             // optional [pair][n^3]
     double* xhi_sum;            // [pair]
     float2* ps_inter;           // [P slots][nh][n][n]
+    const float* ftab;          // [pair][kFTab] with a mass-dependent efficiency, else nullptr
     int pair0, n_pairs, j0, G;
     float delta_c;
 };
@@ -455,14 +456,15 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_ionize(Pass2Args 
         pencil_load_spectrum<N>(s, src, (size_t)N * N);
         __syncthreads();
         pencil_c2r<N>(s, p, i, z);
-        const float dcrit = pi.delta_crit[j];
+        const float dcrit = pi.delta_crit[j], dhi = pi.delta_hi[j];
 #pragma unroll
         for (int q = 0; q < P::NBp; q++)
 #pragma unroll
             for (int k2 = 0; k2 < P::P2; k2++) {
                 const int bit = 2 * (q * P::P2 + k2);
-                flags |= (uint32_t)(z[q][k2].x * scale >= dcrit) << bit;
-                flags |= (uint32_t)(z[q][k2].y * scale >= dcrit) << (bit + 1);
+                const float d0 = z[q][k2].x * scale, d1 = z[q][k2].y * scale;
+                flags |= (uint32_t)(d0 >= dcrit && d0 <= dhi) << bit;
+                flags |= (uint32_t)(d1 >= dcrit && d1 <= dhi) << (bit + 1);
             }
     }
     if (!last) {
@@ -487,7 +489,8 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_ionize(Pass2Args 
             for (int h = 0; h < 2; h++) {
                 const float dr = (h ? z[q][k2].y : z[q][k2].x) * scale;
                 float f = 0.0f;
-                if (cell_ok) f = dr >= dc ? 1.0f : erfcf((dc - dr) * inv);
+                if (a.ftab) f = pop_table_f(a.ftab + (size_t)pair * kFTab, dc - dr, pi.f_inv_h);   // efficiency-weighted
+                else if (cell_ok) f = dr >= dc ? 1.0f : erfcf((dc - dr) * inv);
                 const float xhii = ((flags >> (bit + h)) & 1u) ? 1.0f : fminf(1.0f, zeta * f);
                 const float xhi = 1.0f - xhii;
                 float* cell = s.ds + p * P::DS + 2 * m + h;
@@ -705,7 +708,8 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
             k_plane_filter_inverse<N, T><<<dim3(NH, G, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
             trace_end(c);
             Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, brightness_base(c), xhi_out,
-                         c->d_xhi_sum, c->d_psinter, pair0, n_pairs, g * G, G, (float)c->cfg.delta_c};
+                         c->d_xhi_sum, c->d_psinter, pop_tables(c), pair0, n_pairs, g * G, G,
+                         (float)c->cfg.delta_c};
             trace_begin(c, kKPencil);
             k_pencil_ionize<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(a2);
             trace_end(c);

@@ -219,6 +219,16 @@ __device__ double interp_lnsig(const double* lnsig, double lnr_lo, double dlnr, 
     return exp(l0 * f0 + l1 * f1 + l2 * f2 + l3 * f3);
 }
 
+// Halo mass of virial temperature 10^logt at redshift z (Sec. 2.1.3, after Barkana & Loeb 2001).
+__device__ double virial_mass(double logt, double z, double h, double om, double ol, double mu) {
+    const double zp = 1.0 + z;
+    const double om_z = om * zp * zp * zp / (om * zp * zp * zp + ol);
+    const double d = om_z - 1.0;
+    const double dc = 18.0 * kPi * kPi + 82.0 * d - 39.0 * d * d;
+    return 1e8 / h * pow(mu / 0.6, -1.5) * pow(om / om_z * dc / (18.0 * kPi * kPi), -0.5) *
+           pow(pow(10.0, logt) / 1.98e4, 1.5) * pow(zp / 10.0, -1.5);
+}
+
 struct WalkerTableArgs {
     const double* params;
     const double* growth;
@@ -267,12 +277,7 @@ __global__ void k_walker_tables(WalkerTableArgs a) {
     }
     // virial temperature -> minimum halo mass at z
     double zp = 1.0 + a.z[zi];
-    double om_z = a.omega_m * zp * zp * zp / (a.omega_m * zp * zp * zp + a.omega_l);
-    double d = om_z - 1.0;
-    double dc = 18.0 * kPi * kPi + 82.0 * d - 39.0 * d * d;
-    double tvir = pow(10.0, logt);
-    double m_min = 1e8 / a.h * pow(a.mu / 0.6, -1.5) * pow(a.omega_m / om_z * dc / (18.0 * kPi * kPi), -0.5) *
-                   pow(tvir / 1.98e4, 1.5) * pow(zp / 10.0, -1.5);
+    double m_min = virial_mass(logt, a.z[zi], a.h, a.omega_m, a.omega_l, a.mu);
     double r_min = cbrt(3.0 * m_min / (4.0 * kPi * a.rho_mean));
     double g2 = a.growth[zi] * a.growth[zi];
     double s2_min = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, r_min, a.err);
@@ -285,11 +290,243 @@ __global__ void k_walker_tables(WalkerTableArgs a) {
         P.delta_crit[j] = (float)dcrit;
     }
     for (int j = nr; j < kMaxRadii; j++) P.delta_crit[j] = INFINITY;
+    for (int j = 0; j < kMaxRadii; j++) P.delta_hi[j] = INFINITY;
+    P.f_inv_h = 0.0f;
     P.zeta = (float)zeta;
     P.cell_ok = s2 > 0.0 ? 1.0f : 0.0f;
     P.inv_sqrt2s2_cell = s2 > 0.0 ? (float)(1.0 / sqrt(2.0 * s2)) : 0.0f;
     double h2 = a.h * a.h;
     P.t0 = (float)(27.0 * sqrt(zp / 10.0 * 0.15 / (a.omega_m * h2)) * (a.omega_b * h2 / 0.023));
+}
+
+// ------------------------------------------------ mass-dependent efficiency (Sec. 5)
+//
+// F(delta_R) = sum_i Int zeta_i(M) f(S(M) | delta_R, S_R) dS over population i's masses below
+// M_R, f the extended Press-Schechter first-crossing distribution
+//     f(S) dS = nu / sqrt(2 pi) (S - S_R)^(-3/2) exp(-nu^2 / (2 (S - S_R))) dS,  nu = delta_c - delta_R.
+// In y = ln(S - S_R) this is Int zeta(M(y)) K(t) dy with t = nu e^(-y/2) / sqrt(2) and the
+// smooth bump K = t e^(-t^2) / sqrt(pi) (unit integral over y), so composite Gauss-Legendre on
+// unit panels in y resolves every nu; M(y) comes from inverting the sigma^2 table once per
+// node. Below the last panel (masses within e^-36 of M_R in variance) zeta is zeta(M_R) and
+// the bump integrates to erfc(t). One warp per (walker, redshift, radius).
+
+constexpr int kPopMax = 2;                   // populations of an efficiency model
+constexpr int kPopPanels = 36;               // unit panels in y per population
+constexpr int kPopGL = 4;                    // Gauss-Legendre nodes per panel
+constexpr int kPopNodes = kPopMax * kPopPanels * kPopGL;
+constexpr int kPopWarps = 4;                 // tasks per block
+constexpr int kPopScan = 64;                 // scan of nu: geometric from nu_max down by 1e-7
+constexpr int kPopRounds = 5;                // 33-way multisection rounds per crossing
+
+__constant__ double kGL4x[kPopGL] = {-0.86113631159405258, -0.33998104358485626, 0.33998104358485626,
+                                     0.86113631159405258};
+__constant__ double kGL4w[kPopGL] = {0.34785484513745386, 0.65214515486254614, 0.65214515486254614,
+                                     0.34785484513745386};
+
+// ln R where interp_lnsig's cubic equals L: bisection over the decreasing table for the
+// cell, then Newton steps on that cell's 4-point Lagrange cubic.
+__device__ double lnr_of_lnsig(const double* lnsig, double lnr_lo, double dlnr, double L, int* err) {
+    if (!(L <= lnsig[1] && L >= lnsig[kSigmaTable - 2])) {
+        atomicOr(err, kErrSigmaRange);
+        L = fmin(fmax(L, lnsig[kSigmaTable - 2]), lnsig[1]);
+    }
+    int lo = 1, hi = kSigmaTable - 2;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lnsig[mid] >= L) lo = mid; else hi = mid;
+    }
+    const double f0 = lnsig[lo - 1], f1 = lnsig[lo], f2 = lnsig[lo + 1], f3 = lnsig[lo + 2];
+    double t = f1 > f2 ? (f1 - L) / (f1 - f2) : 0.0;
+    for (int it = 0; it < 6; it++) {
+        const double t2 = t * t;
+        const double p = -t * (t - 1.0) * (t - 2.0) / 6.0 * f0 + (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0 * f1 -
+                         (t + 1.0) * t * (t - 2.0) / 2.0 * f2 + (t + 1.0) * t * (t - 1.0) / 6.0 * f3 - L;
+        const double dp = -(3.0 * t2 - 6.0 * t + 2.0) / 6.0 * f0 + (3.0 * t2 - 4.0 * t - 1.0) / 2.0 * f1 -
+                          (3.0 * t2 - 2.0 * t - 2.0) / 2.0 * f2 + (3.0 * t2 - 1.0) / 6.0 * f3;
+        if (dp == 0.0) break;
+        t = fmin(fmax(t - p / dp, -0.5), 1.5);
+    }
+    return lnr_lo + (lo + t) * dlnr;
+}
+
+struct Pop {
+    double zeta0, lnmp, slope, lnm_lo, lnm_hi;   // zeta0 (M / M_p)^slope on [M_lo, M_hi)
+};
+
+struct PopArgs {
+    const double* params;   // [walker][3]
+    const double* effp;     // [walker][4]
+    const double* growth;
+    const double* lnsig;
+    double lnr_lo, dlnr;
+    double z[EOR21_MAX_Z];
+    int n_z, n_walkers, max_radii, model;
+    double delta_c, mu, h, omega_m, omega_l, rho_mean;
+    const WalkerInfo* walkers;
+    PairInfo* pairs;
+    float* ftab;            // [pair][kFTab]
+    int* err;
+};
+
+__device__ int make_pops(const PopArgs& a, const double* p, const double* q, double z, Pop* out) {
+    const double ln1e10 = 23.025850929940457;
+    if (a.model == 1) {
+        int n = 0;
+        out[n++] = Pop{p[0], ln1e10, q[0], log(virial_mass(p[2], z, a.h, a.omega_m, a.omega_l, a.mu)), INFINITY};
+        if (q[1] > 0.0)
+            out[n++] = Pop{q[1], ln1e10, q[2], log(virial_mass(q[3], z, a.h, a.omega_m, a.omega_l, a.mu)), INFINITY};
+        return n;
+    }
+    // Sec. 5: zeta0 (T / T_F)^alpha on [10^4 K, T_F), zeta0 (T / T_F)^beta above; T ~ M^(2/3)
+    const double lmf = log(virial_mass(p[2], z, a.h, a.omega_m, a.omega_l, a.mu));
+    const double lmc = log(virial_mass(4.0, z, a.h, a.omega_m, a.omega_l, a.mu));
+    int n = 0;
+    if (lmc < lmf) out[n++] = Pop{p[0], lmf, 2.0 * q[0] / 3.0, lmc, lmf};
+    out[n++] = Pop{p[0], lmf, 2.0 * q[1] / 3.0, fmax(lmf, lmc), INFINITY};
+    return n;
+}
+
+__global__ void __launch_bounds__(32 * kPopWarps) k_pop_tables(PopArgs a) {
+    __shared__ double s_c[kPopWarps][kPopNodes];   // e^(-y/2) / sqrt(2) of each node
+    __shared__ double s_a[kPopWarps][kPopNodes];   // Gauss-Legendre weight x zeta(M(y)) / sqrt(pi)
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * kPopWarps + wid;
+    const int pair = (int)(task / a.max_radii), j = (int)(task % a.max_radii);
+    if (pair >= a.n_walkers * a.n_z) return;   // warp-uniform exits
+    PairInfo& P = a.pairs[pair];
+    const int n_r = P.n_r;
+    if (j >= n_r) return;
+    const int w = pair / a.n_z, zi = pair % a.n_z;
+    const double* p = a.params + 3 * w;
+    const double* q = a.effp + 4 * w;
+    bool ok = true;
+    for (int i = 0; i < 4; i++) ok = ok && isfinite(q[i]);
+    ok = ok && fabs(q[0]) <= 10.0 && fabs(q[a.model == 1 ? 2 : 1]) <= 10.0;
+    if (a.model == 1) ok = ok && q[1] >= 0.0 && q[3] > 0.0 && q[3] < 12.0;
+    if (!ok) {
+        if (lane == 0) {
+            atomicOr(a.err, kErrParam);
+            P.delta_crit[j] = INFINITY;
+            P.delta_hi[j] = INFINITY;
+        }
+        return;
+    }
+    Pop pops[kPopMax];
+    const int np = make_pops(a, p, q, a.z[zi], pops);
+    const double g2 = a.growth[zi] * a.growth[zi];
+    const double ln_mass_r3 = log(4.0 / 3.0 * kPi * a.rho_mean);   // ln M = this + 3 ln R
+    const double r = a.walkers[w].radii[j];
+    const double lnm_r = ln_mass_r3 + 3.0 * log(r);
+    const double s_r = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, r, a.err);
+    double f_c = 0.0, ds_max = 0.0;
+    double tail_z[kPopMax] = {0.0, 0.0}, tail_c[kPopMax] = {0.0, 0.0};
+    int nb[kPopMax] = {0, 0}, ne[kPopMax] = {0, 0};
+    int base = 0;
+    for (int i = 0; i < np; i++) {
+        const Pop pp = pops[i];
+        nb[i] = ne[i] = base;
+        if (lnm_r >= pp.lnm_lo && lnm_r < pp.lnm_hi) f_c += pp.zeta0 * exp(pp.slope * (lnm_r - pp.lnmp));
+        if (pp.lnm_lo >= lnm_r) continue;
+        const double ds_lo = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, exp((pp.lnm_lo - ln_mass_r3) / 3.0), a.err) - s_r;
+        if (!(ds_lo > 0.0)) continue;
+        const double y_lo = log(ds_lo);
+        double y_bot = y_lo - kPopPanels;
+        bool tail = true;
+        if (pp.lnm_hi < lnm_r) {
+            const double ds_top =
+                g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, exp((pp.lnm_hi - ln_mass_r3) / 3.0), a.err) - s_r;
+            if (ds_top > 0.0 && log(ds_top) > y_bot) {
+                y_bot = log(ds_top);
+                tail = false;
+            }
+        }
+        if (!(y_lo > y_bot)) continue;
+        ds_max = fmax(ds_max, ds_lo);
+        const int panels = max(1, min(kPopPanels, (int)ceil(y_lo - y_bot - 1e-9)));
+        const double hp = (y_lo - y_bot) / panels;
+        const int nn = panels * kPopGL;
+        for (int k = lane; k < nn; k += 32) {
+            const int pan = k / kPopGL, g = k % kPopGL;
+            const double y = y_bot + (pan + 0.5 * (kGL4x[g] + 1.0)) * hp;
+            const double lnr = lnr_of_lnsig(a.lnsig, a.lnr_lo, a.dlnr, log((s_r + exp(y)) / g2), a.err);
+            const double lnm = ln_mass_r3 + 3.0 * lnr;
+            s_c[wid][base + k] = exp(-0.5 * y) * 0.70710678118654752;
+            s_a[wid][base + k] = 0.5 * hp * kGL4w[g] * pp.zeta0 * exp(pp.slope * (lnm - pp.lnmp)) * 0.56418958354775628;
+        }
+        if (tail) {
+            tail_z[i] = pp.zeta0 * exp(pp.slope * (fmin(lnm_r, pp.lnm_hi) - pp.lnmp));
+            tail_c[i] = exp(-0.5 * y_bot) * 0.70710678118654752;
+        }
+        ne[i] = base + nn;
+        base += nn;
+    }
+    __syncwarp();
+    auto F = [&](double nu) {   // efficiency-weighted collapsed fraction at nu > 0 (one lane)
+        double f = 0.0;
+        for (int i = 0; i < np; i++) {
+            for (int k = nb[i]; k < ne[i]; k++) {
+                const double t = nu * s_c[wid][k];
+                if (t < 6.0) f += s_a[wid][k] * t * exp(-t * t);
+            }
+            if (tail_z[i] != 0.0) f += tail_z[i] * erfc(nu * tail_c[i]);
+        }
+        return f;
+    };
+    // scan nu_k = nu_max q^k (k < 64), then nu = 0 (the collapsed value)
+    const double nu_max = ds_max > 0.0 ? 8.0 * sqrt(2.0 * ds_max) : 1.0;
+    const double ratio = pow(1e-7, 1.0 / (kPopScan - 1));
+    const unsigned full = 0xffffffffu;
+    const bool s0 = F(nu_max * pow(ratio, lane)) >= 1.0, s1 = F(nu_max * pow(ratio, lane + 32)) >= 1.0;
+    const unsigned long long bits =
+        (unsigned long long)__ballot_sync(full, s0) | ((unsigned long long)__ballot_sync(full, s1) << 32);
+    const bool sc = f_c >= 1.0;
+    int ncross = 0, kc[2] = {0, 0};
+    for (int k = 0; k < kPopScan; k++) {
+        const bool bk = (bits >> k) & 1ull, bn = k + 1 < kPopScan ? ((bits >> (k + 1)) & 1ull) != 0 : sc;
+        if (bk != bn) {
+            if (ncross < 2) kc[ncross] = k;
+            ncross++;
+        }
+    }
+    double root[2] = {INFINITY, INFINITY};
+    if ((bits & 1ull) || ncross > 2) {
+        if (lane == 0) atomicOr(a.err, kErrShape);
+        ncross = 0;
+    }
+    for (int c = 0; c < ncross; c++) {
+        const int k = kc[c];
+        const bool sa = (bits >> k) & 1ull;
+        double nu_a = nu_max * pow(ratio, k), nu_b = k + 1 < kPopScan ? nu_max * pow(ratio, k + 1) : 0.0;
+        for (int it = 0; it < kPopRounds; it++) {
+            const double hh = (nu_a - nu_b) / 33.0;
+            const bool sx = F(nu_b + (lane + 1) * hh) >= 1.0;
+            const unsigned m = __ballot_sync(full, sx == sa);
+            if (m == 0u) {
+                nu_b = nu_b + 32.0 * hh;
+            } else {
+                const int l = __ffs(m) - 1;
+                const double na = nu_b + (l + 1) * hh;
+                nu_b = l == 0 ? nu_b : nu_b + l * hh;
+                nu_a = na;
+            }
+        }
+        root[c] = a.delta_c - 0.5 * (nu_a + nu_b);
+    }
+    if (lane == 0) {
+        P.delta_crit[j] = ncross >= 1 ? (float)root[0] : INFINITY;
+        P.delta_hi[j] = ncross == 2 ? (float)root[1] : INFINITY;
+    }
+    if (j == n_r - 1) {   // R_cell: the table of F for the partial ionization
+        float* tab = a.ftab + (size_t)pair * kFTab;
+        const double ht = nu_max / (kFTab - 1);
+        for (int i = lane; i < kFTab; i += 32) tab[i] = (float)(i == 0 ? f_c : F(i * ht));
+        if (lane == 0) {
+            P.f_inv_h = (float)(1.0 / ht);
+            P.zeta = 1.0f;
+            P.cell_ok = 1.0f;
+            P.inv_sqrt2s2_cell = 0.0f;
+        }
+    }
 }
 
 // W(kR) of each walker's radii on the grid's |m|^2 values, FP32: a 12-term series below
@@ -390,6 +627,32 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
     trace_begin(c, kKTables);
     k_walker_tables<<<(np + 127) / 128, 128, 0, c->stream>>>(a);
     trace_end(c);
+    if (g.efficiency_model) {
+        PopArgs pa{};
+        pa.params = c->d_params;
+        pa.effp = c->d_effp;
+        pa.growth = c->d_growth;
+        pa.lnsig = c->d_lnsig;
+        pa.lnr_lo = a.lnr_lo;
+        pa.dlnr = a.dlnr;
+        for (int j = 0; j < g.n_z; j++) pa.z[j] = g.z[j];
+        pa.n_z = g.n_z;
+        pa.n_walkers = n_walkers;
+        pa.max_radii = c->max_radii;
+        pa.model = g.efficiency_model;
+        pa.delta_c = g.delta_c;
+        pa.mu = g.mu;
+        pa.h = g.h; pa.omega_m = g.omega_m; pa.omega_l = 1.0 - g.omega_m;
+        pa.rho_mean = a.rho_mean;
+        pa.walkers = c->d_walkers;
+        pa.pairs = c->d_pairs;
+        pa.ftab = c->d_ftab;
+        pa.err = c->d_err;
+        const long long tasks = (long long)np * c->max_radii;
+        trace_begin(c, kKTables);
+        k_pop_tables<<<(unsigned)((tasks + kPopWarps - 1) / kPopWarps), 32 * kPopWarps, 0, c->stream>>>(pa);
+        trace_end(c);
+    }
     dim3 grid((c->n_m2 + 255) / 256, n_walkers * c->max_radii);
     trace_begin(c, kKTables);
     k_window_tables<<<grid, 256, 0, c->stream>>>(c->d_walkers, c->max_radii, c->n_m2,

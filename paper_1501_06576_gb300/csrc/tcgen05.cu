@@ -104,9 +104,11 @@ constexpr uint32_t kTileBytes = 128 * tc::kKMax * 4;   // one 128 x 32 TF32 tile
 constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of a CTA (64 KB)
 constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chunk (32 KB)
 // chunk meta: one 16-byte record per group of kGroup columns: (walker << 2 | first << 1 |
-// last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0)
+// last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0, or
+// with a mass-dependent efficiency the inverse step of the pair's table), then per column the
+// width delta_hi - delta_crit of its flag interval (+inf for the step-function efficiency)
 constexpr int kGroupsPerChunk = kTcN / kGroup;
-constexpr uint32_t kMBytes = kGroupsPerChunk * 16;
+constexpr uint32_t kMBytes = kGroupsPerChunk * 16 + kTcN * 4;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
 constexpr int kTmemBufs = 2;                              // accumulator buffers in tensor memory
 constexpr uint32_t kTmemCols = kTmemBufs * kTcTiles * kTcN;   // 2 buffers x kTcTiles x kTcN columns (512)
@@ -153,11 +155,12 @@ __global__ void k_format_a(const float* F, int kb, int rank, long long n3, int n
 __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* gmeta, const int* ncols,
                                                    const float* coef, const PairInfo* pairs, int kb, int rank,
                                                    int max_radii,
-                                                   int n_z, int chunks_per_z, float delta_c, unsigned char* out) {
+                                                   int n_z, int chunks_per_z, float delta_c, int pops,
+                                                   unsigned char* out) {
     const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kTcN + row;
     const int nc = *ncols;
     unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * kChunkBytes;
-    float thr = kNever;
+    float thr = kNever, width = INFINITY;
     const float* src = nullptr;
     const int cw = slot < nc ? cols[slot] : -1;
     if (cw >= 0) {
@@ -166,7 +169,9 @@ __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* g
         src = coef + ((size_t)w * max_radii + j) * kb;
         const float dcrit = pi.delta_crit[j];
         thr = j == pi.n_r - 1 ? delta_c : (isfinite(dcrit) ? dcrit : kNever);
+        if (j != pi.n_r - 1 && isfinite(dcrit) && isfinite(pi.delta_hi[j])) width = pi.delta_hi[j] - dcrit;
     }
+    reinterpret_cast<float*>(chunk + kBBytes + kGroupsPerChunk * 16)[row] = width;
     for (int b = 0; b < tc::kKMax; b++) {
         const float v = b < rank ? (src ? src[b] : 0.0f) : (b == rank ? -thr : 0.0f);
         const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* g
             const PairInfo& pi = pairs[(size_t)(info >> 2) * n_z + zi];
             zeta = pi.zeta;
             t0 = pi.t0;
-            inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
+            inv = pops ? pi.f_inv_h : (pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f);
         }
         reinterpret_cast<int4*>(chunk + kBBytes)[g] =
             make_int4(info, __float_as_int(zeta), __float_as_int(t0), __float_as_int(inv));
@@ -224,6 +229,7 @@ struct TcArgs {
     float* dtb;                 // [pair][n3]
     float* xhi_out;             // optional [pair][n3]
     unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
+    const float* ftab;          // [pair][kFTab] with a mass-dependent efficiency, else nullptr
     int* err;
     int n_z, chunks_per_z;
     int ksteps;                 // MMA K steps of 8: (rank + 1) / 8 rounded up
@@ -391,23 +397,47 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                 tc::tmem_ld32x2(base, v[0], v[1]);
                 m[0] = gm[0];
                 m[1] = gm[1];
-                tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
-                // flags: AND of sign bits over the walker's radii above R_cell (column 0 of its
-                // first group is R_cell, D = delta_R - delta_c)
-                const uint32_t a0 = and31(v[0]), a1 = and31(v[1]);
                 const bool second = (m[1].x & 2) == 0;   // group 1 continues the walker of group 0
-                fa[0] = a0;
+                if (a.ftab) {
+                    // mass-dependent efficiency: flagged where 0 <= D <= width (the interval of
+                    // delta_R between the two crossings of zeta f_coll = 1)
+                    const float* wd = reinterpret_cast<const float*>(Ms + st * kMBytes + kGroupsPerChunk * 16) + g0 * kGroup;
+                    bool n0 = true, n1 = true;
+#pragma unroll
+                    for (int i = 1; i < 32; i++) {
+                        n0 = n0 && !(v[0][i] >= 0.0f && v[0][i] <= wd[i]);
+                        n1 = n1 && !(v[1][i] >= 0.0f && v[1][i] <= wd[kGroup + i]);
+                    }
+                    const bool c10 = !(v[1][0] >= 0.0f && v[1][0] <= wd[kGroup]);
+                    tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
+                    fa[0] = n0 ? 0x80000000u : 0u;
+                    fa[1] = (second ? (n0 && n1 && c10) : n1) ? 0x80000000u : 0u;
+                } else {
+                    tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
+                    // flags: AND of sign bits over the walker's radii above R_cell (column 0 of its
+                    // first group is R_cell, D = delta_R - delta_c)
+                    const uint32_t a0 = and31(v[0]), a1 = and31(v[1]);
+                    fa[0] = a0;
+                    fa[1] = second ? a0 & a1 & __float_as_uint(v[1][0]) : a1;
+                }
                 dd[0] = v[0][0];
-                fa[1] = second ? a0 & a1 & __float_as_uint(v[1][0]) : a1;
                 dd[1] = second ? v[0][0] : v[1][0];
             }
             float xh[2];
 #pragma unroll
             for (int u = 0; u < 2; u++) {   // two independent chains
                 const float zeta = __int_as_float(m[u].y), inv = __int_as_float(m[u].w);
-                // f_coll at R_cell (1 where delta_R >= delta_c), no ionization where s^2 <= 0
-                const float f = dd[u] >= 0.0f ? 1.0f : erfc_cheb(-dd[u] * inv);
-                xh[u] = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+                if (a.ftab) {
+                    // efficiency-weighted f_coll at R_cell from the pair's table in nu = -D
+                    const bool ends = m[u].x >= 0 && (m[u].x & 1);
+                    const float f = ends ? pop_table_f(a.ftab + ((size_t)(m[u].x >> 2) * a.n_z + zi) * kFTab, -dd[u], inv)
+                                         : 0.0f;
+                    xh[u] = 1.0f - fminf(1.0f, f);
+                } else {
+                    // f_coll at R_cell (1 where delta_R >= delta_c), no ionization where s^2 <= 0
+                    const float f = dd[u] >= 0.0f ? 1.0f : erfc_cheb(-dd[u] * inv);
+                    xh[u] = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+                }
                 xh[u] = (fa[u] >> 31) == 0u ? 0.0f : xh[u];   // flagged at a larger radius (Eq. 1)
             }
 #pragma unroll
@@ -529,7 +559,8 @@ cudaError_t build_columns(eor_ctx* c, int n_walkers) {
     k_format_b<<<dim3(chunks, c->cfg.n_z), kTcN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
                                                                c->d_pairs, c->kb, c->basis_rank, c->max_radii, c->cfg.n_z,
                                                                chunks,
-                                                               (float)c->cfg.delta_c, c->d_tcB);
+                                                               (float)c->cfg.delta_c, c->cfg.efficiency_model ? 1 : 0,
+                                                               c->d_tcB);
     trace_end(c);
     return cudaGetLastError();
 }
@@ -538,7 +569,7 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     const int pairs = c->n_walkers * c->cfg.n_z;
     cudaError_t e = cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * pairs, c->stream);
     if (e != cudaSuccess) return e;
-    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, brightness_base(c), c->d_dtb, xhi_out, c->d_xq, c->d_err,
+    TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, brightness_base(c), c->d_dtb, xhi_out, c->d_xq, pop_tables(c), c->d_err,
              c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3};
     trace_begin(c, kKBasis);
     k_basis_ionize_tc<<<dim3((unsigned)(c->n3 / kTcCells), c->cfg.n_z), kTcThreads, basis_tc_smem(), c->stream>>>(a);

@@ -19,7 +19,8 @@ EOR_HOST, EOR_DEVICE = 0, 1
 MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 
 # names exported by include/eor21.h
-EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_params", "eor_run_ionization",
+EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_efficiency", "eor_set_params",
+           "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
            "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
@@ -49,7 +50,8 @@ class EorConfig(ctypes.Structure):
                 ("k_hi", ctypes.c_double), ("chi2_k_lo", ctypes.c_double), ("chi2_k_hi", ctypes.c_double),
                 ("max_walkers", ctypes.c_int), ("r_mfp_max", ctypes.c_double),
                 ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", ctypes.c_void_p),
-                ("rsd", ctypes.c_int), ("rsd_max_dvdr", ctypes.c_double), ("zeldovich", ctypes.c_int)]
+                ("rsd", ctypes.c_int), ("rsd_max_dvdr", ctypes.c_double), ("zeldovich", ctypes.c_int),
+                ("efficiency_model", ctypes.c_int)]
 
 
 class EmuConfig(ctypes.Structure):
@@ -97,6 +99,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_create": (I, [ctypes.POINTER(EorConfig), P, ctypes.POINTER(P)]),
         "eor_init_boxes": (I, [P, P, I]),
         "eor_set_params": (I, [P, P, I, I]),
+        "eor_set_efficiency": (I, [P, P, I, I]),
         "eor_run_ionization": (I, [P, P, P, I]),
         "eor_power_spectrum": (I, [P, P, P, P, I]),
         "eor_chi2": (I, [P, P, P, P, I]),
@@ -260,6 +263,11 @@ class Context:
         self._check(self.lib.eor_set_params(self.handle, p, nw, mem))
         self.n_walkers = nw
 
+    def eor_set_efficiency(self, q):
+        """Efficiency parameters [n_walkers][4] of efficiency_model 1 or 2."""
+        p, mem, keep = _arg(q, np.float64)
+        self._check(self.lib.eor_set_efficiency(self.handle, p, int(keep.shape[0]), mem))
+
     def eor_run_ionization(self, want_xhi: bool = False, device: bool = False):
         pairs = (self.n_walkers, self.n_z)
         xhi = self._out(device, pairs + (self.n,) * 3, np.float32) if want_xhi else None
@@ -384,6 +392,7 @@ class Context:
     # short aliases
     init_boxes = eor_init_boxes
     set_params = eor_set_params
+    set_efficiency = eor_set_efficiency
     run_ionization = eor_run_ionization
     power_spectrum = eor_power_spectrum
     chi2 = eor_chi2
