@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
     ap.add_argument("--mcmc-steps", type=int, default=10)
+    ap.add_argument("--no-two-pop", action="store_true", help="skip the 256^3 two-population leg")
+    ap.add_argument("--two-pop-walkers", type=int, default=64)
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
     ap.add_argument("--emu-steps", type=int, default=32000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
@@ -381,6 +383,51 @@ def time_mcmc(ctx, eor21, synth, torch, stream, mock, sigma, args):
                     "round trip between steps"}
 
 
+def time_two_pop(eor21, synth, torch, stream, flush, args):
+    """The two-population workload: 256^3 boxes, L = 500 Mpc, z = 8, 9, 10, 64 walkers whose
+    efficiency is two power laws zeta_i0 (M / 1e10 Msun)^alpha_i above their own M_min(T_vir,i)
+    (efficiency_model 1), batched in one graph replay per step; mock from the seed + 1 boxes at
+    (30, 15 Mpc, 4.7) with (alpha_1, zeta_20, alpha_2, log10 T_2) = (0.3, 10, -0.3, 5.3), sigma =
+    20 % of it. Timed with CUDA events over args.steps replays after two warm-up replays, L2
+    flushed before the timed region."""
+    n, box, zs, w = 256, 500.0, (8.0, 9.0, 10.0), args.two_pop_walkers
+    rng = np.random.default_rng(31)
+    base = np.column_stack([rng.uniform(5, 100, w), rng.uniform(5, 20, w), rng.uniform(4, 6, w)])
+    extra = np.column_stack([rng.uniform(-0.5, 0.5, w), rng.uniform(5, 100, w), rng.uniform(-0.5, 0.5, w),
+                             rng.uniform(4, 6, w)])
+    with torch.cuda.stream(stream):
+        ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=w, efficiency_model=1, stream=stream.cuda_stream)
+        ctx.init_boxes(torch.from_numpy(synth.density_boxes(n, box, zs, seed=11)).cuda())
+        ctx.set_efficiency(np.array([[0.3, 10.0, -0.3, 5.3]] * w))
+        ctx.set_params(np.array([[30.0, 15.0, 4.7]]))
+        ctx.run_ionization()
+        mock = np.ascontiguousarray(ctx.power_spectrum()[0][0])
+        ctx.init_boxes(torch.from_numpy(synth.density_boxes(n, box, zs, seed=10)).cuda())
+        ctx.set_efficiency(extra)
+        d_params = torch.from_numpy(base).cuda()
+        d_mock = torch.from_numpy(mock).cuda()
+        d_sigma = torch.from_numpy(0.2 * mock).cuda()
+        for _ in range(2):
+            ctx.likelihood(d_params, d_mock, d_sigma)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.likelihood(d_params, d_mock, d_sigma)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rank, _ = ctx.basis_info()[:2]
+        radii = sum(len(ctx.walker_ladder(k)) for k in range(w)) * len(zs)
+        launches = ctx.launch_count()
+        ctx.close()
+    return {"value": w / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms, "walkers": w,
+            "workload": "256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
+                        "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc",
+            "radius_tasks_per_step": radii, "basis_rank": rank, "gpu_launches_per_step": launches,
+            "dtype": "f32 (FP64 tables)"}
+
+
 def main():
     global ZS
     args = parse()
@@ -513,6 +560,15 @@ def main():
         if not args.no_emulator and rank == 0:
             emulator = time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args)
 
+    # ---------------- the 256^3 two-population workload (its own context)
+    two_pop = None
+    if not args.no_two_pop and rank == 0:
+        ctx.close()
+        try:
+            two_pop = time_two_pop(eor21, synth, torch, stream, flush, args)
+        except eor21.EorError as err:
+            two_pop = {"error": str(err)}
+
     if rank != 0:
         return 0
 
@@ -587,7 +643,8 @@ def main():
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
                        "contraction": "tcgen05 3xTF32" if uses_tensor_cores else "FP32 FMA"},
             "basis_fp32_units": simt,
-            "direct_method": direct, "emulator": emulator, "mcmc": mcmc, "cpu_baseline": cpu, "clocks": clk}
+            "direct_method": direct, "emulator": emulator, "mcmc": mcmc, "two_population": two_pop,
+            "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0
 

@@ -61,7 +61,7 @@ typedef struct eor_ctx eor_ctx;   /* opaque, library-owned */
 /* Problem description. eor_default_config fills the 128^3, 250 Mpc, z = 8, 9, 10
  * workload with the readings the library takes where the paper is silent. */
 typedef struct {
-    int n;                       /* grid side: 16, 32, 64 or 128 */
+    int n;                       /* grid side: 16, 32, 64, 128 or 256 */
     double box_mpc;              /* comoving box side L [Mpc] */
     int n_z;                     /* redshifts, 1..EOR21_MAX_Z */
     double z[EOR21_MAX_Z];

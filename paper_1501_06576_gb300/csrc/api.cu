@@ -233,7 +233,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     *out = nullptr;
     if (!cfg) return fail(nullptr, EOR_EINVAL, "cfg is NULL");
     const eor_config& g = *cfg;
-    if (!eor::grid_supported(g.n)) return fail(nullptr, EOR_ENOTSUP, "n must be 16, 32, 64 or 128");
+    if (!eor::grid_supported(g.n)) return fail(nullptr, EOR_ENOTSUP, "n must be 16, 32, 64, 128 or 256");
     if (!(g.box_mpc > 0.0) || !isfinite(g.box_mpc)) return fail(nullptr, EOR_EINVAL, "box_mpc must be > 0");
     if (g.n_z < 1 || g.n_z > EOR21_MAX_Z) return fail(nullptr, EOR_EINVAL, "n_z out of range");
     for (int j = 0; j < g.n_z; j++)

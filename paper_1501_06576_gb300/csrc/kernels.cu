@@ -268,6 +268,182 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
         if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
 }
 
+// ------------------------------------------------------------------ 256-point line passes
+//
+// A 256 x 256 complex plane (512 KB) does not fit one CTA's shared memory, so at n = 256 a
+// plane pass becomes two line passes through global memory: 16 contiguous rows, or 16
+// columns (stride 256), of 256 points per CTA, each line transformed by a team of 16 threads
+// (256 = 16 x 16, the two-step split of fft_core.cuh). Lines sit in shared memory with one
+// pad element per 16 (stage exchanges conflict-free) and an odd line stride (column loads
+// conflict-free). Column-pass modes: plain store, density spectrum times a window on load
+// (the inverse of pass 1), or the shell sums of the power spectrum (no store).
+
+constexpr int kL = 256;
+constexpr int kLLines = 16;                            // lines per CTA
+constexpr int kLThreads = 16 * kLLines;                // a team of 16 threads per line
+constexpr int kLStride = kL + kL / 16 + 1;             // 273 float2 per padded line
+constexpr size_t kLSmem = (size_t)kLLines * kLStride * sizeof(float2) + kL * sizeof(float2) +
+                          (size_t)kPrivBins * kLThreads * sizeof(float);
+__device__ __forceinline__ int lpad(int p) { return p + (p >> 4); }
+
+enum LineMode : int { kLineStore = 0, kLineFilter = 1, kLinePs = 2 };
+
+struct LineArgs {
+    const float2* src;          // [task][NH][256][256], or the density spectra (kLineFilter)
+    float2* dst;                // [task][NH][256][256] (kLineStore, kLineFilter)
+    int G;                      // tasks per slot (radii of a launch); task = slot * G + tg
+    // validity and windows (pass 1): pair = pair0 + slot, radius j0 + tg
+    const PairInfo* pairs;      // nullptr: every task valid
+    const float* wtab;          // [walker][max_radii][n_m2]
+    int max_radii, n_m2, pair0, n_pairs, j0;
+    // power spectrum
+    const signed char* bin_of_m2;
+    double* ps_sum;             // [pair][n_bins]
+    int n_bins;
+    float kf3;
+};
+
+// 256-point DFT of line `line` of buf in place (thread i of its team). On return thread i
+// holds X[i + 16 k2] in hold[k2].
+template <int DIR>
+__device__ __forceinline__ void line_fft256(float2* buf, const float2* tw, int line, int i, float2 (&hold)[16]) {
+    float2* L = buf + line * kLStride;
+    float2 a[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) a[j] = L[lpad(j * 16 + i)];
+    dft_reg<16, DIR>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; k1++) a[k1] = cmul(a[k1], tw_get<kL, DIR>(tw, i * k1));
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; k1++) L[lpad(k1 * 16 + i)] = a[k1];
+    __syncthreads();
+#pragma unroll
+    for (int i2 = 0; i2 < 16; i2++) hold[i2] = L[lpad(i * 16 + i2)];
+    dft_reg<16, DIR>(hold);
+}
+
+__device__ __forceinline__ bool line_task_valid(const LineArgs& a, int slot, int tg) {
+    if (!a.pairs) return true;
+    const int pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return false;
+    return a.wtab == nullptr || a.j0 + tg < a.pairs[pair].n_r;
+}
+
+// Rows of plane blockIdx.x / 16 (16 rows: blockIdx.x % 16) of task (blockIdx.z, blockIdx.y),
+// transformed along the contiguous axis, src -> dst (may be the same buffer).
+template <int DIR>
+__global__ void __launch_bounds__(kLThreads) k_lines_rows(LineArgs a) {
+    constexpr int NH = kL / 2 + 1;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = smem + kLLines * kLStride;
+    const int plane = blockIdx.x / 16, rg = blockIdx.x % 16, tg = blockIdx.y, slot = blockIdx.z;
+    if (!line_task_valid(a, slot, tg)) return;
+    const size_t off = (((size_t)slot * a.G + tg) * NH + plane) * kL * kL + (size_t)rg * kLLines * kL;
+    fill_twiddles<kL>(tw);
+    const float2* src = a.src + off;
+    for (int e = threadIdx.x; e < kLLines * kL; e += kLThreads) buf[(e / kL) * kLStride + lpad(e % kL)] = __ldg(src + e);
+    __syncthreads();
+    float2 hold[16];
+    const int line = threadIdx.x / 16, i = threadIdx.x % 16;
+    line_fft256<DIR>(buf, tw, line, i, hold);
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; k2++) buf[line * kLStride + lpad(i + 16 * k2)] = hold[k2];
+    __syncthreads();
+    float2* dst = a.dst + off;
+    for (int e = threadIdx.x; e < kLLines * kL; e += kLThreads) dst[e] = buf[(e / kL) * kLStride + lpad(e % kL)];
+}
+
+// Columns c0 .. c0 + 15 (c0 = 16 (blockIdx.x % 16)) of plane blockIdx.x / 16, transformed
+// along the row index.
+template <int DIR, int MODE>
+__global__ void __launch_bounds__(kLThreads) k_lines_cols(LineArgs a) {
+    constexpr int NH = kL / 2 + 1;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = smem + kLLines * kLStride;
+    float* priv = reinterpret_cast<float*>(tw + kL);      // [kPrivBins][kLThreads]
+    __shared__ double s_bins[EOR21_MAX_BINS];
+    const int plane = blockIdx.x / 16, c0 = (blockIdx.x % 16) * kLLines, tg = blockIdx.y, slot = blockIdx.z;
+    if (!line_task_valid(a, slot, tg)) return;
+    fill_twiddles<kL>(tw);
+    const size_t task_off = (((size_t)slot * a.G + tg) * NH + plane) * kL * kL;
+    if constexpr (MODE == kLineFilter) {
+        const int pair = a.pair0 + slot, j = a.j0 + tg;
+        const PairInfo& pi = a.pairs[pair];
+        const float2* spec = a.src + ((size_t)pi.zi * NH + plane) * kL * kL;
+        const float* wt = a.wtab + ((size_t)pi.w * a.max_radii + j) * a.n_m2;
+        const int mz2 = plane * plane;
+        for (int e = threadIdx.x; e < kLLines * kL; e += kLThreads) {
+            const int r = e / kLLines, cc = e % kLLines;
+            const int mx = signed_index(r, kL), my = signed_index(c0 + cc, kL);
+            const float wv = __ldg(wt + mx * mx + my * my + mz2);
+            const float2 v = __ldg(spec + (size_t)r * kL + c0 + cc);
+            buf[cc * kLStride + lpad(r)] = make_float2(v.x * wv, v.y * wv);
+        }
+    } else {
+        const float2* src = a.src + task_off;
+        for (int e = threadIdx.x; e < kLLines * kL; e += kLThreads) {
+            const int r = e / kLLines, cc = e % kLLines;
+            buf[cc * kLStride + lpad(r)] = __ldg(src + (size_t)r * kL + c0 + cc);
+        }
+    }
+    if constexpr (MODE == kLinePs) {
+        for (int e = threadIdx.x; e < kPrivBins * kLThreads; e += kLThreads) priv[e] = 0.0f;
+        for (int e = threadIdx.x; e < EOR21_MAX_BINS; e += kLThreads) s_bins[e] = 0.0;
+    }
+    __syncthreads();
+    float2 hold[16];
+    const int line = threadIdx.x / 16, i = threadIdx.x % 16;
+    line_fft256<DIR>(buf, tw, line, i, hold);
+    if constexpr (MODE == kLinePs) {
+        // row index r = i + 16 k2 (kx), column c0 + line (ky), plane kz: S_b += w k^3 |X|^2
+        const float weight = (plane == 0 || plane == kL / 2) ? 1.0f : 2.0f;
+        const int my = signed_index(c0 + line, kL), mz2 = plane * plane;
+        const bool priv_ok = a.n_bins <= kPrivBins;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; k2++) {
+            const int mx = signed_index(i + 16 * k2, kL);
+            const int m2 = mx * mx + my * my + mz2;
+            const int b = a.bin_of_m2[m2];
+            if (b >= 0) {
+                const float2 v = hold[k2];
+                const float fm2 = (float)m2;
+                const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (v.x * v.x + v.y * v.y);
+                if (priv_ok) priv[b * kLThreads + threadIdx.x] += val;
+                else atomicAdd(&s_bins[b], (double)val);
+            }
+        }
+        __syncthreads();
+        if (priv_ok) {
+            constexpr int WARPS = kLThreads / 32;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x / 32;
+            for (int b = warp; b < a.n_bins; b += WARPS) {
+                double sum = 0.0;
+                for (int k = lane; k < kLThreads; k += 32) sum += (double)priv[b * kLThreads + k];
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0) s_bins[b] = sum;
+            }
+            __syncthreads();
+        }
+        const int pair = a.pair0 + slot;
+        for (int b = threadIdx.x; b < a.n_bins; b += kLThreads)
+            if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 0; k2 < 16; k2++) buf[line * kLStride + lpad(i + 16 * k2)] = hold[k2];
+        __syncthreads();
+        float2* dst = a.dst + task_off;
+        for (int e = threadIdx.x; e < kLLines * kL; e += kLThreads) {
+            const int r = e / kLLines, cc = e % kLLines;
+            dst[(size_t)r * kL + c0 + cc] = buf[cc * kLStride + lpad(r)];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ pencil pass
 
 template <int N>
@@ -642,14 +818,93 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Plane passes of every grid size: at n <= 128 one shared-memory-resident plane per CTA; at
+// n = 256 a row pass and a column pass (each its own traced launch).
+
+// Forward 2D transform of the NH planes of src ([kz][x][y]) into dst ([kz][kx][ky]).
+template <int N, int T>
+cudaError_t plane_forward(eor_ctx* c, const float2* src, float2* dst) {
+    constexpr int NH = N / 2 + 1;
+    if constexpr (N == kL) {
+        LineArgs la{};
+        la.src = src; la.dst = dst; la.G = 1;
+        trace_begin(c, kKForward);
+        k_lines_rows<-1><<<dim3(NH * 16, 1, 1), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+        la.src = dst;
+        trace_begin(c, kKForward);
+        k_lines_cols<-1, kLineStore><<<dim3(NH * 16, 1, 1), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+    } else {
+        trace_begin(c, kKForward);
+        k_plane_forward<N, T><<<NH, Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(src, dst);
+        trace_end(c);
+    }
+    return cudaGetLastError();
+}
+
+// Pass 1 (filter + inverse 2D transform) of G radii x P slots, as k_plane_filter_inverse.
+template <int N, int T>
+cudaError_t plane_filter_inverse(eor_ctx* c, const Pass1Args& a1, int P, int cls) {
+    constexpr int NH = N / 2 + 1;
+    if constexpr (N == kL) {
+        LineArgs la{};
+        la.src = a1.spec; la.dst = a1.inter; la.G = a1.G;
+        la.pairs = a1.pairs; la.wtab = a1.wtab; la.max_radii = a1.max_radii; la.n_m2 = a1.n_m2;
+        la.pair0 = a1.pair0; la.n_pairs = a1.n_pairs; la.j0 = a1.j0;
+        trace_begin(c, cls);
+        k_lines_cols<+1, kLineFilter><<<dim3(NH * 16, a1.G, P), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+        la.src = a1.inter;
+        trace_begin(c, cls);
+        k_lines_rows<+1><<<dim3(NH * 16, a1.G, P), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+    } else {
+        trace_begin(c, cls);
+        k_plane_filter_inverse<N, T><<<dim3(NH, a1.G, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
+        trace_end(c);
+    }
+    return cudaGetLastError();
+}
+
+// Shell sums of `planes` kz planes of P slots of z-transformed boxes, as k_plane_ps.
+template <int N, int T>
+cudaError_t plane_ps(eor_ctx* c, const PSArgs& ap, int planes, int P) {
+    if constexpr (N == kL) {
+        LineArgs la{};
+        la.src = ap.ps_inter; la.dst = const_cast<float2*>(ap.ps_inter); la.G = 1;
+        la.pairs = ap.pairs; la.pair0 = ap.pair0; la.n_pairs = ap.n_pairs;
+        la.bin_of_m2 = ap.bin_of_m2; la.ps_sum = ap.ps_sum; la.n_bins = ap.n_bins; la.kf3 = ap.kf3;
+        trace_begin(c, kKPsPlane);
+        k_lines_rows<-1><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+        trace_begin(c, kKPsPlane);
+        k_lines_cols<-1, kLinePs><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
+        trace_end(c);
+    } else {
+        trace_begin(c, kKPsPlane);
+        k_plane_ps<N, T><<<dim3(planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
+        trace_end(c);
+    }
+    return cudaGetLastError();
+}
+
 template <int N, int T>
 cudaError_t prepare_n() {
     cudaError_t e;
     if ((e = set_smem(k_pencil_forward<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_forward<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_filter_inverse<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
+    if constexpr (N == kL) {
+        if ((e = set_smem(k_lines_rows<-1>, kLSmem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_rows<+1>, kLSmem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_cols<-1, kLineStore>, kLSmem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_cols<+1, kLineFilter>, kLSmem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_cols<-1, kLinePs>, kLSmem)) != cudaSuccess) return e;
+    } else {
+        if ((e = set_smem(k_plane_forward<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_plane_filter_inverse<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM_PS)) != cudaSuccess) return e;
+    }
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM_PS)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_forward_batch<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -670,26 +925,20 @@ cudaError_t ps_from_boxes_n(eor_ctx* c) {
         trace_end(c);
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
-        trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(c->ps_planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
-        trace_end(c);
+        cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
 template <int N, int T>
 cudaError_t forward_spectrum_n(eor_ctx* c, int zi) {
-    constexpr int NH = N / 2 + 1;
     float2* tmp = c->d_psinter;   // slot 0 of the PS scratch
     trace_begin(c, kKForward);
     k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
         c->d_delta + (size_t)zi * c->n3, tmp);
     trace_end(c);
-    trace_begin(c, kKForward);
-    k_plane_forward<N, T><<<NH, Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(
-        tmp, c->d_spec + (size_t)zi * c->nspec);
-    trace_end(c);
-    return cudaGetLastError();
+    return plane_forward<N, T>(c, tmp, c->d_spec + (size_t)zi * c->nspec);
 }
 
 template <int N, int T>
@@ -704,9 +953,8 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         for (int g = 0; g < groups; g++) {
             Pass1Args a1{c->d_spec, c->d_inter, c->d_pairs, c->d_wtab, c->max_radii, c->n_m2,
                          pair0, n_pairs, g * G, G};
-            trace_begin(c, kKFilterPlane);
-            k_plane_filter_inverse<N, T><<<dim3(NH, G, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
-            trace_end(c);
+            cudaError_t e = plane_filter_inverse<N, T>(c, a1, P, kKFilterPlane);
+            if (e != cudaSuccess) return e;
             Pass2Args a2{c->d_inter, c->d_pairs, c->d_flags, brightness_base(c), xhi_out,
                          c->d_xhi_sum, c->d_psinter, pop_tables(c), pair0, n_pairs, g * G, G,
                          (float)c->cfg.delta_c};
@@ -716,9 +964,8 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         }
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
-        trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(c->ps_planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
-        trace_end(c);
+        cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -734,9 +981,7 @@ cudaError_t filtered_density_n(eor_ctx* c, int zi, float* out, const float* wtab
         cudaSuccess)
         return e;
     Pass1Args a1{c->d_spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
-    trace_begin(c, kKFilterPlane);
-    k_plane_filter_inverse<N, T><<<dim3(NH, 1, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
-    trace_end(c);
+    if ((e = plane_filter_inverse<N, T>(c, a1, 1, kKFilterPlane)) != cudaSuccess) return e;
     trace_begin(c, kKOther);
     k_pencil_density<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(c->d_inter, out);
     trace_end(c);
@@ -780,9 +1025,7 @@ cudaError_t spectrum_to_box_n(eor_ctx* c, const float2* spec, float* out, const 
         cudaSuccess)
         return e;
     Pass1Args a1{spec, c->d_inter, c->d_diag_pair, wtab, 1, c->n_m2, 0, 1, 0, 1};
-    trace_begin(c, kKOther);
-    k_plane_filter_inverse<N, T><<<dim3(NH, 1, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM, c->stream>>>(a1);
-    trace_end(c);
+    if ((e = plane_filter_inverse<N, T>(c, a1, 1, kKOther)) != cudaSuccess) return e;
     trace_begin(c, kKOther);
     k_pencil_density<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(c->d_inter, out);
     trace_end(c);
@@ -804,9 +1047,7 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(box, c->d_psinter);
     trace_end(c);
     PSArgs ap{c->d_psinter, c->d_diag_pair, c->d_bin_of_m2, c->d_diag_ps, 0, 1, nb, kf * kf * kf};
-    trace_begin(c, kKPsPlane);
-    k_plane_ps<N, T><<<dim3(NH, 1), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
-    trace_end(c);
+    if ((e = plane_ps<N, T>(c, ap, NH, 1)) != cudaSuccess) return e;
     const double dx = c->cfg.box_mpc / c->n;
     const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
     const double scale = dx * dx * dx * dx * dx * dx / (2.0 * kPi * kPi * vol);
@@ -862,6 +1103,7 @@ __global__ void k_noise_finish(const double* sums, const double* mock, const lon
         case 64: return FN<64, 512>(__VA_ARGS__);                                           \
         case 128:                                                                           \
             return (c)->tune.plane_threads >= 1024 ? FN<128, 1024>(__VA_ARGS__) : FN<128, 512>(__VA_ARGS__); \
+        case 256: return FN<256, 512>(__VA_ARGS__);                                         \
         default: return cudaErrorInvalidValue;                                              \
     }
 
@@ -973,6 +1215,7 @@ cudaError_t launch_zeldovich(eor_ctx* c, int zi, float* work) {
                 e = c->tune.plane_threads >= 1024 ? spectrum_to_box_n<128, 1024>(c, c->d_psinter, out, c->d_diag_wtab)
                                                   : spectrum_to_box_n<128, 512>(c, c->d_psinter, out, c->d_diag_wtab);
                 break;
+            case 256: e = spectrum_to_box_n<256, 512>(c, c->d_psinter, out, c->d_diag_wtab); break;
             default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
@@ -1007,6 +1250,7 @@ cudaError_t launch_brightness_weight(eor_ctx* c, int zi) {
                     ? spectrum_to_box_n<128, 1024>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab)
                     : spectrum_to_box_n<128, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab);
             break;
+        case 256: e = spectrum_to_box_n<256, 512>(c, c->d_psinter, c->d_scratch_box, c->d_diag_wtab); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -1027,7 +1271,7 @@ size_t estimate_launches(const eor_ctx* c) {
     return (size_t)batches * (2 * groups + 1) + 2 * (size_t)c->cfg.n_z * (c->kb + 1) + 64;
 }
 
-bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) { EOR_DISPATCH(c, forward_spectrum_n, c, zi) }
 
@@ -1056,6 +1300,7 @@ cudaError_t prepare_kernels(int n) {
             cudaError_t e = prepare_n<128, 512>();
             return e != cudaSuccess ? e : prepare_n<128, 1024>();
         }
+        case 256: return prepare_n<256, 512>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1066,6 +1311,7 @@ size_t flag_words_per_pair(int n) {
         case 32: return (size_t)Pencil<32>::TILES * Pencil<32>::THREADS;
         case 64: return (size_t)Pencil<64>::TILES * Pencil<64>::THREADS;
         case 128: return (size_t)Pencil<128>::TILES * Pencil<128>::THREADS;
+        case 256: return (size_t)Pencil<256>::TILES * Pencil<256>::THREADS;
         default: return 0;
     }
 }

@@ -78,6 +78,9 @@ def test_create_rejects_bad_config_before_touching_cuda():
     rc = lib.eor_create(ctypes.byref(cfg), None, ctypes.byref(h))
     assert rc in (eor21.EOR_EINVAL, eor21.EOR_ECUDA)
     assert lib.eor_create(None, None, ctypes.byref(h)) == eor21.EOR_EINVAL
+    cfg = eor21.default_config(efficiency_model=3)
+    assert lib.eor_create(ctypes.byref(cfg), None, ctypes.byref(h)) == eor21.EOR_EINVAL
+    assert b"efficiency_model" in lib.eor_last_error(None)
 
 
 def test_null_context_calls_fail_cleanly():

@@ -1,8 +1,11 @@
 """GPU parity of the mass-dependent ionizing efficiency (two populations, Sec. 5) against the
 FP64 oracle (oracle.Oracle.ionize_pops), through the C ABI, for every ionization method.
-Tolerances as for the step-function efficiency: at most 1e-4 of cells with a flipped
-decision (|x_HI difference| > 1e-3), 1e-4 absolute on every other cell, 1e-3 relative per
-Delta^2 bin. The grid spacing is the 256^3, 500 Mpc workload's (1.95 Mpc)."""
+Tolerances: at most 1e-4 of cells with a flipped decision (|x_HI difference| > 1e-3), 1e-4
+absolute on every other cell; Delta^2 within 1e-3 of the oracle's spectrum of the GPU's own
+x_HI field (the spectrum stage alone), and within 1e-2 of the oracle's end to end: at 32^3
+the low bins hold 6 to 30 modes, and one flipped cell (3e-5 of the box, within the flip
+tolerance) moves such a bin by up to about 1e-2. The grid spacing is the 256^3, 500 Mpc
+workload's (1.95 Mpc)."""
 import numpy as np
 import pytest
 
@@ -89,6 +92,10 @@ def test_pops_parity(model, walkers, method, boxes):
             assert np.array_equal(cnt[w, j], rcnt)
             ok = rcnt > 0
             rel = np.abs(d2[w, j][ok] - rd2[ok]) / np.abs(rd2[ok])
+            assert rel.max() <= 10 * PS_TOL, (w, j, rel.max())
+            own = oracle.Oracle().t0_mk(ZS[j]) * xhi[w, j].astype(np.float64) * (1.0 + boxes[j].astype(np.float64))
+            od2, _, _ = oracle.power_spectrum(own, BOX)
+            rel = np.abs(d2[w, j][ok] - od2[ok]) / np.abs(od2[ok])
             assert rel.max() <= PS_TOL, (w, j, rel.max())
 
 
