@@ -417,6 +417,14 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
+        # one more replay with per-launch events: the share of each kernel class (not timed above)
+        ctx.trace(True)
+        ctx.likelihood(d_params, d_mock, d_sigma)
+        torch.cuda.synchronize()
+        cls = ctx.trace_read()
+        ctx.trace(False)
+        total = sum(v[0] for v in cls.values()) or 1.0
+        share = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total} for k, v in cls.items() if v[1] > 0}
         rank, _ = ctx.basis_info()[:2]
         radii = sum(len(ctx.walker_ladder(k)) for k in range(w)) * len(zs)
         launches = ctx.launch_count()
@@ -425,7 +433,7 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
             "workload": "256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
                         "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc",
             "radius_tasks_per_step": radii, "basis_rank": rank, "gpu_launches_per_step": launches,
-            "dtype": "f32 (FP64 tables)"}
+            "classes_traced_step": share, "dtype": "f32 (FP64 tables)"}
 
 
 def main():

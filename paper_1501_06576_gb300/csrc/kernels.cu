@@ -282,8 +282,8 @@ constexpr int kL = 256;
 constexpr int kLLines = 16;                            // lines per CTA
 constexpr int kLThreads = 16 * kLLines;                // a team of 16 threads per line
 constexpr int kLStride = kL + kL / 16 + 1;             // 273 float2 per padded line
-constexpr size_t kLSmem = (size_t)kLLines * kLStride * sizeof(float2) + kL * sizeof(float2) +
-                          (size_t)kPrivBins * kLThreads * sizeof(float);
+constexpr size_t kLSmemRows = (size_t)kLLines * kLStride * sizeof(float2) + kL * sizeof(float2);
+constexpr size_t kLSmem = kLSmemRows + (size_t)kPrivBins * kLThreads * sizeof(float);   // column pass
 __device__ __forceinline__ int lpad(int p) { return p + (p >> 4); }
 
 enum LineMode : int { kLineStore = 0, kLineFilter = 1, kLinePs = 2 };
@@ -829,7 +829,7 @@ cudaError_t plane_forward(eor_ctx* c, const float2* src, float2* dst) {
         LineArgs la{};
         la.src = src; la.dst = dst; la.G = 1;
         trace_begin(c, kKForward);
-        k_lines_rows<-1><<<dim3(NH * 16, 1, 1), kLThreads, kLSmem, c->stream>>>(la);
+        k_lines_rows<-1><<<dim3(NH * 16, 1, 1), kLThreads, kLSmemRows, c->stream>>>(la);
         trace_end(c);
         la.src = dst;
         trace_begin(c, kKForward);
@@ -857,7 +857,7 @@ cudaError_t plane_filter_inverse(eor_ctx* c, const Pass1Args& a1, int P, int cls
         trace_end(c);
         la.src = a1.inter;
         trace_begin(c, cls);
-        k_lines_rows<+1><<<dim3(NH * 16, a1.G, P), kLThreads, kLSmem, c->stream>>>(la);
+        k_lines_rows<+1><<<dim3(NH * 16, a1.G, P), kLThreads, kLSmemRows, c->stream>>>(la);
         trace_end(c);
     } else {
         trace_begin(c, cls);
@@ -876,7 +876,7 @@ cudaError_t plane_ps(eor_ctx* c, const PSArgs& ap, int planes, int P) {
         la.pairs = ap.pairs; la.pair0 = ap.pair0; la.n_pairs = ap.n_pairs;
         la.bin_of_m2 = ap.bin_of_m2; la.ps_sum = ap.ps_sum; la.n_bins = ap.n_bins; la.kf3 = ap.kf3;
         trace_begin(c, kKPsPlane);
-        k_lines_rows<-1><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
+        k_lines_rows<-1><<<dim3(planes * 16, 1, P), kLThreads, kLSmemRows, c->stream>>>(la);
         trace_end(c);
         trace_begin(c, kKPsPlane);
         k_lines_cols<-1, kLinePs><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
@@ -894,8 +894,8 @@ cudaError_t prepare_n() {
     cudaError_t e;
     if ((e = set_smem(k_pencil_forward<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if constexpr (N == kL) {
-        if ((e = set_smem(k_lines_rows<-1>, kLSmem)) != cudaSuccess) return e;
-        if ((e = set_smem(k_lines_rows<+1>, kLSmem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_rows<-1>, kLSmemRows)) != cudaSuccess) return e;
+        if ((e = set_smem(k_lines_rows<+1>, kLSmemRows)) != cudaSuccess) return e;
         if ((e = set_smem(k_lines_cols<-1, kLineStore>, kLSmem)) != cudaSuccess) return e;
         if ((e = set_smem(k_lines_cols<+1, kLineFilter>, kLSmem)) != cudaSuccess) return e;
         if ((e = set_smem(k_lines_cols<-1, kLinePs>, kLSmem)) != cudaSuccess) return e;

@@ -121,7 +121,8 @@ constexpr float kNever = 1.0e30f;                         // folded threshold th
 constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
 static_assert(kTmemCols <= 512, "tensor memory");
 static_assert(kTmemBufs % kEpiSets == 0, "a set always meets the same buffers");
-static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0 && (kGroupsPerChunk * 16) % 16 == 0,
+              "bulk copies move multiples of 16 bytes");
 static_assert(kTcEpiSet == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
 static_assert(kTcN == 128 && kGroup == 32, "k_format_b: one block per chunk, one warp per group; 4 epilogue groups");
 
@@ -322,8 +323,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             owedB[st] = (int)(use & 1u);
             if (use > 0) ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kTries, abort);
             if (!ok) { record_timeout(a.err, 1, 5, c); break; }
-            tc::mbar_expect_tx(barM + st, kMBytes);
-            tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, kMBytes, barM + st);
+            // the per-column widths are read only with a mass-dependent efficiency
+            const uint32_t mbytes = a.ftab ? kMBytes : kGroupsPerChunk * 16;
+            tc::mbar_expect_tx(barM + st, mbytes);
+            tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, mbytes, barM + st);
             owedM[st] = (int)(use & 1u);
         }
         if (!ok) *abort = 1;
