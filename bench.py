@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--mcmc-steps", type=int, default=10)
     ap.add_argument("--no-two-pop", action="store_true", help="skip the 256^3 two-population leg")
     ap.add_argument("--two-pop-walkers", type=int, default=64)
+    ap.add_argument("--two-pop-only", action="store_true",
+                    help="time only the 256^3 two-population workload (its own JSON object)")
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
     ap.add_argument("--emu-steps", type=int, default=32000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
@@ -455,6 +457,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     W = args.walkers
+    if args.two_pop_only:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"two_population": time_two_pop(eor21, synth, torch, stream, flush, args)}))
+        return 0
 
     delta = synth.density_boxes(N, BOX, ZS, seed=1)
     mock_delta = synth.density_boxes(N, BOX, ZS, seed=2)

@@ -20,7 +20,7 @@ constexpr int kBasisCand = 512;            // candidate radii of the filter basi
 constexpr int kBasisMax = 48;              // largest filter basis
 constexpr double kBasisTol = 1e-6;         // max |W - projection| over candidates and |k| (FP32 level)
 constexpr int kCoefGrid = 8192;            // uniform R grid of the basis coefficient table
-constexpr int kFTab = 2048;                // entries of a walker's partial-ionization table in nu
+constexpr int kFTab = 1024;                // entries of a walker's partial-ionization table in nu
 
 // Device error word bits (set by kernels, read by the host).
 enum : int {
@@ -47,11 +47,11 @@ struct PairInfo {
 // Efficiency-weighted collapsed fraction at nu = delta_c - delta_R from a pair's table
 // (kFTab values at nu = i / inv_h; nu <= 0: the collapsed-region value in entry 0).
 __device__ __forceinline__ float pop_table_f(const float* tab, float nu, float inv_h) {
-    if (!(nu > 0.0f)) return __ldg(tab);
+    if (!(nu > 0.0f)) return tab[0];
     const float x = nu * inv_h;
-    if (x >= (float)(kFTab - 1)) return __ldg(tab + kFTab - 1);
+    if (x >= (float)(kFTab - 1)) return tab[kFTab - 1];
     const int i = (int)x;
-    const float a = __ldg(tab + i), b = __ldg(tab + i + 1);
+    const float a = tab[i], b = tab[i + 1];
     return fmaf(x - (float)i, b - a, a);
 }
 

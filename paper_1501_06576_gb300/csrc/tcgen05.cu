@@ -105,10 +105,14 @@ constexpr uint32_t kABytes = 2 * kTcTiles * kTileBytes;   // hi and lo tiles of 
 constexpr uint32_t kBBytes = 2 * kTcN * tc::kKMax * 4;    // hi and lo of a chunk (32 KB)
 // chunk meta: one 16-byte record per group of kGroup columns: (walker << 2 | first << 1 |
 // last, or -1 for an unused group; zeta, T_0, 1/sqrt(2 s^2(R_cell)) or 0 when s^2 <= 0, or
-// with a mass-dependent efficiency the inverse step of the pair's table), then per column the
-// width delta_hi - delta_crit of its flag interval (+inf for the step-function efficiency)
+// with a mass-dependent efficiency the inverse step of the pair's table). With a
+// mass-dependent efficiency two more parts follow: per column the width delta_hi -
+// delta_crit of its flag interval, and per group the partial-ionization table of the walker
+// that ends there (kFTab floats), so that the epilogue reads both from shared memory.
 constexpr int kGroupsPerChunk = kTcN / kGroup;
-constexpr uint32_t kMBytes = kGroupsPerChunk * 16 + kTcN * 4;
+constexpr uint32_t kMRecBytes = kGroupsPerChunk * 16;
+constexpr uint32_t kMTabOff = kMRecBytes + kTcN * 4;
+constexpr uint32_t kMBytes = kMTabOff + kGroupsPerChunk * kFTab * 4;
 constexpr uint32_t kChunkBytes = kBBytes + kMBytes;       // one chunk in global memory
 constexpr int kTmemBufs = 2;                              // accumulator buffers in tensor memory
 constexpr uint32_t kTmemCols = kTmemBufs * kTcTiles * kTcN;   // 2 buffers x kTcTiles x kTcN columns (512)
@@ -121,7 +125,7 @@ constexpr float kNever = 1.0e30f;                         // folded threshold th
 constexpr float kXScale = 8388608.0f;                     // 2^23: x_HI in fixed point for exact sums
 static_assert(kTmemCols <= 512, "tensor memory");
 static_assert(kTmemBufs % kEpiSets == 0, "a set always meets the same buffers");
-static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0 && (kGroupsPerChunk * 16) % 16 == 0,
+static_assert(kMBytes % 16 == 0 && kChunkBytes % 16 == 0 && kMRecBytes % 16 == 0,
               "bulk copies move multiples of 16 bytes");
 static_assert(kTcEpiSet == 2 * 128 * kTcTiles, "two epilogue threads per cell: groups 0-1 and 2-3 of a chunk");
 static_assert(kTcN == 128 && kGroup == 32, "k_format_b: one block per chunk, one warp per group; 4 epilogue groups");
@@ -156,8 +160,9 @@ __global__ void k_format_a(const float* F, int kb, int rank, long long n3, int n
 __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* gmeta, const int* ncols,
                                                    const float* coef, const PairInfo* pairs, int kb, int rank,
                                                    int max_radii,
-                                                   int n_z, int chunks_per_z, float delta_c, int pops,
+                                                   int n_z, int chunks_per_z, float delta_c, const float* ftab,
                                                    unsigned char* out) {
+    const int pops = ftab != nullptr;
     const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kTcN + row;
     const int nc = *ncols;
     unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * kChunkBytes;
@@ -172,7 +177,16 @@ __global__ void __launch_bounds__(kTcN) k_format_b(const int* cols, const int* g
         thr = j == pi.n_r - 1 ? delta_c : (isfinite(dcrit) ? dcrit : kNever);
         if (j != pi.n_r - 1 && isfinite(dcrit) && isfinite(pi.delta_hi[j])) width = pi.delta_hi[j] - dcrit;
     }
-    reinterpret_cast<float*>(chunk + kBBytes + kGroupsPerChunk * 16)[row] = width;
+    reinterpret_cast<float*>(chunk + kBBytes + kMRecBytes)[row] = width;
+    if (pops) {   // the tables of the walkers that end in each group
+        for (int g = 0; g < kGroupsPerChunk; g++) {
+            const int gi = blockIdx.x * kGroupsPerChunk + g;
+            const int info = gi < nc / kGroup ? gmeta[gi] : -1;
+            float* dst = reinterpret_cast<float*>(chunk + kBBytes + kMTabOff) + g * kFTab;
+            const float* src = info >= 0 && (info & 1) ? ftab + ((size_t)(info >> 2) * n_z + zi) * kFTab : nullptr;
+            for (int e = row; e < kFTab; e += kTcN) dst[e] = src ? src[e] : 0.0f;
+        }
+    }
     for (int b = 0; b < tc::kKMax; b++) {
         const float v = b < rank ? (src ? src[b] : 0.0f) : (b == rank ? -thr : 0.0f);
         const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             if (use > 0) ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kTries, abort);
             if (!ok) { record_timeout(a.err, 1, 5, c); break; }
             // the per-column widths are read only with a mass-dependent efficiency
-            const uint32_t mbytes = a.ftab ? kMBytes : kGroupsPerChunk * 16;
+            const uint32_t mbytes = a.ftab ? kMBytes : kMRecBytes;
             tc::mbar_expect_tx(barM + st, mbytes);
             tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, mbytes, barM + st);
             owedM[st] = (int)(use & 1u);
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) +
                                   (uint32_t)(tb * kTcTiles * kTcN + q * kTcN + g0 * kGroup);
             int4 m[2];
-            float dd[2];
+            float dd[2], pf[2] = {0.0f, 0.0f};
             uint32_t fa[2];
             {
                 float v[2][32];
@@ -403,8 +417,14 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                 const bool second = (m[1].x & 2) == 0;   // group 1 continues the walker of group 0
                 if (a.ftab) {
                     // mass-dependent efficiency: flagged where 0 <= D <= width (the interval of
-                    // delta_R between the two crossings of zeta f_coll = 1)
-                    const float* wd = reinterpret_cast<const float*>(Ms + st * kMBytes + kGroupsPerChunk * 16) + g0 * kGroup;
+                    // delta_R between the two crossings of zeta f_coll = 1); the efficiency-
+                    // weighted f_coll at R_cell from the ending walker's table in nu = -D
+                    const unsigned char* meta = Ms + st * kMBytes;
+                    const float* wd = reinterpret_cast<const float*>(meta + kMRecBytes) + g0 * kGroup;
+                    const float* tb = reinterpret_cast<const float*>(meta + kMTabOff) + g0 * kFTab;
+                    const float d1 = second ? v[0][0] : v[1][0];
+                    const float f0 = (m[0].x >= 0 && (m[0].x & 1)) ? pop_table_f(tb, -v[0][0], __int_as_float(m[0].w)) : 0.0f;
+                    const float f1 = (m[1].x >= 0 && (m[1].x & 1)) ? pop_table_f(tb + kFTab, -d1, __int_as_float(m[1].w)) : 0.0f;
                     bool n0 = true, n1 = true;
 #pragma unroll
                     for (int i = 1; i < 32; i++) {
@@ -415,6 +435,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                     tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
                     fa[0] = n0 ? 0x80000000u : 0u;
                     fa[1] = (second ? (n0 && n1 && c10) : n1) ? 0x80000000u : 0u;
+                    pf[0] = f0;
+                    pf[1] = f1;
                 } else {
                     tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
                     // flags: AND of sign bits over the walker's radii above R_cell (column 0 of its
@@ -431,11 +453,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             for (int u = 0; u < 2; u++) {   // two independent chains
                 const float zeta = __int_as_float(m[u].y), inv = __int_as_float(m[u].w);
                 if (a.ftab) {
-                    // efficiency-weighted f_coll at R_cell from the pair's table in nu = -D
-                    const bool ends = m[u].x >= 0 && (m[u].x & 1);
-                    const float f = ends ? pop_table_f(a.ftab + ((size_t)(m[u].x >> 2) * a.n_z + zi) * kFTab, -dd[u], inv)
-                                         : 0.0f;
-                    xh[u] = 1.0f - fminf(1.0f, f);
+                    xh[u] = 1.0f - fminf(1.0f, pf[u]);
                 } else {
                     // f_coll at R_cell (1 where delta_R >= delta_c), no ionization where s^2 <= 0
                     const float f = dd[u] >= 0.0f ? 1.0f : erfc_cheb(-dd[u] * inv);
@@ -562,8 +580,7 @@ cudaError_t build_columns(eor_ctx* c, int n_walkers) {
     k_format_b<<<dim3(chunks, c->cfg.n_z), kTcN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
                                                                c->d_pairs, c->kb, c->basis_rank, c->max_radii, c->cfg.n_z,
                                                                chunks,
-                                                               (float)c->cfg.delta_c, c->cfg.efficiency_model ? 1 : 0,
-                                                               c->d_tcB);
+                                                               (float)c->cfg.delta_c, pop_tables(c), c->d_tcB);
     trace_end(c);
     return cudaGetLastError();
 }
