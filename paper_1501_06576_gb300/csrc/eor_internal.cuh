@@ -45,14 +45,20 @@ struct PairInfo {
 };
 
 // Efficiency-weighted collapsed fraction at nu = delta_c - delta_R from a pair's table
-// (kFTab values at nu = i / inv_h; nu <= 0: the collapsed-region value in entry 0).
+// (kFTab values at nu = i / inv_h; nu <= 0: the collapsed-region value in entry 0), by
+// Catmull-Rom cubic interpolation (end intervals use a linearly extrapolated neighbour),
+// clamped at 0.
 __device__ __forceinline__ float pop_table_f(const float* tab, float nu, float inv_h) {
     if (!(nu > 0.0f)) return tab[0];
     const float x = nu * inv_h;
     if (x >= (float)(kFTab - 1)) return tab[kFTab - 1];
     const int i = (int)x;
-    const float a = tab[i], b = tab[i + 1];
-    return fmaf(x - (float)i, b - a, a);
+    const float t = x - (float)i;
+    const float p1 = tab[i], p2 = tab[i + 1];
+    const float p0 = i > 0 ? tab[i - 1] : 2.0f * p1 - p2;
+    const float p3 = i + 2 < kFTab ? tab[i + 2] : 2.0f * p2 - p1;
+    const float c3 = 3.0f * (p1 - p2) + p3 - p0, c2 = 2.0f * p0 - 5.0f * p1 + 4.0f * p2 - p3;
+    return fmaxf(0.0f, fmaf(0.5f * t, p2 - p0 + t * (c2 + t * c3), p1));
 }
 
 // Per walker (FP64 ladder, kept for diagnostics).
