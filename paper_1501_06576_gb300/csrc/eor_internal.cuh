@@ -209,7 +209,7 @@ size_t basis_ionize_smem(int kb, int max_radii);
 int basis_cells_per_cta();
 
 // tcgen05.cu
-size_t basis_tc_smem();
+size_t basis_tc_smem(bool pops);
 bool basis_tc_fits(int rank);
 size_t basis_tc_a_bytes(long long n3, int n_z);
 size_t basis_tc_b_bytes(const eor_ctx* c);

@@ -269,12 +269,17 @@ struct TcArgs {
 // epilogue's read of chunk c's meta; MMA(c) reuses the tensor memory of chunk c - 2 after
 // its epilogue. Every wait is bounded in GPU time; on a timeout the CTA records where, sets
 // kErrTimeout, waits for its copies and MMAs in flight and frees its tensor memory.
+// POPS: the mass-dependent efficiency (interval flags, partial ionization from the tables
+// in the chunk meta); otherwise the step function (sign-bit AND, erfc). The meta stage holds
+// only the group records without POPS.
+template <bool POPS>
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(TcArgs a) {
+    constexpr uint32_t kMB = POPS ? kMBytes : kMRecBytes;  // meta bytes copied and staged per chunk
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* As = sm;                                // A hi tiles then lo tiles
     unsigned char* Bs = As + kABytes;                      // [kTcStages][kBBytes]
-    unsigned char* Ms = Bs + kTcStages * kBBytes;          // [kTcStages][kMBytes]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kTcStages * kMBytes);
+    unsigned char* Ms = Bs + kTcStages * kBBytes;          // [kTcStages][kMB]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kTcStages * kMB);
     uint64_t* barA = bars;
     uint64_t* barB = bars + 1;                  // [kTcStages] coefficient tile landed
     uint64_t* barBe = barB + kTcStages;         // [kTcStages] its MMAs are done: stage free
@@ -337,10 +342,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             owedB[st] = (int)(use & 1u);
             if (use > 0) ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kTries, abort);
             if (!ok) { record_timeout(a.err, 1, 5, c); break; }
-            // the per-column widths are read only with a mass-dependent efficiency
-            const uint32_t mbytes = a.ftab ? kMBytes : kMRecBytes;
-            tc::mbar_expect_tx(barM + st, mbytes);
-            tc::bulk_g2s(Ms + st * kMBytes, Bg + (size_t)c * kChunkBytes + kBBytes, mbytes, barM + st);
+            tc::mbar_expect_tx(barM + st, kMB);
+            tc::bulk_g2s(Ms + st * kMB, Bg + (size_t)c * kChunkBytes + kBBytes, kMB, barM + st);
             owedM[st] = (int)(use & 1u);
         }
         if (!ok) *abort = 1;
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                 break;
             }
             tc::fence_after_sync();
-            const int4* gm = reinterpret_cast<const int4*>(Ms + st * kMBytes) + g0;
+            const int4* gm = reinterpret_cast<const int4*>(Ms + st * kMB) + g0;
             const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) +
                                   (uint32_t)(tb * kTcTiles * kTcN + q * kTcN + g0 * kGroup);
             int4 m[2];
@@ -415,11 +418,11 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                 m[0] = gm[0];
                 m[1] = gm[1];
                 const bool second = (m[1].x & 2) == 0;   // group 1 continues the walker of group 0
-                if (a.ftab) {
+                if constexpr (POPS) {
                     // mass-dependent efficiency: flagged where 0 <= D <= width (the interval of
                     // delta_R between the two crossings of zeta f_coll = 1); the efficiency-
                     // weighted f_coll at R_cell from the ending walker's table in nu = -D
-                    const unsigned char* meta = Ms + st * kMBytes;
+                    const unsigned char* meta = Ms + st * kMB;
                     const float* wd = reinterpret_cast<const float*>(meta + kMRecBytes) + g0 * kGroup;
                     const float* tb = reinterpret_cast<const float*>(meta + kMTabOff) + g0 * kFTab;
                     const float d1 = second ? v[0][0] : v[1][0];
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
 #pragma unroll
             for (int u = 0; u < 2; u++) {   // two independent chains
                 const float zeta = __int_as_float(m[u].y), inv = __int_as_float(m[u].w);
-                if (a.ftab) {
+                if constexpr (POPS) {
                     xh[u] = 1.0f - fminf(1.0f, pf[u]);
                 } else {
                     // f_coll at R_cell (1 where delta_R >= delta_c), no ionization where s^2 <= 0
@@ -550,8 +553,9 @@ int tc_slots(const eor_ctx* c) {
 
 bool basis_tc_fits(int rank) { return rank + 1 <= tc::kKMax; }   // basis values plus the constant column
 
-size_t basis_tc_smem() {
-    return kABytes + kTcStages * (kBBytes + kMBytes) + (4 * kTcStages + 2 * kTmemBufs + 2) * sizeof(uint64_t) + 16;
+size_t basis_tc_smem(bool pops) {
+    return kABytes + kTcStages * (kBBytes + (pops ? kMBytes : kMRecBytes)) +
+           (4 * kTcStages + 2 * kTmemBufs + 2) * sizeof(uint64_t) + 16;
 }
 size_t basis_tc_a_bytes(long long n3, int n_z) { return (size_t)n_z * (size_t)(n3 / kTcCells) * kABytes; }
 size_t basis_tc_b_bytes(const eor_ctx* c) { return (size_t)c->cfg.n_z * (size_t)(tc_slots(c) / kTcN) * kChunkBytes; }
@@ -560,7 +564,10 @@ size_t basis_tc_column_slots(const eor_ctx* c) { return (size_t)tc_slots(c); }
 cudaError_t prepare_basis_tc(eor_ctx* c) {
     (void)c;
     cudaError_t e =
-        cudaFuncSetAttribute(k_basis_ionize_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)basis_tc_smem());
+        cudaFuncSetAttribute(k_basis_ionize_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)basis_tc_smem(false));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_basis_ionize_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)basis_tc_smem(true));
     return e;
 }
 
@@ -592,7 +599,11 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, brightness_base(c), c->d_dtb, xhi_out, c->d_xq, pop_tables(c), c->d_err,
              c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3};
     trace_begin(c, kKBasis);
-    k_basis_ionize_tc<<<dim3((unsigned)(c->n3 / kTcCells), c->cfg.n_z), kTcThreads, basis_tc_smem(), c->stream>>>(a);
+    const dim3 grid((unsigned)(c->n3 / kTcCells), c->cfg.n_z);
+    if (a.ftab)
+        k_basis_ionize_tc<true><<<grid, kTcThreads, basis_tc_smem(true), c->stream>>>(a);
+    else
+        k_basis_ionize_tc<false><<<grid, kTcThreads, basis_tc_smem(false), c->stream>>>(a);
     trace_end(c);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     trace_begin(c, kKFinish);
