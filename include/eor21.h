@@ -8,7 +8,9 @@
  * Call order (EOR_ESTATE otherwise):
  *   eor_create -> eor_init_boxes -> eor_set_params -> eor_run_ionization
  *              -> eor_power_spectrum -> eor_chi2
- * eor_likelihood runs set_params .. chi2 as one call (one CUDA-graph replay).
+ * eor_likelihood runs set_params .. chi2 as one call (one CUDA-graph replay). With a
+ * mass-dependent efficiency (eor_config.efficiency_model 1 or 2), eor_set_efficiency
+ * comes before eor_set_params / eor_likelihood.
  *
  * Memory: the caller owns every pointer it passes; the library copies inputs and
  * never keeps a caller pointer past the call. The library owns its device memory
@@ -24,6 +26,7 @@
  * Layouts (row-major, last index fastest):
  *   density boxes   float [n_z][n][n][n]      (x, y, z), box j at redshift cfg.z[j]
  *   walker params   double [n_walkers][3]     (zeta, R_mfp [Mpc], log10 T_vir [K])
+ *   efficiency      double [n_walkers][4]     (efficiency_model 1 and 2, see eor_config)
  *   x_HI boxes      float [n_walkers][n_z][n][n][n]
  *   x_HI means      double [n_walkers][n_z]
  *   spectra         double [n_walkers][n_z][n_bins]  (Delta^2 in mK^2, mean |k| in 1/Mpc)
