@@ -139,3 +139,25 @@ def test_ionize_pops_monotone_in_efficiency(o):
     assert np.all(hi["xhi"] <= lo["xhi"] + 1e-12)
     assert np.all(lo["flag"] <= hi["flag"])
     assert 0.0 <= hi["xhi"].min() and lo["xhi"].max() <= 1.0
+
+
+def test_feedback_form_without_faint_range(o):
+    # T_F below the atomic-cooling threshold: no faint population, the bright one starts at
+    # M(10^4 K) and is pivoted at M_F
+    pops = o.populations(2, (40.0, 10.0, 3.8), (1.0, -0.2, 0.0, 0.0), 9.0)
+    assert pops.shape == (1, 5)
+    assert pops[0][3] == pytest.approx(o.mmin(1e4, 9.0), rel=1e-12)
+    assert pops[0][1] == pytest.approx(o.mmin(10 ** 3.8, 9.0), rel=1e-12)
+    assert pops[0][2] == pytest.approx(2.0 * -0.2 / 3.0)
+    assert pops[0][4] == 0.0
+
+
+def test_two_population_model_second_population_off(o, z9):
+    # zeta_20 = 0 in model 1 adds nothing
+    _, tab = z9
+    one = o.populations(1, (25.0, 10.0, 4.6), (0.2, 0.0, 0.4, 5.0), 9.0)
+    assert one.shape == (2, 5)
+    m_r = _m_r(o, 5.0)
+    single = one[:1]
+    for dr in (0.3, 1.2):
+        assert tab.fcoll(one, m_r, dr) == pytest.approx(tab.fcoll(single, m_r, dr), rel=1e-14)
