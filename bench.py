@@ -17,6 +17,7 @@ workload instead.
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -431,11 +432,46 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
         radii = sum(len(ctx.walker_ladder(k)) for k in range(w)) * len(zs)
         launches = ctx.launch_count()
         ctx.close()
+    rates = two_pop_rates(share, rank, radii, n, box, w * len(zs))
     return {"value": w / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms, "walkers": w,
             "workload": "256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
                         "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc",
             "radius_tasks_per_step": radii, "basis_rank": rank, "gpu_launches_per_step": launches,
-            "classes_traced_step": share, "dtype": "f32 (FP64 tables)"}
+            "classes_traced_step": share, "rates": rates, "dtype": "f32 (FP64 tables)"}
+
+
+def two_pop_rates(share, rank: int, radii: int, n: int, box: float, pairs: int) -> dict:
+    """Achieved rates of the traced replay: the contraction's useful TFLOP/s (2 x rank flop per
+    cell and radius task) and the power spectrum's algorithmic GB/s (per (walker, z): the R2C
+    pencil pass reads the n^3 delta T_b box and writes the nh n^2 half spectrum; the row pass
+    reads and writes, the column pass reads, the planes holding a binned mode)."""
+    out = {}
+    try:
+        hbm_peak, hbm_kind = measured_peak()
+        c_ms = share.get("basis_ionize", {}).get("ms", 0.0)
+        if c_ms > 0:
+            tflops = 2.0 * rank * n ** 3 * radii / (c_ms / 1e3) / 1e12
+            peak, kind = tf32_peak_tflops()
+            out["contraction"] = {"achieved": tflops, "unit": "TFLOP/s", "peak": peak, "frac": tflops / peak,
+                                  "peak_kind": kind}
+        kf = 2.0 * math.pi / box
+        planes = 0
+        while planes < n // 2 + 1 and kf * planes < 1.5:
+            planes += 1
+        plane_bytes = n * n * 8
+        fwd_ms = share.get("forward_fft", {}).get("ms", 0.0)
+        ps_ms = share.get("ps_plane", {}).get("ms", 0.0)
+        if fwd_ms > 0:
+            b = pairs * (n ** 3 * 4 + (n // 2 + 1) * plane_bytes)
+            out["pencil_r2c"] = {"achieved": b / (fwd_ms / 1e3) / 1e9, "unit": "GB/s", "peak": hbm_peak,
+                                 "frac": b / (fwd_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": hbm_kind}
+        if ps_ms > 0:
+            b = pairs * 3 * planes * plane_bytes
+            out["ps_line_passes"] = {"achieved": b / (ps_ms / 1e3) / 1e9, "unit": "GB/s", "peak": hbm_peak,
+                                     "frac": b / (ps_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": hbm_kind}
+    except Exception as err:   # rates are a report; the timing above stands without them
+        out["error"] = str(err)
+    return out
 
 
 def main():
