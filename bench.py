@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--two-pop-walkers", type=int, default=64)
     ap.add_argument("--two-pop-only", action="store_true",
                     help="time only the 256^3 two-population workload (its own JSON object)")
+    ap.add_argument("--two-pop-efficiency", type=int, default=1, choices=[0, 1],
+                    help="efficiency model of the 256^3 leg (0: the step function, for comparison)")
     ap.add_argument("--emu-train", type=int, default=20000, help="simulated walkers the surrogate trains on")
     ap.add_argument("--emu-steps", type=int, default=32000, help="Adam steps of the surrogate")
     ap.add_argument("--emu-walkers", type=int, default=4096, help="walkers per surrogate likelihood call")
@@ -394,19 +396,22 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
     20 % of it. Timed with CUDA events over args.steps replays after two warm-up replays, L2
     flushed before the timed region."""
     n, box, zs, w = 256, 500.0, (8.0, 9.0, 10.0), args.two_pop_walkers
+    model = args.two_pop_efficiency
     rng = np.random.default_rng(31)
     base = np.column_stack([rng.uniform(5, 100, w), rng.uniform(5, 20, w), rng.uniform(4, 6, w)])
     extra = np.column_stack([rng.uniform(-0.5, 0.5, w), rng.uniform(5, 100, w), rng.uniform(-0.5, 0.5, w),
                              rng.uniform(4, 6, w)])
     with torch.cuda.stream(stream):
-        ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=w, efficiency_model=1, stream=stream.cuda_stream)
+        ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=w, efficiency_model=model, stream=stream.cuda_stream)
         ctx.init_boxes(torch.from_numpy(synth.density_boxes(n, box, zs, seed=11)).cuda())
-        ctx.set_efficiency(np.array([[0.3, 10.0, -0.3, 5.3]] * w))
+        if model:
+            ctx.set_efficiency(np.array([[0.3, 10.0, -0.3, 5.3]] * w))
         ctx.set_params(np.array([[30.0, 15.0, 4.7]]))
         ctx.run_ionization()
         mock = np.ascontiguousarray(ctx.power_spectrum()[0][0])
         ctx.init_boxes(torch.from_numpy(synth.density_boxes(n, box, zs, seed=10)).cuda())
-        ctx.set_efficiency(extra)
+        if model:
+            ctx.set_efficiency(extra)
         d_params = torch.from_numpy(base).cuda()
         d_mock = torch.from_numpy(mock).cuda()
         d_sigma = torch.from_numpy(0.2 * mock).cuda()
@@ -434,8 +439,10 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
         ctx.close()
     rates = two_pop_rates(share, rank, radii, n, box, w * len(zs))
     return {"value": w / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms, "walkers": w,
-            "workload": "256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
-                        "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc",
+            "workload": ("256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
+                         "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc") if model else
+                        "256^3, L = 500 Mpc, z = 8, 9, 10, step-function efficiency (comparison), zeta in [5, 100], "
+                        "log10 T_vir in [4, 6], R_mfp in [5, 20] Mpc",
             "radius_tasks_per_step": radii, "basis_rank": rank, "gpu_launches_per_step": launches,
             "classes_traced_step": share, "rates": rates, "dtype": "f32 (FP64 tables)"}
 
