@@ -423,21 +423,35 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                     // delta_R between the two crossings of zeta f_coll = 1); the efficiency-
                     // weighted f_coll at R_cell from the ending walker's table in nu = -D
                     const unsigned char* meta = Ms + st * kMB;
-                    const float* wd = reinterpret_cast<const float*>(meta + kMRecBytes) + g0 * kGroup;
+                    const float4* wd4 = reinterpret_cast<const float4*>(meta + kMRecBytes) + g0 * (kGroup / 4);
                     const float* tb = reinterpret_cast<const float*>(meta + kMTabOff) + g0 * kFTab;
                     const float d1 = second ? v[0][0] : v[1][0];
                     const float f0 = (m[0].x >= 0 && (m[0].x & 1)) ? pop_table_f(tb, -v[0][0], __int_as_float(m[0].w)) : 0.0f;
                     const float f1 = (m[1].x >= 0 && (m[1].x & 1)) ? pop_table_f(tb + kFTab, -d1, __int_as_float(m[1].w)) : 0.0f;
-                    bool n0 = true, n1 = true;
+                    // a column does not flag iff D < 0 or D > width: the sign bit of D | (width - D)
+                    // (width - D = +inf for an infinite width); the columns' values are replaced by
+                    // that word and AND-ed as for the step function
+                    float w10 = 0.0f;
 #pragma unroll
-                    for (int i = 1; i < 32; i++) {
-                        n0 = n0 && !(v[0][i] >= 0.0f && v[0][i] <= wd[i]);
-                        n1 = n1 && !(v[1][i] >= 0.0f && v[1][i] <= wd[kGroup + i]);
+                    for (int q = 0; q < kGroup / 4; q++) {
+                        const float4 wa = wd4[q], wb = wd4[kGroup / 4 + q];
+                        const float xa[4] = {wa.x, wa.y, wa.z, wa.w}, xb[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const int i = 4 * q + k;
+                            if (i == 0) {
+                                w10 = xb[0];
+                                continue;
+                            }
+                            v[0][i] = __uint_as_float(__float_as_uint(v[0][i]) | __float_as_uint(xa[k] - v[0][i]));
+                            v[1][i] = __uint_as_float(__float_as_uint(v[1][i]) | __float_as_uint(xb[k] - v[1][i]));
+                        }
                     }
-                    const bool c10 = !(v[1][0] >= 0.0f && v[1][0] <= wd[kGroup]);
                     tc::mbar_arrive(barMe + st);   // meta read: its stage may be refilled
-                    fa[0] = n0 ? 0x80000000u : 0u;
-                    fa[1] = (second ? (n0 && n1 && c10) : n1) ? 0x80000000u : 0u;
+                    const uint32_t x10 = __float_as_uint(v[1][0]) | __float_as_uint(w10 - v[1][0]);
+                    const uint32_t a0 = and31(v[0]), a1 = and31(v[1]);
+                    fa[0] = a0;
+                    fa[1] = second ? a0 & a1 & x10 : a1;
                     pf[0] = f0;
                     pf[1] = f1;
                 } else {
