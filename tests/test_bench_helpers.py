@@ -1,0 +1,45 @@
+"""Host-side helpers of bench.py (no GPU): the achieved-rate report of the two-population
+leg and the traffic-record lookup, so that an edit cannot break the JSON line."""
+import importlib.util
+import json
+import math
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_two_pop_rates_from_a_traced_step(bench):
+    share = {"basis_ionize": {"ms": 42.1}, "forward_fft": {"ms": 6.6}, "ps_plane": {"ms": 20.0},
+             "tables": {"ms": 8.8}}
+    r = bench.two_pop_rates(share, 24, 4797, 256, 500.0, 192)
+    assert set(r) == {"contraction", "pencil_r2c", "ps_line_passes"}
+    # useful flops: 2 x rank per cell and radius task
+    assert r["contraction"]["achieved"] == pytest.approx(2 * 24 * 256 ** 3 * 4797 / 42.1e-3 / 1e12)
+    # power spectrum: 3 passes over the planes below k_hi = 1.5 / Mpc (k_f = 2 pi / 500)
+    planes = math.ceil(1.5 / (2 * math.pi / 500.0))
+    assert r["ps_line_passes"]["achieved"] == pytest.approx(192 * 3 * planes * 256 * 256 * 8 / 20.0e-3 / 1e9)
+    for v in r.values():
+        assert 0 < v["frac"] < 2 and v["peak"] > 0
+
+
+def test_two_pop_rates_without_classes(bench):
+    assert bench.two_pop_rates({}, 24, 0, 256, 500.0, 0) == {}
+
+
+def test_traffic_record_matches_the_contraction_sources(bench):
+    # the committed ncu record is used only while the contraction sources hash to its value
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        rec = json.load(f)
+    assert rec["basis_source_hash"] == bench.basis_source_hash()
+    e = rec["per_launch"]["basis_ionize"]
+    assert e["bytes"] == e["read"] + e["write"]
