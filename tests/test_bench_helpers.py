@@ -36,10 +36,16 @@ def test_two_pop_rates_without_classes(bench):
     assert bench.two_pop_rates({}, 24, 0, 256, 500.0, 0) == {}
 
 
-def test_traffic_record_matches_the_contraction_sources(bench):
-    # the committed ncu record is used only while the contraction sources hash to its value
+def test_traffic_record_used_only_for_its_sources(bench):
+    # the committed ncu record feeds roofline.traffic only while the contraction sources
+    # hash to the recorded value and the workload is the recorded one; otherwise None
     with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
         rec = json.load(f)
-    assert rec["basis_source_hash"] == bench.basis_source_hash()
     e = rec["per_launch"]["basis_ionize"]
     assert e["bytes"] == e["read"] + e["write"]
+    got = bench.ncu_launch_traffic("basis_ionize", e["walkers"])
+    if rec["basis_source_hash"] == bench.basis_source_hash() and e["n"] == bench.N:
+        assert got == e["bytes"]
+    else:
+        assert got is None
+    assert bench.ncu_launch_traffic("basis_ionize", e["walkers"] + 1) is None
