@@ -304,6 +304,8 @@ int eor_tensor_core_check(const float* a, const float* b, float* d, int n, int* 
  * largest per-bin standard deviation of the members' log10 Delta^2 exceeds the threshold
  * tau (set by eor_emu_calibrate or eor_emu_set_threshold; +infinity before), when a
  * predicted bin lies below 10 x d2_floor, or when its parameters leave the prior box.
+ * The network's inputs are (zeta, R_mfp, log10 T_vir, z): it emulates the step-function
+ * efficiency (a context with efficiency_model 0) only.
  * -------------------------------------------------------------------------------------- */
 #define EOR21_EMU_MAX_HIDDEN 8
 #define EOR21_EMU_MAX_MEMBERS 8
@@ -432,7 +434,11 @@ typedef struct {
 } eor_mcmc_config;
 
 void eor_mcmc_default_config(eor_mcmc_config* cfg);   /* 128 walkers, a = 2, the workloads' prior box */
-/* ctx: the likelihood (boxes loaded); it must outlive the sampler, which runs on its stream. */
+/* ctx: the likelihood (boxes loaded); it must outlive the sampler, which runs on its stream.
+ * The sampled parameters are (zeta, R_mfp, log10 T_vir). With a mass-dependent efficiency
+ * (efficiency_model 1 or 2) the four efficiency parameters are held fixed: the
+ * likelihood of proposal slot i (of each half-ensemble call) uses row i of
+ * eor_set_efficiency, which must cover n_walkers / 2 rows (equal rows fix them for all). */
 int eor_mcmc_create(const eor_mcmc_config* cfg, eor_ctx* ctx, eor_mcmc** out);
 /* Starting walkers params double [n_walkers][3], mock and sigma as for eor_likelihood
  * (ignored without a context); lnp (optional) double [n_walkers] receives their log
