@@ -305,7 +305,8 @@ int eor_tensor_core_check(const float* a, const float* b, float* d, int n, int* 
  * tau (set by eor_emu_calibrate or eor_emu_set_threshold; +infinity before), when a
  * predicted bin lies below 10 x d2_floor, or when its parameters leave the prior box.
  * The network's inputs are (zeta, R_mfp, log10 T_vir, z): it emulates the step-function
- * efficiency (a context with efficiency_model 0) only.
+ * efficiency only, and eor_emu_likelihood returns EOR_ENOTSUP for a context with
+ * efficiency_model 1 or 2.
  * -------------------------------------------------------------------------------------- */
 #define EOR21_EMU_MAX_HIDDEN 8
 #define EOR21_EMU_MAX_MEMBERS 8

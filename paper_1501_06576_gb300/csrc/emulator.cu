@@ -1366,6 +1366,8 @@ int eor_emu_likelihood(eor_emu* m, eor_ctx* ctx, const double* params, int n_wal
     if (!m) return EOR_EINVAL;
     if (!ctx || !mock_d2 || !sigma || !chi2) return efail(m, EOR_EINVAL, "ctx, mock_d2, sigma or chi2 is NULL");
     if (ctx->stage < 1) return efail(m, EOR_ESTATE, "the simulation context has no density boxes");
+    if (ctx->cfg.efficiency_model != 0)
+        return efail(m, EOR_ENOTSUP, "the surrogate emulates the step-function efficiency (efficiency_model 0) only");
     if (ctx->cfg.n_z != m->Z || ctx->cfg.n_bins != m->B)
         return efail(m, EOR_EINVAL, "the simulation context covers other redshifts or bins");
     for (int j = 0; j < m->Z; j++)
