@@ -161,3 +161,14 @@ def test_two_population_model_second_population_off(o, z9):
     single = one[:1]
     for dr in (0.3, 1.2):
         assert tab.fcoll(one, m_r, dr) == pytest.approx(tab.fcoll(single, m_r, dr), rel=1e-14)
+
+
+def test_flat_feedback_form_is_the_step_function_at_the_cooling_threshold(o):
+    # alpha = beta = 0: faint [M(10^4 K), M_F) plus bright [M_F, inf) at the same zeta0 is one
+    # population of zeta0 above M(10^4 K), whatever T_F is
+    n, box, z = 16, 40.0, 8.5
+    d = synth.density_box(n, box, z, seed=9)
+    ref = o.ionize(d, box, z, 40.0, 9.0, 4.0)
+    got = o.ionize_pops(d, box, z, o.populations(2, (40.0, 9.0, 4.9), (0.0, 0.0, 0.0, 0.0), z), 9.0)
+    assert np.array_equal(got["flag"], ref["flag"])
+    assert np.abs(got["xhi"] - ref["xhi"]).max() < 1e-7
