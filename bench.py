@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-trace", action="store_true", help="time without the per-kernel event brackets")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
     ap.add_argument("--mcmc-steps", type=int, default=10)
@@ -79,25 +80,88 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
 
-def oracle_sample(seconds: float, walkers_params, delta, mock, sigma):
+def oracle_sample(seconds: float, walkers_params, delta, mock, sigma, gpu=None):
     """Time the FP64 oracle on (walker, redshift) realizations of the workload until the
-    budget is spent (at least one). Returns (evals/s, realizations, seconds, threads)."""
+    budget is spent (at least one). Returns (evals/s, realizations, seconds, threads, parity):
+    with gpu = (x_HI boxes [walker][z] (torch, device), Delta^2 [walker][z][bin]) of the
+    batched GPU path on the same walkers, parity holds the errors of those realizations
+    against the oracle's (outside the timed sum)."""
     import oracle
     orc = oracle.Oracle()
     t0 = time.perf_counter()
-    done = 0
+    done, el, errs = 0, 0.0, []
     while True:
         w, j = divmod(done, len(ZS))
         w %= len(walkers_params)
+        t1 = time.perf_counter()
         ion = orc.ionize(delta[j], BOX, ZS[j], *walkers_params[w])
         d2, _, cnt = oracle.power_spectrum(ion["dtb"], BOX, 14, 0.1, 1.5)
-        oracle.chi2(d2, cnt, mock[j], sigma[j])
+        c_ref = oracle.chi2(d2, cnt, mock[j], sigma[j])
+        el += time.perf_counter() - t1
         done += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
+        if gpu is not None:
+            xg = gpu[0][w, j].double().cpu().numpy()
+            diff = np.abs(xg - ion["xhi"])
+            flipped = diff > 1e-3
+            ok = cnt > 0
+            dg = gpu[1][w, j]
+            if ion["xhi_mean"] > 0.01:
+                pe = float(np.max(np.abs(dg[ok] - d2[ok]) / np.abs(d2[ok])))
+            else:
+                pe = float(np.max(np.abs(dg[ok] - d2[ok])) / max(np.max(np.abs(d2[ok])), 1e-6))
+            c_gpu = oracle.chi2(dg, cnt, mock[j], sigma[j])
+            errs.append((float(flipped.mean()), float(diff[~flipped].max()) if (~flipped).any() else 0.0, pe,
+                         abs(c_gpu - c_ref) / max(abs(c_ref), 1e-12)))
+        if time.perf_counter() - t0 >= seconds:
             break
     per_eval = el / done * len(ZS)
-    return 1.0 / per_eval, done, el, orc.threads
+    parity = None
+    if errs:
+        e = np.array(errs)
+        parity = {"realizations": len(errs), "flipped_frac_max": float(e[:, 0].max()),
+                  "xhi_abs_err_max": float(e[:, 1].max()), "xhi_abs_err_median": float(np.median(e[:, 1])),
+                  "d2_rel_err_max": float(e[:, 2].max()), "d2_rel_err_median": float(np.median(e[:, 2])),
+                  "chi2_rel_err_max": float(e[:, 3].max()),
+                  "tolerances": {"flipped": 1e-4, "xhi": 1e-4, "d2": 1e-3},
+                  "def": "batched GPU x_HI and Delta^2 of the sampled (walker, z) against the FP64 oracle; "
+                         "chi^2 per redshift on a flat mock (10 mK^2, sigma 20 %)"}
+    return 1.0 / per_eval, done, el, orc.threads, parity
+
+
+def oracle_one_thread():
+    """Seconds of one 128^3 realization (fiducial walker, z = 9) by the oracle on one host
+    thread, the setting of the paper's single-core timing (Sec. 2.3), and the CPU model."""
+    import oracle
+    from paper_1501_06576_gb300 import synth
+    orc = oracle.Oracle()
+    before = orc.threads
+    orc.lib.or_set_threads(1)
+    try:
+        box = synth.density_boxes(N, BOX, (9.0,), seed=1)[0]
+        t0 = time.perf_counter()
+        ion = orc.ionize(box, BOX, 9.0, *FIDUCIAL)
+        oracle.power_spectrum(ion["dtb"], BOX, 14, 0.1, 1.5)
+        secs = time.perf_counter() - t0
+    finally:
+        orc.lib.or_set_threads(before)
+    return secs
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def reference_arm(args, rank, world):
@@ -259,6 +323,30 @@ def tf32_peak_tflops():
     return bf16 * 1.1 / 2.25, kind
 
 
+def fp16_peak_tflops():
+    """Dense FP16 tensor peak: the measured BF16 GEMM peak (FP16 and BF16 run at the same
+    rate), sustained (the contraction runs inside a long step)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured bf16 sustained (FP16 runs at the BF16 rate)"
+    except Exception:
+        return 1700.0, "fallback bf16 sustained"
+
+
+def f16_column_chunks(ladders) -> int:
+    """256-column chunks of the FP16 contraction for walkers with these radius counts: each
+    walker's radii above R_cell in groups of 32 (at least one group; a two-group walker starts
+    on an even group)."""
+    g = 0
+    for nr in ladders:
+        ng = max(1, -(-(nr - 1) // 32))
+        if ng == 2 and g % 2:
+            g += 1
+        g += ng
+    return -(-g * 32 // 256)
+
+
 def algorithmic_bytes(n: int):
     """HBM bytes each FFT-pass kernel class must move per unit (one (walker, redshift,
     radius) task): complex64 half spectrum nh*n*n*8."""
@@ -284,6 +372,68 @@ def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, 
     ctx.set_method(eor21.EOR_METHOD_BASIS)
     return {"value": W * dsteps / (d0.elapsed_time(d1) / 1e3), "unit": "evals/s",
             "note": note or "filter + inverse FFT per radius (EOR_METHOD_DIRECT), same walkers"}
+
+
+def time_cufft(ctx, eor21, torch, stream, d_delta, d_params, d_mock, d_sigma, W, tasks, step_share):
+    """cuFFT (through torch.fft), timed only as a comparison for the hand-written FFT passes,
+    on the same transforms: (1) the forward R2C of the density boxes, once per box; (2) the
+    filter W(kR) times the density spectrum and the C2R back to the cells, per (walker, z,
+    radius), the work of the per-radius method; (3) the R2C of a delta T_b box, per (walker, z).
+    Each against the library's own kernels on the same workload (CUDA-event traces). Nothing
+    here feeds a result of the library."""
+    n, nz = N, len(ZS)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    with torch.cuda.stream(stream):
+        # (1) forward R2C of the n_z density boxes
+        ms = timed(lambda: torch.fft.rfftn(d_delta, dim=(1, 2, 3)))
+        ctx.trace(True)
+        ctx.init_boxes(d_delta)
+        ours = ctx.trace_read().get("forward_fft", (0.0, 0))[0]
+        out["density_r2c_per_box_ms"] = {"cufft": ms / nz, "ours": ours / nz}
+        # (2) filter + C2R per radius task, batches of 16 radii on one box
+        kf = 2.0 * math.pi / BOX
+        f = torch.fft.fftfreq(n, d=1.0 / n, device="cuda") * kf
+        fz = torch.fft.rfftfreq(n, d=1.0 / n, device="cuda") * kf
+        kk = torch.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + fz[None, None, :] ** 2)
+        spec = torch.fft.rfftn(d_delta[0], dim=(0, 1, 2))
+        radii = torch.exp(torch.linspace(math.log(1.3), math.log(20.0), 16, device="cuda")).view(16, 1, 1, 1)
+        x = kk[None] * radii
+        xs = torch.where(x > 1e-3, x, torch.ones_like(x))
+        win = torch.where(x > 1e-3, 3.0 * (torch.sin(xs) - xs * torch.cos(xs)) / xs ** 3, torch.ones_like(x))
+        ms = timed(lambda: torch.fft.irfftn(spec[None] * win, s=(n, n, n), dim=(1, 2, 3)))
+        ctx.set_method(eor21.EOR_METHOD_DIRECT)
+        ctx.likelihood(d_params, d_mock, d_sigma)
+        t = ctx.trace_read()
+        ctx.set_method(eor21.EOR_METHOD_BASIS)
+        ctx.trace(False)
+        ours = t.get("filter_plane", (0.0, 0))[0] + t.get("pencil_ionize", (0.0, 0))[0]
+        out["filter_c2r_per_radius_ms"] = {"cufft": ms / 16, "ours_direct_method": ours / max(tasks, 1),
+                                           "note": "ours also tests Eq. 1 per cell and, at R_cell, forms x_HI, "
+                                                   "delta T_b and its R2C along z"}
+        del x, xs, win
+        # (3) R2C of delta T_b boxes, batches of 32
+        boxes = torch.randn((32, n, n, n), dtype=torch.float32, device="cuda")
+        ms = timed(lambda: torch.fft.rfftn(boxes, dim=(1, 2, 3)))
+        ours = (step_share.get("forward_fft", 0.0) + step_share.get("ps_plane", 0.0)) / (W * nz)
+        out["dtb_r2c_per_pair_ms"] = {"cufft": ms / 32, "ours": ours,
+                                      "note": "ours also bins k^3 |X|^2 into the 14 shells (FP64 sums)"}
+        del boxes
+    for v in out.values():
+        v["ours_over_cufft"] = (v.get("ours") or v.get("ours_direct_method")) / v["cufft"]
+    return out
 
 
 def time_emulator(ctx, eor21, synth, torch, stream, flush, d_mock, d_sigma, args):
@@ -561,9 +711,10 @@ def main():
 
         # units: one per (walker, z, radius)
         ctx.set_params(params)
-        tasks_per_step = sum(len(ctx.walker_ladder(w)) for w in range(W)) * len(ZS)
+        ladders = [len(ctx.walker_ladder(w)) for w in range(W)]
+        tasks_per_step = sum(ladders) * len(ZS)
         basis_rank, basis_resid = ctx.basis_info()
-        uses_tensor_cores = basis_rank + 1 <= 32   # basis values plus the folded threshold fit K = 32
+        contract_kind, k_slots = ctx.contraction_info()
 
         # ---------------- the per-radius FFT method on the same workload (for comparison)
         ctx.trace(False)
@@ -605,6 +756,20 @@ def main():
         torch.cuda.synchronize()
         plain = pw / (p0.elapsed_time(p1) / 1e3)
 
+        # ---------------- x_HI and Delta^2 of the batch, for the oracle parity sample (untimed)
+        gpu_parity = None
+        if not args.no_cpu_baseline and world == 1:
+            ctx.set_params(params)
+            xg, _ = ctx.run_ionization(want_xhi=True, device=True)
+            gpu_parity = (xg, ctx.power_spectrum()[0])
+
+        # ---------------- cuFFT on the same transforms (comparison only)
+        cufft = None
+        if not args.no_cufft and rank == 0:
+            per_step = {k: v / args.steps for k, v in class_ms.items()}
+            cufft = time_cufft(ctx, eor21, torch, stream, torch.from_numpy(delta).cuda(), d_params, d_mock,
+                               d_sigma, W, tasks_per_step, per_step)
+
         # ---------------- the device-side ensemble sampler on the same likelihood
         mcmc = None
         if not args.no_mcmc and rank == 0:
@@ -641,7 +806,16 @@ def main():
             flops_per_unit = 2.0 * basis_rank * N ** 3
             units_per_launch = tasks_per_step * args.steps / launches_dom
             achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
-            if uses_tensor_cores:
+            if contract_kind == eor21.EOR_CONTRACT_FP16:
+                peak, peak_kind = fp16_peak_tflops()
+                # executed: the three products side by side along K (k_slots FP16 values), every
+                # cell against 256-column chunks of radii above R_cell
+                executed = 2 * k_slots * N ** 3 * f16_column_chunks(ladders) * 256 * len(ZS)
+                tf32, _ = tf32_peak_tflops()
+                extra = {"executed_fp16_tflops": executed * args.steps / launches_dom / (avg_launch_ms / 1e3) / 1e12,
+                         "frac_of_tf32_peak": achieved / tf32, "k_slots": k_slots}
+                bound = "tensor"
+            elif contract_kind == eor21.EOR_CONTRACT_TF32:
                 peak, peak_kind = tf32_peak_tflops()
                 # executed: 3 TF32 products (hi*hi, hi*lo, lo*hi) over K = rank + 1 rounded up to
                 # whole MMA steps of 8, and 64-column chunks
@@ -669,18 +843,27 @@ def main():
                     "peak_kind": peak_kind, "bytes_per_unit": per_unit.get(dom, 0),
                     "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
     hbm_peak, hbm_kind = measured_peak()
-    # the excursion-set path's algorithmic HBM bytes per (walker, z, radius): read the density
-    # spectrum (nh n^2 complex64) and read + write the cell's flag byte (2 n^3)
+    # the excursion-set path's algorithmic HBM bytes per (walker, z, radius) of a per-radius FFT
+    # design: read the density spectrum (nh n^2 complex64) and read + write the cell's flag byte
     task_bytes = (N // 2 + 1) * N * N * 8 + 2 * N ** 3
-    hbm_equiv = task_bytes * tasks_per_step * args.steps / (total_ms / 1e3) / 1e9
+    per_radius_rate = task_bytes * tasks_per_step * args.steps / (total_ms / 1e3) / 1e9
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         flat = np.full((len(ZS), 14), 10.0)     # the oracle takes no input from the GPU path
-        cv, nrel, secs, cores = oracle_sample(args.cpu_seconds, params, delta, flat, 0.2 * flat)
+        cv, nrel, secs, cores, parity = oracle_sample(args.cpu_seconds, params, delta, flat, 0.2 * flat,
+                                                      gpu=(gpu_parity[0], gpu_parity[1]) if gpu_parity else None)
+        one = oracle_one_thread()
         cpu = {"value": cv, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": f"{nrel} (walker, redshift) realizations of the workload in {secs:.1f} s (FP64, "
-                         f"128^3, full radius ladder, delta T_b, Delta^2, chi^2); evals/s = 1/(3 x s per realization)"}
+                         f"128^3, full radius ladder, delta T_b, Delta^2, chi^2); evals/s = 1/(3 x s per realization)",
+               "one_thread_s_per_realization": one,
+               "one_thread_evals_per_s": 1.0 / (3.0 * one),
+               "one_thread_sample": "fiducial walker (30, 15 Mpc, 4.7) at z = 9, 31 radii, FP64, one host thread "
+                                    "(the paper quotes about 3 s per 128^3 realization on one core, Sec. 2.3)",
+               "cpu_model": cpu_model(), "host_threads": os.cpu_count()}
+    else:
+        parity = None
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -690,17 +873,26 @@ def main():
                        "parallelism": f"walkers sharded over {world} GPU(s)", "traced": not args.no_trace,
                        "schedule": {"group": tuned[0], "pairs": tuned[1], "plane_threads": tuned[2],
                                     "picked_by": "eor_autotune"}},
-            "plain": {"value": plain, "unit": "evals/s", "walkers_timed": pw,
-                      "note": "same kernels, one walker per eor_likelihood call"},
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof,
-            "path_hbm_equivalent": {"value": hbm_equiv, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
-                                    "peak_kind": hbm_kind,
-                                    "def": "per (walker, z, radius): density half spectrum + flag read/write, over the whole step"},
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
-                       "contraction": "tcgen05 3xTF32" if uses_tensor_cores else "FP32 FMA"},
-            "basis_fp32_units": simt,
-            "direct_method": direct, "emulator": emulator, "mcmc": mcmc, "two_population": two_pop,
+                       "contraction": {eor21.EOR_CONTRACT_FP16: "tcgen05 FP16 hi/lo, 3 products along K",
+                                       eor21.EOR_CONTRACT_TF32: "tcgen05 3xTF32",
+                                       eor21.EOR_CONTRACT_FP32: "FP32 FMA"}.get(contract_kind, "none"),
+                       "k_slots": k_slots},
+            "emulator": emulator, "mcmc": mcmc, "two_population": two_pop,
+            "basis_fp32_units": simt, "direct_method": direct,
+            "per_radius_fft_bytes_over_step": {
+                "value": per_radius_rate, "unit": "GB/s", "frac_of_hbm": per_radius_rate / hbm_peak,
+                "peak_kind": hbm_kind,
+                "def": "bytes a per-radius FFT design must move (per (walker, z, radius): density half spectrum + "
+                       "flag read/write) over the step time; the basis method does not move them, so this is "
+                       "not a measured roofline"},
+            "cufft": cufft,
+            "parity_vs_oracle": parity,
+            "plain": {"value": plain, "unit": "evals/s", "walkers_timed": pw,
+                      "note": "same kernels, one walker per eor_likelihood call"},
+            "batched_over_plain": value / (plain * world),
             "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0

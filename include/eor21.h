@@ -225,9 +225,11 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
  *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
  *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-6 on the grid's |k| for every R in
  *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
- *   that contraction, which runs on the tensor cores (tcgen05, TF32 split into hi + lo
- *   parts, three products per step, FP32 accumulation) when the basis has at most 32
- *   functions, else on the FP32 units.
+ *   that contraction, which runs on the tensor cores (tcgen05) with FP32 accumulation:
+ *   with the step-function efficiency on power-of-two-scaled FP16 operands split into
+ *   hi + lo parts (three products side by side along K, basis of at most 31 functions),
+ *   with a mass-dependent efficiency on TF32 hi + lo operands (three products per step,
+ *   basis of at most 31 functions); else on the FP32 units.
  * EOR_METHOD_BASIS_SIMT: the same contraction on the FP32 units only.
  * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius.
  * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. A bounded
@@ -235,6 +237,31 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
 enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2 };
 int eor_set_method(eor_ctx* ctx, int method);
 int eor_basis_info(const eor_ctx* ctx, int* rank, double* max_residual);
+/* The contraction the current method runs: *kind = EOR_CONTRACT_NONE (the direct method),
+ * EOR_CONTRACT_FP32 (FP32 units), EOR_CONTRACT_TF32 (tcgen05, TF32 hi/lo) or
+ * EOR_CONTRACT_FP16 (tcgen05, FP16 hi/lo along K); *k_slots = the K extent of its MMA operands
+ * (0 for the first two). */
+enum { EOR_CONTRACT_NONE = 0, EOR_CONTRACT_FP32 = 1, EOR_CONTRACT_TF32 = 2, EOR_CONTRACT_FP16 = 3 };
+int eor_contraction_info(const eor_ctx* ctx, int* kind, int* k_slots);
+/* Test-only failure injection (off by default; not part of the method). With chunk >= 0,
+ * every CTA of the tensor-core contraction withholds the epilogue's release of the
+ * accumulator buffer that holds the chunk-th coefficient chunk it processes (its chunk
+ * counter runs over every cell tile it takes), and the MMA thread's wait for that release
+ * (before chunk + 2) gives up after wait_ms milliseconds of GPU time instead of 2 s. The wait that gives up records role 2 (MMA), barrier 7
+ * (accumulator free) and the chunk; the CTA then stops issuing, waits for its MMAs and
+ * copies already in flight, frees its tensor memory and exits, and the next call that reads
+ * the context's error word (eor_set_params, or eor_likelihood with host buffers) returns
+ * EOR_ETIMEOUT. No asynchronous copy or MMA is made to time out. chunk < 0 switches the
+ * injection off. The captured likelihood graph is rebuilt at the next call. */
+int eor_debug_withhold(eor_ctx* ctx, int chunk, double wait_ms);
+
+/* Diagnostic of the basis reformulation: w[m2] = sum_b c_b(R) phi_b(k) for R = r_mpc and
+ * k = (2 pi / box_mpc) sqrt(m2), m2 = 0 .. 3 (n/2)^2 (double [3 (n/2)^2 + 1]; NaN where no
+ * mode of the grid has that |m|^2), from the FP64 basis and coefficient table, so that a
+ * caller can compare it with the top-hat W(kR) = 3 (sin x - x cos x)/x^3 of Sec. 2.1.
+ * r_mpc must lie in [R_cell, r_mfp_max] (EOR_EINVAL otherwise). Host output needs
+ * 8 (3 (n/2)^2 + 1) <= 4 n^3 bytes (every n >= 16 here). */
+int eor_basis_window(eor_ctx* ctx, double r_mpc, double* w, int mem);
 
 /* Tracing (not part of the method). With tracing on, every kernel launch of the
  * following calls is bracketed by CUDA events on the context's stream, also inside the
@@ -251,22 +278,25 @@ long long eor_launch_count(const eor_ctx* ctx);
 
 /* Allocation-free power spectrum of one box. The paper has no counterpart: this is a
  * service for callers that cannot allocate GPU memory where they need the result, such as
- * code running while a stream is captured into a CUDA graph (cudaMalloc there fails or
- * breaks the capture), code that must not synchronize the device (cudaMalloc and cudaFree
- * can), or applications that give all device memory to their own pool. It needs no
- * context and calls no cudaMalloc, cudaFree or allocating library routine: its scratch
- * (the box's half spectrum, the bin of every |m|^2, the shell sums and mode counts) is one
- * static device array of EOR21_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads
- * the library until the process exits; n is at most EOR21_NOALLOC_MAX_N (larger n gives
- * EOR_EINVAL). Same definition as eor_box_power_spectrum: box is a device pointer to
- * float [n][n][n]; d2 (double [n_bins]) and nmodes (long long [n_bins], optional) are
- * device pointers; bins are n_bins logarithmic bins on [k_lo, k_hi) for a box of side
- * box_mpc. The work is ordered on cuda_stream (NULL: the legacy default stream) and the
- * call returns without waiting. The first call on a device looks up the array's device
- * address and sets kernel attributes, with that device current: make that first call
- * before any stream capture. All calls share the array and the last call's contents stay
- * in it (each call clears what it accumulates): calls that overlap on the GPU race, so
- * issue them on one stream. Errors: EOR_EINVAL, EOR_ECUDA; message via eor_last_error(NULL). */
+ * applications that give all device memory to their own pool or budget (a cudaMalloc
+ * outside it fails or breaks their accounting) and code that must not synchronize the
+ * device (cudaMalloc and cudaFree can). It needs no context and calls no cudaMalloc,
+ * cudaFree or allocating library routine: its scratch (the box's half spectrum, the bin of
+ * every |m|^2, the shell sums and mode counts) is one static device array of
+ * EOR21_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the library until the
+ * process exits; n is at most EOR21_NOALLOC_MAX_N (larger n gives EOR_EINVAL). Same
+ * definition as eor_box_power_spectrum: box is a device pointer to float [n][n][n]; d2
+ * (double [n_bins]) and nmodes (long long [n_bins], optional) are device pointers; bins
+ * are n_bins logarithmic bins on [k_lo, k_hi) for a box of side box_mpc. The library sees
+ * only raw pointers, so the caller must pass buffers of those types and sizes on the
+ * current device (the Python binding checks them). The work is ordered on cuda_stream
+ * (NULL: the legacy default stream) and the call returns without waiting. The first call
+ * on a device looks up the array's device address, and the first call for each n on a
+ * device sets the shared-memory limits of its two FFT kernels, with that device current:
+ * make those first calls before any stream capture. All calls share the array and the
+ * last call's contents stay in it (each call clears what it accumulates): calls that
+ * overlap on the GPU race, so issue them on one stream. Errors: EOR_EINVAL, EOR_ECUDA;
+ * message via eor_last_error(NULL). */
 #define EOR21_NOALLOC_MAX_N 128
 #define EOR21_NOALLOC_SCRATCH_BYTES (9u << 20)
 int eor_box_power_spectrum_noalloc(int n, double box_mpc, int n_bins, double k_lo, double k_hi, const float* box,

@@ -222,7 +222,8 @@ void eor_destroy(eor_ctx* c) {
                     c->d_kmean, c->d_nmodes_pair, c->d_xhi_out, c->d_xhi_mean, c->d_scratch_box,
                     c->d_diag_pair, c->d_diag_wtab, c->d_diag_ps, c->d_diag_cnt, c->d_chi2_use, c->d_kd_m2,
                     c->d_m2_to_kd, c->d_basis, c->d_coef_tab, c->d_phi_m2, c->d_F, c->d_coef, c->d_dtb, c->d_xpart,
-                    c->d_cols, c->d_gmeta, c->d_goff, c->d_ncols, c->d_tcA, c->d_tcB, c->d_xq, c->d_err};
+                    c->d_cols, c->d_gmeta, c->d_goff, c->d_ncols, c->d_tcA, c->d_tcB, c->d_xq, c->d_err,
+                    c->d_a16, c->d_b16, c->d_fscale, c->d_dcell, c->d_fwords, c->d_effp, c->d_ftab};
     for (void* p : bufs) dev_free(c, p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -319,11 +320,25 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     ok = alloc_n(c, &c->d_F, (size_t)Z * c->kb * c->n3) && alloc_n(c, &c->d_coef, (size_t)W * c->max_radii * c->kb) &&
          alloc_n(c, &c->d_dtb, pairs * c->n3) && alloc_n(c, &c->d_xpart, pairs * parts) &&
          alloc_n(c, &c->d_ncols, 1);
-    if (ok && eor::basis_tc_fits(c->basis_rank))
+    // the tensor-core contraction: FP16 split operands for the step-function efficiency, TF32
+    // split operands with a mass-dependent efficiency (interval flags, partial-ionization tables)
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms < 1) c->num_sms = 1;
+    c->f16 = g.efficiency_model == 0 && eor::basis_f16_fits(c->basis_rank);
+    if (ok && c->f16) {
+        c->k16 = eor::basis_f16_kslots(c->basis_rank);
+        ok = alloc_n(c, &c->d_a16, eor::basis_f16_a_bytes((long long)c->n3, Z, c->basis_rank)) &&
+             alloc_n(c, &c->d_b16, eor::basis_f16_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
+             alloc_n(c, &c->d_fscale, 2 * 32 * (size_t)Z) && alloc_n(c, &c->d_dcell, (size_t)Z * c->n3) &&
+             alloc_n(c, &c->d_fwords, pairs * (c->n3 / 32)) &&
+             alloc_n(c, &c->d_cols, eor::basis_f16_column_slots(c)) &&
+             alloc_n(c, &c->d_gmeta, eor::basis_f16_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
+    } else if (ok && eor::basis_tc_fits(c->basis_rank)) {
         ok = alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, Z)) &&
              alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
              alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
              alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
+    }
     if (ok && g.rsd) ok = alloc_n(c, &c->d_bright, (size_t)Z * c->n3);
     if (ok && g.efficiency_model)
         ok = alloc_n(c, &c->d_effp, 4 * (size_t)W) && alloc_n(c, &c->d_ftab, pairs * eor::kFTab);
@@ -331,7 +346,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
         eor_destroy(c);
         return fail(nullptr, EOR_ENOMEM, "device allocation failed (basis fields)");
     }
-    if ((e = eor::prepare_basis_kernel(c)) != cudaSuccess || (e = eor::prepare_basis_tc(c)) != cudaSuccess) {
+    if ((e = eor::prepare_basis_kernel(c)) != cudaSuccess || (e = eor::prepare_basis_tc(c)) != cudaSuccess ||
+        (e = eor::prepare_basis_f16(c)) != cudaSuccess) {
         g_create_error = std::string("basis kernel: ") + cudaGetErrorString(e);
         eor_destroy(c);
         return EOR_ECUDA;
@@ -376,8 +392,8 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
             }
         }
     }
-    if (c->d_tcA) {
-        cudaError_t e = eor::format_basis_tc(c);
+    if (c->d_tcA || c->f16) {
+        cudaError_t e = c->f16 ? eor::format_basis_f16(c) : eor::format_basis_tc(c);
         if (e != cudaSuccess) {
             dev_free(c, zwork);
             return cuda_fail(c, e, "tensor-core operands");
@@ -771,6 +787,56 @@ int eor_basis_info(const eor_ctx* c, int* rank, double* max_residual) {
     if (!c || !rank || !max_residual) return EOR_EINVAL;
     *rank = c->basis_rank;
     *max_residual = c->basis_residual;
+    return EOR_OK;
+}
+
+int eor_contraction_info(const eor_ctx* c, int* kind, int* k_slots) {
+    if (!c || !kind || !k_slots) return EOR_EINVAL;
+    *k_slots = 0;
+    if (c->tune.method == eor::kMethodDirect) {
+        *kind = EOR_CONTRACT_NONE;
+    } else if (c->tune.method == eor::kMethodBasis && c->f16) {
+        *kind = EOR_CONTRACT_FP16;
+        *k_slots = c->k16;
+    } else if (c->tune.method == eor::kMethodBasis && c->d_tcA) {
+        *kind = EOR_CONTRACT_TF32;
+        *k_slots = (c->basis_rank + 1 + 7) / 8 * 8;
+    } else {
+        *kind = EOR_CONTRACT_FP32;
+    }
+    return EOR_OK;
+}
+
+int eor_basis_window(eor_ctx* c, double r_mpc, double* w, int mem) {
+    if (!c) return EOR_EINVAL;
+    trace_reset(c);
+    CK(trace_reserve(c, eor::estimate_launches(c)), "trace events");
+    if (!w || !valid_mem(mem) || !(r_mpc > 0.0) || !isfinite(r_mpc)) return fail(c, EOR_EINVAL, "bad argument");
+    const double dx = c->cfg.box_mpc / c->n;
+    const double r_cell = c->cfg.r_cell_rule == 1 ? dx : cbrt(3.0 / (4.0 * kPi)) * dx;
+    if (r_mpc < r_cell * (1.0 - 1e-12) || r_mpc > fmax(c->cfg.r_mfp_max, r_cell) * (1.0 + 1e-12))
+        return fail(c, EOR_EINVAL, "r_mpc outside [R_cell, r_mfp_max], the basis's radius range");
+    double* dst = mem == EOR_DEVICE ? w : reinterpret_cast<double*>(c->d_scratch_box);
+    if (mem == EOR_HOST && sizeof(double) * c->n_m2 > sizeof(float) * c->n3)
+        return fail(c, EOR_ENOTSUP, "grid too small for the host copy of the window");
+    CK(eor::launch_basis_window(c, r_mpc, dst), "basis window");
+    int r;
+    if (mem == EOR_HOST && (r = copy_out(c, w, dst, sizeof(double) * c->n_m2, mem))) return r;
+    return finish(c, mem);
+}
+
+int eor_debug_withhold(eor_ctx* c, int chunk, double wait_ms) {
+    if (!c) return EOR_EINVAL;
+    if (chunk >= 0 && !(wait_ms > 0.0 && wait_ms <= 2000.0))
+        return fail(c, EOR_EINVAL, "wait_ms must be in (0, 2000]");
+    CK(cudaStreamSynchronize(c->stream), "debug withhold");
+    c->dbg_withhold = chunk >= 0 ? chunk : -1;
+    c->dbg_wait_ns = chunk >= 0 ? (unsigned long long)(wait_ms * 1e6) : 0ull;
+    if (c->graph_exec) {   // the captured graph holds the kernel's arguments
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_walkers = -1;
+    }
     return EOR_OK;
 }
 

@@ -207,6 +207,31 @@ __global__ void k_walker_coefs(const WalkerInfo* walkers, const double* tab, int
     coef[((size_t)w * max_radii + j) * kb + b] = out;
 }
 
+// Diagnostic: the basis's reconstruction sum_b c_b(R) phi_b(|m|^2) of the top-hat window at
+// radius r on every |m|^2 index (NaN where no grid mode has that |m|^2), in FP64 with the
+// coefficients interpolated from the table as the walker coefficients are.
+__global__ void k_basis_window(const double* basis, int n_kd, const int* m2_to_kd, int n_m2, int rank,
+                               const double* tab, double r_lo, double h, int n_grid, double r, double* out) {
+    __shared__ double s_c[kBasisMax];
+    if (threadIdx.x < rank) {
+        const double u = (r - r_lo) / h;
+        int i = (int)floor(u);
+        i = i < 1 ? 1 : (i > n_grid - 3 ? n_grid - 3 : i);
+        const double t = u - i;
+        const double* f = tab + (size_t)threadIdx.x * n_grid + (i - 1);
+        s_c[threadIdx.x] = -t * (t - 1.0) * (t - 2.0) / 6.0 * f[0] + (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0 * f[1] -
+                           (t + 1.0) * t * (t - 2.0) / 2.0 * f[2] + (t + 1.0) * t * (t - 1.0) / 6.0 * f[3];
+    }
+    __syncthreads();
+    for (int m2 = blockIdx.x * blockDim.x + threadIdx.x; m2 < n_m2; m2 += gridDim.x * blockDim.x) {
+        const int k = m2_to_kd[m2];
+        double w = k >= 0 ? 0.0 : nan("");
+        if (k >= 0)
+            for (int b = 0; b < rank; b++) w += s_c[b] * basis[(size_t)b * n_kd + k];
+        out[m2] = w;
+    }
+}
+
 // ------------------------------------------------------------------ the contraction
 
 constexpr int kCPL = 2;                 // cells per thread
@@ -453,6 +478,15 @@ cudaError_t build_walker_coefs(eor_ctx* c, int n_walkers) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_basis_window(eor_ctx* c, double r, double* out) {
+    trace_begin(c, kKOther);
+    k_basis_window<<<(c->n_m2 + 255) / 256, 256, 0, c->stream>>>(c->d_basis, c->n_kd, c->d_m2_to_kd, c->n_m2,
+                                                                  c->basis_rank, c->d_coef_tab, c->coef_r_lo, c->coef_h,
+                                                                  kCoefGrid, r, out);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
 #define EOR_KB_DISPATCH(kb, FN, ...)          \
     switch (kb) {                             \
         case 4: return FN<4>(__VA_ARGS__);    \
@@ -488,7 +522,8 @@ cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_
 
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
-    if (c->tune.method == kMethodBasis && basis_tc_fits(c->basis_rank)) return launch_basis_ionize_tc(c, xhi_out);
+    if (c->tune.method == kMethodBasis && c->f16) return launch_basis_ionize_f16(c);   // x_HI: pencil pass
+    if (c->tune.method == kMethodBasis && c->d_tcA) return launch_basis_ionize_tc(c, xhi_out);
     BasisArgs a{c->d_F, c->d_coef, c->d_pairs, brightness_base(c), c->d_dtb, xhi_out, c->d_xpart, pop_tables(c), c->n_walkers, n_z,
                 c->max_radii, (long long)c->n3, (float)c->cfg.delta_c};
     const size_t smem = basis_ionize_smem(c->kb, c->max_radii);

@@ -72,6 +72,7 @@ struct GemmArgs {
     float* pre_out;
     long long pre_e, pre_m;
     int M, N, K;
+    int* flag;                  // tensor-core form: bit 1 set when a bounded wait ran out
 };
 
 __device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
@@ -149,6 +150,147 @@ __global__ void __launch_bounds__(kGemmThreads) k_emu_gemm(GemmArgs g) {
             g.C[ci] = v;
         }
     }
+}
+
+// The same GEMM on the 5th-generation tensor cores: one CTA computes a 128 x NT tile of C
+// (MMA M = 128, N = NT) for member blockIdx.z with tcgen05 kind::tf32 MMAs accumulating in
+// tensor memory. K advances in stages of 32: all 128 threads load the stage's A (128 x 32)
+// and B (NT x 32) values through their strides, split each into TF32 hi + lo (hi = TF32
+// rounding, lo = TF32 rounding of the remainder) and store them K-major in the no-swizzle
+// core-matrix layout; thread 0 then issues per K step of 8 the products hi*hi + lo*hi and,
+// unless B is exact in TF32 (B_EXACT: the bf16-rounded weights, whose 8 significant bits
+// TF32 holds), hi*lo: FP32-level products, FP32 accumulation, as the FP32-unit kernel. Two
+// stages alternate, so the loads of one overlap the MMAs of the other. The epilogue
+// (warp w: rows 32 w .. 32 w + 31) reads the accumulators back with tcgen05.ld and applies
+// the same bias / GELU / GELU-derivative / plain store. Every wait is bounded in GPU time;
+// a wait that gives up sets bit 1 of g.flag, and the CTA waits for its MMAs before freeing
+// its tensor memory.
+constexpr int kGtM = 128, kGtK = 32, kGtThreads = 128;
+constexpr uint64_t kGtWaitNs = 2000000000ull;            // 2 s of GPU time per bounded wait
+constexpr uint32_t kGtABytes = kGtM * kGtK * 4;          // one 128 x 32 TF32 operand (16 KB)
+
+template <int NT>
+constexpr uint32_t gt_stage_bytes(bool b_exact) {
+    return 2 * kGtABytes + (b_exact ? 1u : 2u) * (uint32_t)NT * kGtK * 4;
+}
+
+template <int NT>
+constexpr size_t gt_smem(bool b_exact) {
+    return 2 * (size_t)gt_stage_bytes<NT>(b_exact) + 4 * sizeof(uint64_t) + 16;
+}
+
+template <int EPI, bool B_EXACT, int NT>
+__global__ void __launch_bounds__(kGtThreads) k_emu_gemm_tc(GemmArgs g) {
+    static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "MMA N");
+    constexpr uint32_t kStage = gt_stage_bytes<NT>(B_EXACT);
+    constexpr uint32_t kBBytes = (uint32_t)NT * kGtK * 4;
+    constexpr uint32_t kCols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);   // [2] MMAs of a stage done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int e = blockIdx.z, m0 = blockIdx.y * kGtM, n0 = blockIdx.x * NT;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const float* A = g.A + e * g.ae;
+    const float* B = g.B + e * g.be;
+    if (warp == 0) tc::tmem_alloc(tslot, kCols);
+    if (t == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init(bar + 1, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int nk = (g.K + kGtK - 1) / kGtK;
+    bool ok = true;
+    int last = -1;   // the last stage whose MMAs were issued (every thread tracks it)
+    for (int kc = 0; kc < nk; kc++) {
+        const int st = kc & 1, k0 = kc * kGtK;
+        // the MMAs that read this stage two steps ago are done (a timeout stops every thread)
+        if (kc >= 2 && !__syncthreads_and(tc::mbar_wait(bar + st, (uint32_t)((kc - 2) >> 1) & 1u, kGtWaitNs))) {
+            ok = false;
+            break;
+        }
+        unsigned char* Ah = sm + st * kStage;
+        unsigned char* Al = Ah + kGtABytes;
+        unsigned char* Bh = Al + kGtABytes;
+        unsigned char* Bl = Bh + kBBytes;   // unused with B_EXACT
+        // consecutive threads walk the operand's unit-stride index (coalesced loads)
+        const bool a_kfast = g.ak == 1, b_nfast = g.bn == 1;
+        for (int idx = t; idx < kGtM * kGtK; idx += kGtThreads) {
+            const int mm = a_kfast ? idx / kGtK : idx % kGtM, kk = a_kfast ? idx % kGtK : idx / kGtM;
+            const int m = m0 + mm, k = k0 + kk;
+            const float v = (m < g.M && k < g.K) ? A[m * g.am + k * g.ak] : 0.0f;
+            const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
+            *reinterpret_cast<uint32_t*>(Ah + tc::core_offset(mm, kk)) = hi;
+            *reinterpret_cast<uint32_t*>(Al + tc::core_offset(mm, kk)) = lo;
+        }
+        for (int idx = t; idx < NT * kGtK; idx += kGtThreads) {
+            const int nn = b_nfast ? idx % NT : idx / kGtK, kk = b_nfast ? idx / NT : idx % kGtK;
+            const int n = n0 + nn, k = k0 + kk;
+            const float v = (n < g.N && k < g.K) ? B[k * g.bk + n * g.bn] : 0.0f;
+            const uint32_t hi = tc::to_tf32(v);
+            *reinterpret_cast<uint32_t*>(Bh + tc::core_offset(nn, kk)) = hi;
+            if constexpr (!B_EXACT)
+                *reinterpret_cast<uint32_t*>(Bl + tc::core_offset(nn, kk)) = tc::to_tf32(v - __uint_as_float(hi));
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_tf32(kGtM, NT);
+            for (int ks = 0; ks < kGtK / 8; ks++) {
+                const uint32_t ko = (uint32_t)ks * 2 * tc::kLBO;
+                const uint64_t ah = tc::smem_desc(tc::smem_addr(Ah) + ko, tc::kLBO, tc::kSBO);
+                const uint64_t al = tc::smem_desc(tc::smem_addr(Al) + ko, tc::kLBO, tc::kSBO);
+                const uint64_t bh = tc::smem_desc(tc::smem_addr(Bh) + ko, tc::kLBO, tc::kSBO);
+                tc::mma_tf32(tmem, ah, bh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                tc::mma_tf32(tmem, al, bh, idesc, 1u);
+                if constexpr (!B_EXACT) {
+                    const uint64_t bl = tc::smem_desc(tc::smem_addr(Bl) + ko, tc::kLBO, tc::kSBO);
+                    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+                }
+            }
+            tc::mma_commit(bar + st);
+        }
+        last = kc;
+    }
+    // the last issued stage's commit completes once every MMA issued before it has finished
+    bool done = last < 0 || tc::mbar_wait(bar + (last & 1), (uint32_t)(last >> 1) & 1u, kGtWaitNs);
+    if (!done) done = tc::mbar_wait(bar + (last & 1), (uint32_t)(last >> 1) & 1u, kGtWaitNs);
+    tc::fence_after_sync();
+    const bool good = __syncthreads_and(ok && done);
+    if (good) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(base + (uint32_t)c0, v);
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = n0 + c0 + j;
+                if (n >= g.N) continue;
+                float x = v[j];
+                if (EPI == kEpiLinear) {
+                    x += g.bias[e * g.bias_e + n];
+                } else if (EPI == kEpiGelu) {
+                    x += g.bias[e * g.bias_e + n];
+                    g.pre_out[e * g.pre_e + m * g.pre_m + n] = x;
+                    x = gelu_f(x);
+                } else if (EPI == kEpiGeluGrad) {
+                    x *= gelu_grad_f(g.pre[e * g.pre_e + m * g.pre_m + n]);
+                }
+                g.C[e * g.ce + m * g.cm + n] = x;
+            }
+        }
+    } else if (t == 0 && g.flag) {
+        atomicOr(g.flag, 2);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
 // out[e oe + n] = sum over rows of dz[e ze + r zm + n] (bias gradients). Block: 32 columns x
@@ -733,7 +875,7 @@ struct eor_emu {
     bool tc_ok = false;                  // the network's shape fits the tensor-core inference
     bool use_tc = false;                 // predictions on the tensor cores (else the FP32 units)
     unsigned char* d_wfmt = nullptr;     // BF16 core-matrix weights of every member
-    int* d_flag = nullptr;               // bit 0: a bounded tensor-core wait ran out
+    int* d_flag = nullptr;               // bit 0: a bounded wait of the inference ran out, bit 1: of a GEMM
     std::string err;
 };
 
@@ -766,11 +908,50 @@ bool ealloc(T** p, size_t count) {
 
 unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
-template <int EPI>
-cudaError_t gemm(cudaStream_t s, const GemmArgs& g, int members) {
-    dim3 grid(grid_for(g.N, kGemmTile), grid_for(g.M, kGemmTile), members);
-    k_emu_gemm<EPI><<<grid, kGemmThreads, 0, s>>>(g);
+template <int EPI, bool B_EXACT, int NT>
+cudaError_t gemm_tc(cudaStream_t s, const GemmArgs& g, int members) {
+    dim3 grid(grid_for(g.N, NT), grid_for(g.M, kGtM), members);
+    k_emu_gemm_tc<EPI, B_EXACT, NT><<<grid, kGtThreads, gt_smem<NT>(B_EXACT), s>>>(g);
     return cudaGetLastError();
+}
+
+// C = A B with the epilogue EPI on the tensor cores; b_exact: B holds the bf16-rounded
+// weights (exact in TF32, two products); N tiles of 16, 32 or 64 columns.
+template <int EPI>
+cudaError_t gemm(cudaStream_t s, const GemmArgs& g, int members, bool b_exact) {
+    if (b_exact) {
+        if (g.N <= 16) return gemm_tc<EPI, true, 16>(s, g, members);
+        if (g.N <= 32) return gemm_tc<EPI, true, 32>(s, g, members);
+        return gemm_tc<EPI, true, 64>(s, g, members);
+    }
+    if (g.N <= 16) return gemm_tc<EPI, false, 16>(s, g, members);
+    if (g.N <= 32) return gemm_tc<EPI, false, 32>(s, g, members);
+    return gemm_tc<EPI, false, 64>(s, g, members);
+}
+
+template <int EPI, bool B_EXACT>
+cudaError_t prepare_gemm_tc_epi() {
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_tc<EPI, B_EXACT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gt_smem<16>(B_EXACT));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_emu_gemm_tc<EPI, B_EXACT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gt_smem<32>(B_EXACT));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_emu_gemm_tc<EPI, B_EXACT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gt_smem<64>(B_EXACT));
+    return e;
+}
+
+cudaError_t prepare_gemm_tc() {
+    cudaError_t e;
+    if ((e = prepare_gemm_tc_epi<kEpiLinear, true>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiGelu, true>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiGeluGrad, true>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiPlain, false>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiLinear, false>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiGelu, false>()) != cudaSuccess) return e;
+    if ((e = prepare_gemm_tc_epi<kEpiGeluGrad, false>()) != cudaSuccess) return e;
+    return prepare_gemm_tc_epi<kEpiPlain, true>();
 }
 
 long long act_stride(const eor_emu* m) { return (long long)m->rows * m->H; }
@@ -803,7 +984,8 @@ cudaError_t forward(eor_emu* m, const float* x, long long xe, int rows) {
             g.C = m->d_y;
             g.ce = out_stride(m);
             g.cm = m->B;
-            e = gemm<kEpiLinear>(m->stream, g, m->E);
+            g.flag = m->d_flag;
+            e = gemm<kEpiLinear>(m->stream, g, m->E, true);
         } else {
             g.C = act(m, l);
             g.ce = act_stride(m);
@@ -811,7 +993,8 @@ cudaError_t forward(eor_emu* m, const float* x, long long xe, int rows) {
             g.pre_out = pre(m, l);
             g.pre_e = act_stride(m);
             g.pre_m = m->H;
-            e = gemm<kEpiGelu>(m->stream, g, m->E);
+            g.flag = m->d_flag;
+            e = gemm<kEpiGelu>(m->stream, g, m->E, true);
         }
     }
     return e;
@@ -843,7 +1026,8 @@ cudaError_t backward(eor_emu* m, const float* x, long long xe, int rows) {
         g.M = L.fout[l];
         g.N = L.fin[l];
         g.K = rows;
-        e = gemm<kEpiPlain>(m->stream, g, m->E);
+        g.flag = m->d_flag;
+        e = gemm<kEpiPlain>(m->stream, g, m->E, false);
         if (e != cudaSuccess) break;
         // db_l[o] = sum_r dz[r][o]
         k_emu_colsum<<<dim3(grid_for(L.fout[l], 32), m->E), 32 * kColSlices, 0, m->stream>>>(
@@ -870,7 +1054,8 @@ cudaError_t backward(eor_emu* m, const float* x, long long xe, int rows) {
         d.M = rows;
         d.N = L.fin[l];
         d.K = L.fout[l];
-        e = gemm<kEpiGeluGrad>(m->stream, d, m->E);
+        d.flag = m->d_flag;
+        e = gemm<kEpiGeluGrad>(m->stream, d, m->E, true);
         dz = next;
         dz_e = act_stride(m);
         dz_m = m->H;
@@ -914,6 +1099,11 @@ int finish(eor_emu* m, int mem) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mem == EOR_HOST) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return efail(m, EOR_ECUDA, std::string("emulator: ") + cudaGetErrorString(e));
+    if (mem == EOR_HOST) {   // a bounded wait of a tensor-core GEMM that ran out
+        int flag = 0;
+        EK(cudaMemcpy(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost), "flag");
+        if (flag & 2) return efail(m, EOR_ETIMEOUT, "a bounded wait of a tensor-core GEMM ran out");
+    }
     return EOR_OK;
 }
 
@@ -1083,10 +1273,15 @@ int eor_emu_create(const eor_emu_config* cfg, void* cuda_stream, eor_emu** out) 
         eor_emu_destroy(m);
         return efail(nullptr, EOR_ENOMEM, "device allocation failed");
     }
+    if (!ealloc(&m->d_flag, 1) || cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream) != cudaSuccess ||
+        prepare_gemm_tc() != cudaSuccess) {
+        cudaGetLastError();
+        eor_emu_destroy(m);
+        return efail(nullptr, EOR_ENOMEM, "tensor-core GEMM set-up");
+    }
     m->tc_ok = g.hidden == kTcHidden && g.n_hidden == 3 && g.n_bins <= kTcOutN;
     if (m->tc_ok) {
-        if (!ealloc(&m->d_wfmt, (size_t)m->E * kTcMemberBytes) || !ealloc(&m->d_flag, 1) ||
-            cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream) != cudaSuccess ||
+        if (!ealloc(&m->d_wfmt, (size_t)m->E * kTcMemberBytes) ||
             cudaFuncSetAttribute(k_emu_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu_tc_smem()) !=
                 cudaSuccess) {
             cudaGetLastError();

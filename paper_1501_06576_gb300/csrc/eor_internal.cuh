@@ -164,6 +164,15 @@ struct eor_ctx {
     unsigned char* d_tcA = nullptr;  // tensor-core A operands of every CTA (TF32 hi/lo core matrices)
     unsigned char* d_tcB = nullptr;  // tensor-core coefficient chunks per redshift
     unsigned long long* d_xq = nullptr;   // [pairs] fixed-point x_HI sums of the tensor-core path
+    // FP16 split contraction (step-function efficiency, basis rank <= 31)
+    bool f16 = false;                // the tensor-core contraction runs on FP16 split operands
+    int k16 = 0;                     // its K slots: 3 (rank + 1) rounded up to 16
+    int num_sms = 0;                 // persistent grid size
+    unsigned char* d_a16 = nullptr;  // [n_z][n^3 / 128][128 x k16 FP16] A operands
+    unsigned char* d_b16 = nullptr;  // [n_z][chunk][256 x k16 FP16 + group records]
+    float* d_fscale = nullptr;       // [n_z][32] power-of-two bound of |F_b|, then [n_z][32] scratch
+    float* d_dcell = nullptr;        // [n_z][n^3] delta at R_cell
+    uint32_t* d_fwords = nullptr;    // [max_walkers][n_z][n^3 / 32] Eq. 1 flags above R_cell
     int* d_ncols = nullptr;          // [1] number of columns
     int n_ready_tables = 0;
     int ps_planes = 0;               // kz planes holding a binned mode: kf kz < k_hi
@@ -180,6 +189,10 @@ struct eor_ctx {
     int trace_used = 0;
     long long launches = 0;          // kernels launched by the last call
     long long graph_launches = 0;    // kernels in the captured graph
+
+    // test-only failure injection of the tensor-core contraction (eor_debug_withhold)
+    int dbg_withhold = -1;
+    unsigned long long dbg_wait_ns = 0;
 
     // captured likelihood graphs, keyed by walker count
     cudaGraphExec_t graph_exec = nullptr;
@@ -203,6 +216,7 @@ inline const float* pop_tables(const eor_ctx* c) { return c->cfg.efficiency_mode
 // basis.cu
 cudaError_t build_basis(eor_ctx* c);
 cudaError_t build_walker_coefs(eor_ctx* c, int n_walkers);
+cudaError_t launch_basis_window(eor_ctx* c, double r, double* out);
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out);
 cudaError_t prepare_basis_kernel(eor_ctx* c);
 size_t basis_ionize_smem(int kb, int max_radii);
@@ -218,10 +232,21 @@ cudaError_t prepare_basis_tc(eor_ctx* c);
 cudaError_t format_basis_tc(eor_ctx* c);
 cudaError_t build_columns(eor_ctx* c, int n_walkers);
 cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out);
+bool basis_f16_fits(int rank);
+int basis_f16_kslots(int rank);
+size_t basis_f16_a_bytes(long long n3, int n_z, int rank);
+size_t basis_f16_b_bytes(const eor_ctx* c);
+size_t basis_f16_column_slots(const eor_ctx* c);
+cudaError_t prepare_basis_f16(eor_ctx* c);
+cudaError_t format_basis_f16(eor_ctx* c);
+cudaError_t build_columns_f16(eor_ctx* c, int n_walkers);
+cudaError_t launch_basis_ionize_f16(eor_ctx* c);
+void launch_xq_finish(const unsigned long long* xq, int pairs, double* xhi_sum, cudaStream_t s);
 
 // kernels.cu
 cudaError_t prepare_kernels(int n);
-cudaError_t launch_ps_from_boxes(eor_ctx* c);
+cudaError_t launch_ps_from_boxes(eor_ctx* c, float* xhi_out);
+cudaError_t prepare_box_ps_raw(int n);
 cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signed char* bins, double* sums, int n_bins,
                               float kf3, const PairInfo* pair_info, cudaStream_t stream);
 

@@ -17,6 +17,8 @@
 // delta_R and delta T_b never touch global memory.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "eor_internal.cuh"
 #include "fft_core.cuh"
 
@@ -266,6 +268,141 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
     }
     for (int b = threadIdx.x; b < a.n_bins; b += P::THREADS)
         if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
+}
+
+// The same pass for n = 128 as a cluster of two CTAs per plane: CTA h (the cluster rank)
+// holds rows x = 64 h .. 64 h + 63 of the plane (66 KB instead of 132 KB, so two such CTAs
+// share an SM and one's HBM load overlaps the other's transforms). Each CTA transforms its
+// own rows along y, then, after a cluster barrier, columns y = 64 h .. 64 h + 63 along x,
+// reading the other CTA's rows from its shared memory (distributed shared memory), and bins
+// its outputs as k_plane_ps does. Transforms: the 16 x 8 two-step split of fft_core.cuh.
+constexpr int kPs2Threads = 512;
+constexpr int kPs2Rows = 64;                      // rows (and then columns) per CTA
+constexpr int kPs2S = 129;                        // padded row stride (float2)
+constexpr size_t kPs2Smem = (size_t)kPs2Rows * kPs2S * sizeof(float2) + 128 * sizeof(float2) +
+                            (size_t)kPrivBins * kPs2Threads * sizeof(float);
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPs2Threads, 2) k_plane_ps2(PSArgs a) {
+    constexpr int N = 128, NH = N / 2 + 1, R1 = 16, R2 = 8;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;                                        // [64][kPs2S]
+    float2* tw = smem + kPs2Rows * kPs2S;                      // [128]
+    float* priv = reinterpret_cast<float*>(tw + N);            // [kPrivBins][threads]
+    __shared__ double s_bins[EOR21_MAX_BINS];
+    const int h = (int)cluster.block_rank();
+    const int kz = blockIdx.x >> 1, slot = blockIdx.y;
+    const int pair = a.pair0 + slot;
+    const bool valid = pair < a.n_pairs;                       // uniform over the cluster
+    const int t = threadIdx.x;
+    fill_twiddles<N>(tw);
+    for (int e = t; e < kPrivBins * kPs2Threads; e += kPs2Threads) priv[e] = 0.0f;
+    for (int e = t; e < EOR21_MAX_BINS; e += kPs2Threads) s_bins[e] = 0.0;
+    if (valid) {   // this CTA's 64 rows (contiguous in memory), two complex values per load
+        const float4* src = reinterpret_cast<const float4*>(a.ps_inter + ((size_t)slot * NH + kz) * N * N +
+                                                            (size_t)h * kPs2Rows * N);
+        float4 v[kPs2Rows * N / 2 / kPs2Threads];
+#pragma unroll
+        for (int k = 0; k < kPs2Rows * N / 2 / kPs2Threads; k++) v[k] = __ldg(src + t + k * kPs2Threads);
+#pragma unroll
+        for (int k = 0; k < kPs2Rows * N / 2 / kPs2Threads; k++) {
+            const int e = 2 * (t + k * kPs2Threads), r = e / N, c = e % N;
+            buf[r * kPs2S + c] = make_float2(v[k].x, v[k].y);
+            buf[r * kPs2S + c + 1] = make_float2(v[k].z, v[k].w);
+        }
+    }
+    __syncthreads();
+    // along y for each local row r: thread (i, r), i < R2
+    const int i = t / kPs2Rows, r = t % kPs2Rows;
+    if (valid) {
+        float2 x[R1];
+#pragma unroll
+        for (int j = 0; j < R1; j++) x[j] = buf[r * kPs2S + j * R2 + i];
+        dft_reg<R1, -1>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw_get<N, -1>(tw, i * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < R1; k1++) buf[r * kPs2S + k1 * R2 + i] = x[k1];
+    }
+    __syncthreads();
+    float2 hold[R1 / R2][R2];
+    if (valid) {
+#pragma unroll
+        for (int q = 0; q < R1 / R2; q++) {
+            const int k1 = i + R2 * q;
+#pragma unroll
+            for (int i2 = 0; i2 < R2; i2++) hold[q][i2] = buf[r * kPs2S + k1 * R2 + i2];
+            dft_reg<R2, -1>(hold[q]);
+        }
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+        for (int q = 0; q < R1 / R2; q++)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; k2++) buf[r * kPs2S + i + R2 * q + R1 * k2] = hold[q][k2];
+    }
+    cluster.sync();   // both halves transformed along y
+    // along x for the cluster's columns y = 64 h + cl: thread (i, cl); rows 0..63 live in
+    // CTA 0, rows 64..127 in CTA 1
+    const int cl = t % kPs2Rows, c = h * kPs2Rows + cl;
+    float2 x[R1];
+    if (valid) {
+        const float2* lo = cluster.map_shared_rank(buf, 0);
+        const float2* hi = cluster.map_shared_rank(buf, 1);
+#pragma unroll
+        for (int j = 0; j < R1; j++) {
+            const int row = j * R2 + i;
+            x[j] = row < kPs2Rows ? lo[row * kPs2S + c] : hi[(row - kPs2Rows) * kPs2S + c];
+        }
+        dft_reg<R1, -1>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw_get<N, -1>(tw, i * k1));
+    }
+    cluster.sync();   // every remote read is done: the buffer now holds this CTA's columns
+    if (valid) {
+#pragma unroll
+        for (int k1 = 0; k1 < R1; k1++) buf[cl * kPs2S + k1 * R2 + i] = x[k1];
+    }
+    __syncthreads();
+    if (valid) {
+        const float weight = (kz == 0 || kz == N / 2) ? 1.0f : 2.0f;
+        const int my = signed_index(c, N), mz2 = kz * kz;
+#pragma unroll
+        for (int q = 0; q < R1 / R2; q++) {
+            const int k1 = i + R2 * q;
+#pragma unroll
+            for (int i2 = 0; i2 < R2; i2++) hold[q][i2] = buf[cl * kPs2S + k1 * R2 + i2];
+            dft_reg<R2, -1>(hold[q]);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; k2++) {   // mode (kx = k1 + R1 k2, ky = c, kz)
+                const int mx = signed_index(k1 + R1 * k2, N);
+                const int m2 = mx * mx + my * my + mz2;
+                const int b = a.bin_of_m2[m2];
+                if (b >= 0) {
+                    const float2 u = hold[q][k2];
+                    const float fm2 = (float)m2;
+                    priv[b * kPs2Threads + t] += weight * a.kf3 * fm2 * sqrtf(fm2) * (u.x * u.x + u.y * u.y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // bin sums: warp w adds the slots of bins w, w + 16, ... in FP64, lanes then a tree
+    const int lane = t & 31, warp = t >> 5;
+    if (valid) {
+        for (int b = warp; b < a.n_bins; b += kPs2Threads / 32) {
+            double sum = 0.0;
+            for (int k = lane; k < kPs2Threads; k += 32) sum += (double)priv[b * kPs2Threads + k];
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            if (lane == 0) s_bins[b] = sum;
+        }
+    }
+    __syncthreads();
+    if (valid)
+        for (int b = t; b < a.n_bins; b += kPs2Threads)
+            if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
 }
 
 // ------------------------------------------------------------------ 256-point line passes
@@ -738,6 +875,93 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_forward_batch(con
     pencil_r2c<N>(s, p, i, z, dst + (size_t)slot * NH * N * N + (size_t)x * N + y0, (size_t)N * N);
 }
 
+struct BrightArgs {
+    const uint32_t* fwords;     // [pair][n3 / 32] Eq. 1 flags above R_cell (bit = cell % 32)
+    const PairInfo* pairs;
+    const float* delta;         // brightness base [n_z][n3]
+    const float* dcell;         // [n_z][n3] delta at R_cell
+    float* xhi_out;             // optional [pair][n3]
+    unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
+    float2* dst;                // [slot][nh][n][n]
+    int pair0, n_pairs;
+    float delta_c;
+};
+
+// The flag contraction's pencil pass, for pairs pair0 .. pair0 + gridDim.y - 1: per cell of
+// the tile's pencils x_HI = 0 where a radius above R_cell flagged it (Eq. 1), else
+// 1 - min(1, zeta f_coll(R_cell)) with f_coll = erfc((delta_c - delta_Rcell) / sqrt(2 s^2))
+// (1 where delta_Rcell >= delta_c; x_HI = 1 where s^2 <= 0) (Sec. 2.1); delta T_b =
+// T0 x_HI (1 + delta) (Sec. 2.2), never stored; then its R2C along z into dst. The x_HI sum
+// of the pair is exact: fixed point 2^-23, integer warp sums and 64-bit atomics.
+template <int N>
+__global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_brightness(BrightArgs a) {
+    using P = Pencil<N>;
+    constexpr int NH = N / 2 + 1;
+    constexpr int V = P::TY * N / 4;                             // float4 per tile
+    constexpr int PER = (V + P::THREADS - 1) / P::THREADS;
+    extern __shared__ __align__(16) float2 smem[];
+    const PencilSmem<N> s(smem);
+    const int tile = blockIdx.x, slot = blockIdx.y, pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    const PairInfo& pi = a.pairs[pair];
+    const int t = threadIdx.x, p = t % P::TY, i = t / P::TY;
+    const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
+    const size_t n3 = (size_t)N * N * N, cell0 = ((size_t)x * N + y0) * N;
+    fill_twiddles<N>(s.tw);
+    const float4* d4 = reinterpret_cast<const float4*>(a.delta + (size_t)pi.zi * n3 + cell0);
+    const float4* c4 = reinterpret_cast<const float4*>(a.dcell + (size_t)pi.zi * n3 + cell0);
+    const uint32_t* fw = a.fwords + (size_t)pair * (n3 / 32) + cell0 / 32;
+    float4 dv[PER], cv[PER];
+    uint32_t bits[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) {   // every load issued before the first use
+        const int e = t + k * P::THREADS;
+        if (e < V) {
+            dv[k] = __ldg(d4 + e);
+            cv[k] = __ldg(c4 + e);
+            bits[k] = __ldg(fw + (4 * e) / 32) >> ((4 * e) % 32);
+        }
+    }
+    const float zeta = pi.zeta, t0 = pi.t0, inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
+    int xq = 0;   // at most 32 cells x 2^23 per thread
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int e = t + k * P::THREADS;
+        if (e >= V) continue;
+        const float dd[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w}, dc[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+        float xh[4], tb[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const float nu = a.delta_c - dc[h];
+            const float f = nu <= 0.0f ? 1.0f : erfcf(nu * inv);
+            float v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+            v = ((bits[k] >> h) & 1u) ? 0.0f : v;
+            xh[h] = v;
+            tb[h] = t0 * v * (1.0f + dd[h]);
+            xq += __float2int_rn(v * 8388608.0f);
+        }
+        const int pp = (4 * e) / N, zz = (4 * e) % N;
+        float2* d = reinterpret_cast<float2*>(s.ds + pp * P::DS + zz);
+        d[0] = make_float2(tb[0], tb[1]);
+        d[1] = make_float2(tb[2], tb[3]);
+        if (a.xhi_out)
+            reinterpret_cast<float4*>(a.xhi_out + (size_t)pair * n3 + cell0)[e] = make_float4(xh[0], xh[1], xh[2], xh[3]);
+    }
+    unsigned long long wsum = (unsigned long long)xq;       // a warp's cells can reach 2^32 in 2^-23 units
+    for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+    if ((t & 31) == 0) atomicAdd(a.xq + pair, wsum);
+    __syncthreads();
+    float2 z[P::NBp][P::P2];
+#pragma unroll
+    for (int q = 0; q < P::NBp; q++)
+#pragma unroll
+        for (int k2 = 0; k2 < P::P2; k2++) {
+            const int m = i + P::P2 * q + P::P1 * k2;
+            z[q][k2] = make_float2(s.ds[p * P::DS + 2 * m], s.ds[p * P::DS + 2 * m + 1]);
+        }
+    pencil_r2c<N>(s, p, i, z, a.dst + (size_t)slot * NH * N * N + (size_t)x * N + y0, (size_t)N * N);
+}
+
 // Inverse C2R along z of one task's plane-pass output, writing delta_R (normalised).
 template <int N>
 __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_density(const float2* src, float* out) {
@@ -881,6 +1105,10 @@ cudaError_t plane_ps(eor_ctx* c, const PSArgs& ap, int planes, int P) {
         trace_begin(c, kKPsPlane);
         k_lines_cols<-1, kLinePs><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
         trace_end(c);
+    } else if constexpr (N == 128) {
+        trace_begin(c, kKPsPlane);
+        k_plane_ps2<<<dim3(2 * planes, P), kPs2Threads, kPs2Smem, c->stream>>>(ap);
+        trace_end(c);
     } else {
         trace_begin(c, kKPsPlane);
         k_plane_ps<N, T><<<dim3(planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
@@ -903,30 +1131,46 @@ cudaError_t prepare_n() {
         if ((e = set_smem(k_plane_forward<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
         if ((e = set_smem(k_plane_filter_inverse<N, T>, Plane<N, T>::SMEM)) != cudaSuccess) return e;
         if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM_PS)) != cudaSuccess) return e;
+        if constexpr (N == 128)
+            if ((e = set_smem(k_plane_ps2, kPs2Smem)) != cudaSuccess) return e;
     }
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_forward_batch<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_pencil_brightness<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 // Power spectra of the delta T_b boxes of every (walker, redshift) written by the basis
 // contraction: batched R2C along z, then the plane pass with the shell sums.
 template <int N, int T>
-cudaError_t ps_from_boxes_n(eor_ctx* c) {
+cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
     constexpr int NH = N / 2 + 1;
     const int n_pairs = c->n_walkers * c->cfg.n_z, P = c->tune.pairs;
     cudaMemsetAsync(c->d_ps_sum, 0, sizeof(double) * n_pairs * c->cfg.n_bins, c->stream);
+    const bool flags = c->f16 && c->tune.method == kMethodBasis;   // the flag contraction's pencil pass
+    if (flags) cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * n_pairs, c->stream);
     const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
     for (int pair0 = 0; pair0 < n_pairs; pair0 += P) {
         trace_begin(c, kKForward);
-        k_pencil_forward_batch<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
-            c->d_dtb, c->d_psinter, pair0, n_pairs);
+        if (flags) {
+            BrightArgs ba{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, c->d_psinter,
+                          pair0, n_pairs, (float)c->cfg.delta_c};
+            k_pencil_brightness<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(ba);
+        } else {
+            k_pencil_forward_batch<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
+                c->d_dtb, c->d_psinter, pair0, n_pairs);
+        }
         trace_end(c);
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
         cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P);
         if (e != cudaSuccess) return e;
+    }
+    if (flags) {
+        trace_begin(c, kKFinish);
+        launch_xq_finish(c->d_xq, n_pairs, c->d_xhi_sum, c->stream);
+        trace_end(c);
     }
     return cudaGetLastError();
 }
@@ -1132,6 +1376,22 @@ cudaError_t launch_box_ps_raw(int n, const float* box, float2* spec, const signe
     }
 }
 
+// Shared-memory limits of the two kernels launch_box_ps_raw runs at grid size n (current device).
+cudaError_t prepare_box_ps_raw(int n) {
+    auto both = [](auto pencil, size_t ps, auto plane, size_t pls) {
+        cudaError_t e = set_smem(pencil, ps);
+        return e != cudaSuccess ? e : set_smem(plane, pls);
+    };
+    switch (n) {
+        case 16: return both(k_pencil_forward<16>, Pencil<16>::SMEM, k_plane_ps<16, 512>, Plane<16, 512>::SMEM_PS);
+        case 32: return both(k_pencil_forward<32>, Pencil<32>::SMEM, k_plane_ps<32, 512>, Plane<32, 512>::SMEM_PS);
+        case 64: return both(k_pencil_forward<64>, Pencil<64>::SMEM, k_plane_ps<64, 512>, Plane<64, 512>::SMEM_PS);
+        case 128:
+            return both(k_pencil_forward<128>, Pencil<128>::SMEM, k_plane_ps<128, 512>, Plane<128, 512>::SMEM_PS);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_noise_sigma(eor_ctx* c, const double* mock, const float* thermal, double model_frac, double* sums,
                                double* sigma) {
     const int nb = c->cfg.n_bins, nz = c->cfg.n_z;
@@ -1279,13 +1539,13 @@ cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
     if (c->tune.method == kMethodBasis || c->tune.method == kMethodBasisSimt) {
         cudaError_t e = launch_basis_ionize(c, xhi_out);
         if (e != cudaSuccess) return e;
-        return launch_ps_from_boxes(c);
+        return launch_ps_from_boxes(c, xhi_out);
     }
     cudaMemsetAsync(c->d_xhi_sum, 0, sizeof(double) * c->n_walkers * c->cfg.n_z, c->stream);
     EOR_DISPATCH(c, ionization_n, c, xhi_out)
 }
 
-cudaError_t launch_ps_from_boxes(eor_ctx* c) { EOR_DISPATCH(c, ps_from_boxes_n, c) }
+cudaError_t launch_ps_from_boxes(eor_ctx* c, float* xhi_out) { EOR_DISPATCH(c, ps_from_boxes_n, c, xhi_out) }
 
 cudaError_t launch_filtered_density(eor_ctx* c, int zi, float* out, const float* wtab) {
     EOR_DISPATCH(c, filtered_density_n, c, zi, out, wtab)

@@ -1,15 +1,15 @@
 // noalloc.cu — eor_box_power_spectrum_noalloc: the power spectrum of one box without any
 // device allocation.
 //
-// Some callers cannot allocate GPU memory where they need this result: code that runs
-// while a stream is being captured into a CUDA graph (a cudaMalloc there fails or breaks
-// the capture), code that must not synchronize the device (cudaMalloc and cudaFree can),
-// or applications that hand all device memory to their own pool. This entry point creates
-// no context and calls no cudaMalloc, cudaFree or allocating library routine. Its scratch
-// (the half spectrum of the box, the bin of every |m|^2, the shell sums and mode counts)
-// is one file-scope device array of kNoAllocBytes that every GPU which loads the library
-// holds until the process exits. Every call shares that array and overwrites it: calls
-// that overlap on the GPU race, so issue them on one stream (or otherwise serialize them).
+// Some callers cannot allocate GPU memory where they need this result: applications that
+// hand all device memory to their own pool or budget (a cudaMalloc outside it fails or
+// breaks their accounting), and code that must not synchronize the device (cudaMalloc and
+// cudaFree can). This entry point creates no context and calls no cudaMalloc, cudaFree or
+// allocating library routine. Its scratch (the half spectrum of the box, the bin of every
+// |m|^2, the shell sums and mode counts) is one file-scope device array of kNoAllocBytes
+// that every GPU which loads the library holds until the process exits. Every call shares
+// that array and overwrites it: calls that overlap on the GPU race, so issue them on one
+// stream (or otherwise serialize them).
 #include <math.h>
 
 #include <mutex>
@@ -32,8 +32,10 @@ static_assert(kNoAllocBytes <= EOR21_NOALLOC_SCRATCH_BYTES, "scratch size stated
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EOR21_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
+constexpr int kSizes = 4;                                  // n = 16, 32, 64, 128
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
+bool g_prepared[kMaxDevices][kSizes] = {};
 
 // Bin of every |m|^2 (FP64 decision, -1 outside [k_lo, k_hi) or k = 0).
 __global__ void k_noalloc_bins(int n_m2, double kf, double k_lo, double k_hi, int n_bins, signed char* bin) {
@@ -76,22 +78,25 @@ __global__ void k_noalloc_finish(const double* sums, const unsigned long long* c
     if (nmodes) nmodes[b] = (long long)k;
 }
 
-// Device address of the scratch array on the current device; looked up once per device.
-cudaError_t scratch_for_current_device(unsigned char** out) {
+// Device address of the scratch array on the current device (looked up once per device) and
+// the shared-memory limits of the two FFT kernels at grid size n (set once per device and n).
+cudaError_t scratch_for_current_device(int n, unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const int si = n == 16 ? 0 : n == 32 ? 1 : n == 64 ? 2 : 3;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        for (int n = 16; n <= kNoAllocMaxN; n *= 2) {
-            e = prepare_kernels(n);   // shared-memory limits of the FFT kernels on this device
-            if (e != cudaSuccess) return e;
-        }
         g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    if (!g_prepared[dev][si]) {
+        e = prepare_box_ps_raw(n);
+        if (e != cudaSuccess) return e;
+        g_prepared[dev][si] = true;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -113,7 +118,7 @@ extern "C" int eor_box_power_spectrum_noalloc(int n, double box_mpc, int n_bins,
         return EOR_EINVAL;
     }
     unsigned char* scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    cudaError_t e = scratch_for_current_device(n, &scratch);
     if (e != cudaSuccess) {
         set_global_error(std::string("eor_box_power_spectrum_noalloc set-up: ") + cudaGetErrorString(e));
         return EOR_ECUDA;

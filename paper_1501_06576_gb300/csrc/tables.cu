@@ -661,6 +661,7 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = build_walker_coefs(c, n_walkers)) != cudaSuccess) return e;
+    if (c->f16) return build_columns_f16(c, n_walkers);
     if (!c->d_tcB) return cudaSuccess;
     return build_columns(c, n_walkers);
 }

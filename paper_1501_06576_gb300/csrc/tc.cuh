@@ -46,6 +46,32 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
            | ((uint32_t)(m >> 4) << 24);   // M / 16
 }
 
+// Instruction descriptor of kind::f16 with FP16 operands (format 0) and FP32 accumulation,
+// both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4)                       // D format: F32
+           | (0u << 7)                     // A format: F16
+           | (0u << 10)                    // B format: F16
+           | ((uint32_t)(n >> 3) << 17)    // N / 8
+           | ((uint32_t)(m >> 4) << 24);   // M / 16
+}
+
+// D (+)= A * B for one K = 16 step of FP16 operands, issued by a single thread.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Byte offset of FP16 element (row, k) in the K-major no-swizzle core-matrix layout with
+// `sbo` bytes between 8-row groups: a core matrix is 8 rows x 8 values (16 bytes per row),
+// cores adjacent along K are 128 bytes apart.
+__host__ __device__ __forceinline__ uint32_t core_offset16(int row, int k, uint32_t sbo) {
+    return (uint32_t)((row >> 3) * sbo + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));

@@ -3,6 +3,8 @@
 // k_tc_check: one CTA computes D = A B^T (A 128 x 32, B n x 32, FP32 in global memory) with
 // TF32 tcgen05 MMAs accumulating in tensor memory: the operand layout, descriptors and
 // tensor-memory reads of the tensor-core contraction, checked in isolation.
+#include <cuda_fp16.h>
+
 #include "eor_internal.cuh"
 #include "tc.cuh"
 
@@ -14,9 +16,12 @@ constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s of GPU time per bounded wai
 // A bounded wait ran out: set kErrTimeout and keep the first record of where,
 // err[1] = role << 28 | barrier << 20 | chunk (roles 1 copy, 2 MMA, 3 epilogue; barriers
 // 1 A, 2 B full, 3 B empty, 4 meta full, 5 meta empty, 6 accumulator full, 7 accumulator free).
+// The fence orders the record before the abort flag that the caller raises next, so a thread
+// that gives up only because it saw that flag cannot overwrite the first record.
 __device__ __forceinline__ void record_timeout(int* err, int role, int bar, int chunk) {
     atomicOr(err, kErrTimeout);
     atomicCAS(err + 1, 0, (role << 28) | (bar << 20) | (chunk & 0xFFFFF));
+    __threadfence();
 }
 
 __global__ void __launch_bounds__(128) k_tc_check(const float* A, const float* B, float* D, int n, uint32_t ncols,
@@ -249,6 +254,11 @@ struct TcArgs {
     int n_z, chunks_per_z;
     int ksteps;                 // MMA K steps of 8: (rank + 1) / 8 rounded up
     long long n3;
+    // test-only failure injection (off: withhold = -1): the epilogue withholds its release of
+    // the accumulator buffer of chunk `withhold`, and the MMA thread's wait for that release
+    // gives up after free_wait_ns (every other wait keeps kWaitNs)
+    int withhold;
+    uint64_t free_wait_ns;
 };
 
 // One CTA: 256 cells of one redshift (two 128-row tiles) against every (walker, radius)
@@ -357,8 +367,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
             ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(c / kTcStages) & 1u, kTries, abort);
             if (!ok) { record_timeout(a.err, 2, 2, c); break; }
             if (c >= kTmemBufs)   // the epilogue of chunk c - kTmemBufs has released buffer tb
-                ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - kTmemBufs) / kTmemBufs) & 1u, kTries,
-                                            abort);
+                ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((c - kTmemBufs) / kTmemBufs) & 1u,
+                                            a.free_wait_ns, abort);
             if (!ok) { record_timeout(a.err, 2, 7, c); break; }
             tc::fence_after_sync();
             // the tiles' accumulators alternate, so that consecutive MMAs are independent
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_basis_ionize_tc(Tc
                 if (lane == 0) atomicAdd(a.xq + pair, (unsigned long long)xq);
             }
             tc::fence_before_sync();
-            tc::mbar_arrive(barE + tb);
+            if (c != a.withhold) tc::mbar_arrive(barE + tb);
         }
     }
     tc::fence_before_sync();
@@ -526,12 +536,16 @@ __global__ void k_xq_finish(const unsigned long long* xq, int pairs, double* xhi
 // first << 1 | last, or -1 for a group left empty; *ncols the number of columns including
 // padding. Thread 0 places the walkers, then the block fills the columns.
 __global__ void k_build_columns(const WalkerInfo* walkers, int n_walkers, int* goff, int* cols, int* gmeta,
-                                int* ncols) {
+                                int* ncols, int rcell_first) {
     static_assert(kMaxRadii <= 2 * kGroup, "a walker spans at most two groups");
+    // columns of a walker: all its radii (R_cell first) or only those above R_cell (at least
+    // one group, which carries the walker's x_HI even when it has no radius above R_cell)
+    auto width = [&](int nr) { return rcell_first ? nr : nr - 1; };
+    auto groups = [&](int nr) { const int ng = (width(nr) + kGroup - 1) / kGroup; return ng > 0 ? ng : 1; };
     if (threadIdx.x == 0) {
         int g = 0;
         for (int w = 0; w < n_walkers; w++) {
-            const int ng = (walkers[w].n_r + kGroup - 1) / kGroup;
+            const int ng = groups(walkers[w].n_r);
             if (ng == 2 && (g & 1)) g++;
             goff[w] = g;
             g += ng;
@@ -545,9 +559,9 @@ __global__ void k_build_columns(const WalkerInfo* walkers, int n_walkers, int* g
     for (int i = threadIdx.x; i < total; i += blockDim.x) gmeta[i] = -1;
     __syncthreads();
     for (int w = threadIdx.x / 32; w < n_walkers; w += blockDim.x / 32) {
-        const int nr = walkers[w].n_r, g0 = goff[w], ng = (nr + kGroup - 1) / kGroup;
+        const int nr = walkers[w].n_r, g0 = goff[w], ng = groups(nr);
         for (int i = threadIdx.x % 32; i < ng * kGroup; i += 32) {
-            const int j = i == 0 ? nr - 1 : (i < nr ? i - 1 : -1);
+            const int j = rcell_first ? (i == 0 ? nr - 1 : (i < nr ? i - 1 : -1)) : (i < nr - 1 ? i : -1);
             cols[(size_t)g0 * kGroup + i] = j >= 0 ? (w << 8) | j : -1;
         }
         for (int i = threadIdx.x % 32; i < ng; i += 32)
@@ -594,7 +608,7 @@ cudaError_t format_basis_tc(eor_ctx* c) {
 
 cudaError_t build_columns(eor_ctx* c, int n_walkers) {
     trace_begin(c, kKTables);
-    k_build_columns<<<1, 256, 0, c->stream>>>(c->d_walkers, n_walkers, c->d_goff, c->d_cols, c->d_gmeta, c->d_ncols);
+    k_build_columns<<<1, 256, 0, c->stream>>>(c->d_walkers, n_walkers, c->d_goff, c->d_cols, c->d_gmeta, c->d_ncols, 1);
     trace_end(c);
     const int chunks = tc_slots(c) / kTcN;
     trace_begin(c, kKTables);
@@ -611,7 +625,8 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     cudaError_t e = cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * pairs, c->stream);
     if (e != cudaSuccess) return e;
     TcArgs a{c->d_tcA, c->d_tcB, c->d_ncols, brightness_base(c), c->d_dtb, xhi_out, c->d_xq, pop_tables(c), c->d_err,
-             c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3};
+             c->cfg.n_z, tc_slots(c) / kTcN, (c->basis_rank + 1 + 7) / 8, (long long)c->n3,
+             c->dbg_withhold, c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
     trace_begin(c, kKBasis);
     const dim3 grid((unsigned)(c->n3 / kTcCells), c->cfg.n_z);
     if (a.ftab)
@@ -622,6 +637,458 @@ cudaError_t launch_basis_ionize_tc(eor_ctx* c, float* xhi_out) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     trace_begin(c, kKFinish);
     k_xq_finish<<<(pairs + 255) / 256, 256, 0, c->stream>>>(c->d_xq, pairs, c->d_xhi_sum);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP16 split contraction
+
+namespace {
+
+//
+// The step-function efficiency's contraction as a persistent kernel on FP16 tensor-core
+// operands. Each basis field is scaled by a power of two so that |F_b| 2^14 / sigma_b <= 2^14
+// (sigma_b >= max |F_b| over the box), each coefficient column by a power of two t so that
+// its largest entry lies in [2^13, 2^14); both sides are split x = hi + lo into two FP16
+// values (hi = x rounded to FP16, lo = the remainder rounded to FP16: 22 significant bits,
+// the same as the TF32 hi/lo split) and the three products hi*hi + hi*lo + lo*hi are laid
+// side by side along K, so that one K = 3 (rank + 1) contraction (padded to a multiple of 16)
+// gives D = t (delta_R - delta_crit(R)) with FP32 accumulation. t > 0 keeps the sign: the
+// Eq. 1 flag is again "sign bit of D clear at some radius". The R_cell radius is not a
+// column: delta at R_cell is the same field for every walker (delta_Rcell, one filtered
+// density per box), read per cell for the partial ionization.
+constexpr int kFM = 128;                        // cells per tile (MMA M)
+constexpr int kFN = 256;                        // coefficient columns per chunk (MMA N)
+constexpr int kFKMax = 96;                      // FP16 K slots at most (six MMA steps of 16)
+constexpr int kFStages = 3;                     // coefficient chunks in flight
+constexpr int kFGroups = kFN / kGroup;          // walker groups per chunk
+constexpr uint32_t kFMetaBytes = kFGroups * 16;
+constexpr int kFEpiWarps = 16;                  // four per tensor-memory lane quarter
+constexpr int kFThreads = 128 + 32 * kFEpiWarps;
+constexpr uint32_t kFTmemCols = 2 * kFN;        // two accumulator buffers
+constexpr float kFScale = 16384.0f;             // 2^14
+static_assert(kFTmemCols <= 512, "tensor memory");
+static_assert(kFN == 8 * kGroup && kFEpiWarps == 16, "epilogue: warp (q, p) reads groups 2p, 2p + 1 of lane quarter q");
+
+__host__ __device__ constexpr int f16_kslots(int rank) { return (3 * (rank + 1) + 15) / 16 * 16; }
+__host__ __device__ constexpr uint32_t f16_sbo(int k) { return (uint32_t)(k / 8) * 128u; }
+
+// sigma_b: the smallest power of two >= max |F_b| over the cells of box z (1 for a zero
+// field), as the bits of a positive float in fmax_bits[z][b] (atomicMax on the bits orders
+// positive floats).
+__global__ void k_field_absmax(const float* F, int kb, int rank, long long n3, unsigned int* fmax_bits) {
+    const int b = blockIdx.y, zi = blockIdx.z;
+    if (b >= rank) return;
+    const float* f = F + ((size_t)zi * kb + b) * n3;
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(f[i]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(fmax_bits + zi * 32 + b, __float_as_uint(m));
+}
+
+__global__ void k_field_scale(const unsigned int* fmax_bits, int n_z, float* fscale) {
+    const int i = threadIdx.x;
+    if (i >= n_z * 32) return;
+    const float m = __uint_as_float(fmax_bits[i]);
+    fscale[i] = m > 0.0f ? exp2f(ceilf(log2f(m))) : 1.0f;
+    if (fscale[i] < m) fscale[i] *= 2.0f;   // guard the rounding of log2f
+}
+
+// FP16 hi/lo split of a value whose magnitude is at most 2^14.
+__device__ __forceinline__ void split_f16(float x, __half& hi, __half& lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
+// A operands: [z][tile of 128 cells][128 x K FP16, core-matrix layout]. Row = cell, K slots:
+// segment 0 hi(a), segment 1 hi(a), segment 2 lo(a) with a_b = F_b 2^14 / sigma_b (b < rank)
+// and a_rank = 2^14 (the constant that carries the threshold), each segment rank + 1 long,
+// zero after 3 (rank + 1). One thread writes one 16-byte core row (8 K slots).
+__global__ void k_format_a16(const float* F, int kb, int rank, long long n3, int n_z, const float* fscale, int kslots,
+                             unsigned char* out) {
+    const int ls = rank + 1, kc = kslots / 8;
+    const uint32_t sbo = f16_sbo(kslots);
+    const size_t tile_bytes = (size_t)kFM * kslots * 2;
+    const long long total = (long long)n_z * n3 * kc;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e % kc);
+        const long long cell = (e / kc) % n3;
+        const int zi = (int)(e / ((long long)kc * n3));
+        __align__(16) __half v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = q * 8 + i, seg = k / ls, b = k % ls;
+            float a = 0.0f;
+            if (seg < 3) a = b < rank ? F[((size_t)zi * kb + b) * n3 + cell] * (kFScale / fscale[zi * 32 + b])
+                                      : (b == rank ? kFScale : 0.0f);
+            __half hi, lo;
+            split_f16(a, hi, lo);
+            v[i] = seg == 2 ? lo : (seg < 3 ? hi : __float2half_rn(0.0f));
+        }
+        const long long tile = cell / kFM;
+        const int row = (int)(cell % kFM);
+        unsigned char* dst = out + ((size_t)zi * (n3 / kFM) + tile) * tile_bytes + tc::core_offset16(row, q * 8, sbo);
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+    }
+}
+
+// Coefficient chunks: [z][chunk of 256 columns][256 x K FP16 | kFGroups group records of 16 B].
+// Column (walker w, radius j > ... above R_cell) holds b_b = t c_b(R_j) sigma_b / 2^14 (b < rank)
+// and b_rank = -t delta_crit(R_j) / 2^14, t a power of two that puts the largest |b| in
+// [2^13, 2^14); segments: hi(b), lo(b), hi(b). An infinite delta_crit becomes kNever. Padding
+// columns: b = 0 and b_rank = -2^13 (D < 0 everywhere). One block per chunk, one thread per
+// column; group records as the TF32 path's (walker << 2 | first << 1 | last, zeta, T0,
+// 1/sqrt(2 s^2(R_cell)) or 0).
+__global__ void __launch_bounds__(kFN) k_format_b16(const int* cols, const int* gmeta, const int* ncols,
+                                                    const float* coef, const PairInfo* pairs, int kb, int rank,
+                                                    int max_radii, int n_z, int chunks_per_z, const float* fscale,
+                                                    int kslots, unsigned char* out) {
+    const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kFN + row;
+    const int nc = *ncols, ls = rank + 1;
+    const uint32_t sbo = f16_sbo(kslots);
+    const size_t bbytes = (size_t)kFN * kslots * 2;
+    unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * (bbytes + kFMetaBytes);
+    float v[kBasisMax + 1];
+    const int cw = slot < nc ? cols[slot] : -1;
+    float mx = 0.0f;
+    if (cw >= 0) {
+        const int w = cw >> 8, j = cw & 255;
+        const float* src = coef + ((size_t)w * max_radii + j) * kb;
+        const float dcrit = pairs[(size_t)w * n_z + zi].delta_crit[j];
+        for (int b = 0; b < rank; b++) v[b] = src[b] * (fscale[zi * 32 + b] / kFScale);
+        v[rank] = -(isfinite(dcrit) ? dcrit : kNever) / kFScale;
+    } else {
+        for (int b = 0; b < rank; b++) v[b] = 0.0f;
+        v[rank] = -1.0f;
+    }
+    for (int b = 0; b <= rank; b++) mx = fmaxf(mx, fabsf(v[b]));
+    const float t = mx > 0.0f ? exp2f((float)(13 - ilogbf(mx))) : 1.0f;   // mx t in [2^13, 2^14)
+    for (int q = 0; q < kslots / 8; q++) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = q * 8 + i, seg = k / ls, b = k % ls;
+            __half hi = __float2half_rn(0.0f), lo = __float2half_rn(0.0f);
+            if (seg < 3) split_f16(v[b] * t, hi, lo);
+            h[i] = seg == 1 ? lo : hi;
+        }
+        *reinterpret_cast<uint4*>(chunk + tc::core_offset16(row, q * 8, sbo)) = *reinterpret_cast<const uint4*>(h);
+    }
+    if ((row & (kGroup - 1)) == 0) {
+        const int g = row / kGroup, gi = blockIdx.x * kFGroups + g;
+        const int info = gi < nc / kGroup ? gmeta[gi] : -1;
+        float zeta = 0.0f, t0 = 0.0f, inv = 0.0f;
+        if (info >= 0) {
+            const PairInfo& pi = pairs[(size_t)(info >> 2) * n_z + zi];
+            zeta = pi.zeta;
+            t0 = pi.t0;
+            inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
+        }
+        reinterpret_cast<int4*>(chunk + bbytes)[g] =
+            make_int4(info, __float_as_int(zeta), __float_as_int(t0), __float_as_int(inv));
+    }
+}
+
+// AND of all 32 values (LOP3 tree): its sign bit is clear iff some value has a clear sign bit.
+__device__ __forceinline__ uint32_t and32(const float (&v)[32]) {
+    uint32_t m[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        m[i] = __float_as_uint(v[i]) & __float_as_uint(v[i + 8]) & __float_as_uint(v[i + 16]) & __float_as_uint(v[i + 24]);
+    return (m[0] & m[1] & m[2]) & (m[3] & m[4] & m[5]) & (m[6] & m[7]);
+}
+
+struct F16Args {
+    const unsigned char* A;     // [n_z][tiles_per_z][a_bytes]
+    const unsigned char* B;     // [n_z][chunks_per_z][b_bytes + kFMetaBytes]
+    const int* ncols;           // [1] number of columns
+    uint32_t* flags;            // [pair][n3 / 32] Eq. 1 flags above R_cell, bit = cell % 32
+    int* err;
+    int n_z, chunks_per_z, tiles_per_z, ksteps;
+    uint32_t a_bytes, b_bytes, sbo;
+    long long n3;
+    int withhold;               // test-only failure injection (see TcArgs), -1 off
+    uint64_t free_wait_ns;
+};
+
+// Persistent CTA (one per SM): tiles of 128 cells t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (all cells of box 0 first), each against every coefficient chunk of its box. Roles: thread
+// 32 issues the bulk copies (a tile's A operands into one of two stages half-way through the
+// previous tile, once the MMAs of the tile two before are done; chunk g into stage
+// g % kFStages as soon as chunk g - kFStages has left it), thread 0 the MMAs (per chunk ksteps
+// M128 N256 K16 FP16 MMAs into tensor-memory buffer g % 2; it waits only for operands and a
+// free buffer, also across tiles), warps 4-19 the epilogue: warp (q = lane quarter, p) reads
+// its 32 cells' columns 64 p .. 64 p + 63 of the buffer, releases the buffer and, for the
+// walkers of groups 2p, 2p + 1, stores the Eq. 1 flags of its 32 cells as one word (a walker's
+// flag: the AND of the sign bits of its columns is clear). x_HI, delta T_b and the power
+// spectrum follow in the pencil pass. Chunk counters g run over all chunks of the CTA's
+// tiles. Every wait is bounded in GPU time; on a timeout the CTA records where (err[1]:
+// role, barrier, g), stops, waits for its MMAs and copies in flight and frees its tensor
+// memory.
+__global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* As = sm;                                    // [2][a_bytes]
+    unsigned char* Bs = As + 2 * a.a_bytes;                    // [kFStages][b_bytes]
+    unsigned char* Ms = Bs + kFStages * a.b_bytes;             // [kFStages][kFMetaBytes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFStages * kFMetaBytes);
+    uint64_t* barA = bars;                   // [2] A stage landed
+    uint64_t* barAe = barA + 2;              // [2] A stage free (MMAs of its tile done)
+    uint64_t* barB = barAe + 2;              // [kFStages] chunk (coefficients + meta) landed
+    uint64_t* barBe = barB + kFStages;       // [kFStages] its MMAs are done
+    uint64_t* barMe = barBe + kFStages;      // [kFStages] the epilogue has read its meta
+    uint64_t* barD = barMe + kFStages;       // [2] accumulator buffer ready
+    uint64_t* barE = barD + 2;               // [2] accumulator buffer released by the epilogue
+    uint64_t* barF = barE + 2;               // MMAs drained (abort path)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(barF + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int ncols = *a.ncols;
+    const int nch = (ncols + kFN - 1) / kFN;
+    const int total = a.n_z * a.tiles_per_z;
+    const int my_tiles = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const bool work = nch > 0 && my_tiles > 0;
+
+    if (warp == 0) tc::tmem_alloc(tslot, kFTmemCols);
+    if (t == 0) {
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(barA + s, 1);
+            tc::mbar_init(barAe + s, 1);
+            tc::mbar_init(barD + s, 1);
+            tc::mbar_init(barE + s, 32 * kFEpiWarps);
+        }
+        for (int s = 0; s < kFStages; s++) {
+            tc::mbar_init(barB + s, 1);
+            tc::mbar_init(barBe + s, 1);
+            tc::mbar_init(barMe + s, 32 * kFEpiWarps);
+        }
+        tc::mbar_init(barF, 1);
+        *abort = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    // copy-thread bookkeeping: parity of the phase each copy barrier still owes, or -1
+    int owedA[2] = {-1, -1}, owedB[kFStages];
+#pragma unroll
+    for (int s = 0; s < kFStages; s++) owedB[s] = -1;
+
+    if (t == 32 && work) {
+        // ---------------- copy thread
+        // A operands of tile j into stage j % 2 once the MMAs of tile j - 2 are done
+        auto issue_a = [&](int j) -> bool {
+            const int as = j & 1;
+            if (j >= 2 && !tc::mbar_wait_or_abort(barAe + as, (uint32_t)((j - 2) >> 1) & 1u, kWaitNs, abort)) {
+                record_timeout(a.err, 1, 9, j * nch);
+                return false;
+            }
+            const int tile = (int)blockIdx.x + j * (int)gridDim.x;
+            tc::mbar_expect_tx(barA + as, a.a_bytes);
+            tc::bulk_g2s(As + (size_t)as * a.a_bytes, a.A + (size_t)tile * a.a_bytes, a.a_bytes, barA + as);
+            owedA[as] = (j >> 1) & 1;
+            return true;
+        };
+        bool ok = issue_a(0);
+        for (int it = 0; it < my_tiles && ok; it++) {
+            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+            const int zi = tile / a.tiles_per_z;
+            const unsigned char* Bz = a.B + (size_t)zi * a.chunks_per_z * (a.b_bytes + kFMetaBytes);
+            for (int c = 0; c < nch; c++) {
+                // the next tile's A operands half-way through this tile's chunks
+                if (c == nch / 2 && it + 1 < my_tiles && !(ok = issue_a(it + 1))) break;
+                const int g = it * nch + c, st = g % kFStages;
+                const uint32_t use = (uint32_t)(g / kFStages);
+                if (use > 0) {
+                    ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kWaitNs, abort);
+                    if (!ok) { record_timeout(a.err, 1, 3, g); break; }
+                    ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kWaitNs, abort);
+                    if (!ok) { record_timeout(a.err, 1, 5, g); break; }
+                }
+                const unsigned char* src = Bz + (size_t)c * (a.b_bytes + kFMetaBytes);
+                tc::mbar_expect_tx(barB + st, a.b_bytes + kFMetaBytes);
+                tc::bulk_g2s(Bs + (size_t)st * a.b_bytes, src, a.b_bytes, barB + st);
+                tc::bulk_g2s(Ms + st * kFMetaBytes, src + a.b_bytes, kFMetaBytes, barB + st);
+                owedB[st] = (int)(use & 1u);
+            }
+        }
+        if (!ok) *abort = 1;
+    } else if (t == 0 && work) {
+        // ---------------- MMA thread
+        const uint32_t idesc = tc::idesc_f16(kFM, kFN);
+        bool ok = true;
+        for (int it = 0; it < my_tiles && ok; it++) {
+            const int as = it & 1;
+            if (!(ok = tc::mbar_wait_or_abort(barA + as, (uint32_t)(it >> 1) & 1u, kWaitNs, abort))) {
+                record_timeout(a.err, 2, 1, it * nch);
+                break;
+            }
+            const uint32_t abase = tc::smem_addr(As + (size_t)as * a.a_bytes);
+            for (int c = 0; c < nch; c++) {
+                const int g = it * nch + c, st = g % kFStages, tb = g & 1;
+                ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / kFStages) & 1u, kWaitNs, abort);
+                if (!ok) { record_timeout(a.err, 2, 2, g); break; }
+                if (g >= 2)   // the epilogue of chunk g - 2 has released buffer tb
+                    ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((g - 2) >> 1) & 1u, a.free_wait_ns, abort);
+                if (!ok) { record_timeout(a.err, 2, 7, g); break; }
+                tc::fence_after_sync();
+                const uint32_t bbase = tc::smem_addr(Bs + (size_t)st * a.b_bytes);
+                for (int ks = 0; ks < a.ksteps; ks++) {
+                    const uint64_t ad = tc::smem_desc(abase + ks * 256, tc::kLBO, a.sbo);
+                    const uint64_t bd = tc::smem_desc(bbase + ks * 256, tc::kLBO, a.sbo);
+                    tc::mma_f16(tmem + (uint32_t)(tb * kFN), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(barD + tb);    // accumulators ready for the epilogue
+                tc::mma_commit(barBe + st);   // coefficient stage free for the copy thread
+            }
+            if (ok) tc::mma_commit(barAe + as);   // the tile's A stage may be refilled
+        }
+        if (!ok) *abort = 1;
+    } else if (warp >= 4 && work) {
+        // ---------------- epilogue warps
+        const int e = warp - 4, q = warp & 3, p = e >> 2;
+        const long long words = a.n3 / 32;
+        bool ok = true;
+        for (int it = 0; it < my_tiles && ok; it++) {
+            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+            const int zi = tile / a.tiles_per_z;
+            const long long word = (long long)(tile % a.tiles_per_z) * (kFM / 32) + q;   // cells 32 word .. + 31
+            for (int c = 0; c < nch; c++) {
+                const int g = it * nch + c, st = g % kFStages, tb = g & 1;
+                const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(g >> 1) & 1u, kWaitNs, abort);
+                const bool okB = okD && tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / kFStages) & 1u, kWaitNs, abort);
+                if (!okB) {
+                    if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, g);
+                    *abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                float v0[32], v1[32];
+                tc::tmem_ld32x2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kFN + p * 2 * kGroup), v0, v1);
+                tc::fence_before_sync();
+                if (g != a.withhold) tc::mbar_arrive(barE + tb);   // accumulators in registers: buffer free
+                const int4* gm = reinterpret_cast<const int4*>(Ms + st * kFMetaBytes) + 2 * p;
+                const int m0 = gm[0].x, m1 = gm[1].x;
+                tc::mbar_arrive(barMe + st);
+                // Eq. 1 flags: AND of the sign bits over the walker's radii above R_cell; group
+                // 2p + 1 continues the walker of group 2p when it is not a first group
+                const uint32_t a0 = and32(v0), a1 = and32(v1);
+                const uint32_t w0 = __ballot_sync(0xffffffffu, (a0 >> 31) == 0u);
+                const uint32_t w1 = __ballot_sync(0xffffffffu, (((m1 & 2) == 0 ? (a0 & a1) : a1) >> 31) == 0u);
+                if (lane == 0) {
+                    if (m0 >= 0 && (m0 & 1)) a.flags[((size_t)(m0 >> 2) * a.n_z + zi) * words + word] = w0;
+                    if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (work && *abort) {
+        if (t == 0) {   // drain every MMA issued so far
+            tc::mma_commit(barF);
+            tc::mbar_wait(barF, 0, kWaitNs);
+        } else if (t == 32) {   // wait for every bulk copy that may still land
+            for (int s = 0; s < 2; s++)
+                if (owedA[s] >= 0) tc::mbar_wait(barA + s, (uint32_t)owedA[s], kWaitNs);
+            for (int s = 0; s < kFStages; s++)
+                if (owedB[s] >= 0) tc::mbar_wait(barB + s, (uint32_t)owedB[s], kWaitNs);
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) {
+        __syncwarp();
+        tc::tmem_dealloc(tmem, kFTmemCols);
+    }
+}
+
+int f16_slots(const eor_ctx* c) {
+    const int groups = (c->max_radii + kGroup - 1) / kGroup;
+    const int per_walker = (groups > 1 ? groups + 1 : groups) * kGroup;
+    return (c->cfg.max_walkers * per_walker + kFN - 1) / kFN * kFN;
+}
+
+// Dynamic shared memory of the contraction: at least 120 KB, so that one CTA holds an SM (and
+// all of its tensor memory) at every basis size.
+size_t f16_smem(int kslots) {
+    const size_t a = (size_t)kFM * kslots * 2, b = (size_t)kFN * kslots * 2;
+    const size_t need = 2 * a + kFStages * (b + kFMetaBytes) + (4 + 3 * kFStages + 4 + 1) * sizeof(uint64_t) + 16;
+    return need > (120u << 10) ? need : (120u << 10);
+}
+
+}  // namespace
+
+bool basis_f16_fits(int rank) { return rank >= 1 && f16_kslots(rank) <= kFKMax; }
+int basis_f16_kslots(int rank) { return f16_kslots(rank); }
+size_t basis_f16_a_bytes(long long n3, int n_z, int rank) { return (size_t)n_z * (size_t)n3 * f16_kslots(rank) * 2; }
+size_t basis_f16_b_bytes(const eor_ctx* c) {
+    return (size_t)c->cfg.n_z * (size_t)(f16_slots(c) / kFN) * ((size_t)kFN * c->k16 * 2 + kFMetaBytes);
+}
+size_t basis_f16_column_slots(const eor_ctx* c) { return (size_t)f16_slots(c); }
+
+cudaError_t prepare_basis_f16(eor_ctx* c) {
+    if (!c->f16) return cudaSuccess;
+    return cudaFuncSetAttribute(k_basis_ionize_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f16_smem(c->k16));
+}
+
+// At eor_init_boxes: the power-of-two bounds of the basis fields, delta at R_cell of every box
+// (the filtered density of the per-radius path, one per box) and the A operands.
+cudaError_t format_basis_f16(eor_ctx* c) {
+    cudaError_t e;
+    const int nz = c->cfg.n_z;
+    unsigned int* bits = reinterpret_cast<unsigned int*>(c->d_fscale + nz * 32);   // scratch after the scales
+    if ((e = cudaMemsetAsync(bits, 0, sizeof(unsigned int) * nz * 32, c->stream)) != cudaSuccess) return e;
+    trace_begin(c, kKOther);
+    k_field_absmax<<<dim3(256, c->basis_rank, nz), 256, 0, c->stream>>>(c->d_F, c->kb, c->basis_rank, (long long)c->n3,
+                                                                         bits);
+    trace_end(c);
+    trace_begin(c, kKOther);
+    k_field_scale<<<1, 256, 0, c->stream>>>(bits, nz, c->d_fscale);
+    trace_end(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double dx = c->cfg.box_mpc / c->n;
+    const double r_cell = c->cfg.r_cell_rule == 1 ? dx : cbrt(3.0 / (4.0 * kPi)) * dx;
+    if ((e = launch_window_table(c, r_cell, c->d_diag_wtab)) != cudaSuccess) return e;
+    for (int zi = 0; zi < nz; zi++)
+        if ((e = launch_filtered_density(c, zi, c->d_dcell + (size_t)zi * c->n3, c->d_diag_wtab)) != cudaSuccess)
+            return e;
+    trace_begin(c, kKOther);
+    k_format_a16<<<4096, 256, 0, c->stream>>>(c->d_F, c->kb, c->basis_rank, (long long)c->n3, nz, c->d_fscale, c->k16,
+                                              c->d_a16);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+cudaError_t build_columns_f16(eor_ctx* c, int n_walkers) {
+    trace_begin(c, kKTables);
+    k_build_columns<<<1, 256, 0, c->stream>>>(c->d_walkers, n_walkers, c->d_goff, c->d_cols, c->d_gmeta, c->d_ncols, 0);
+    trace_end(c);
+    const int chunks = f16_slots(c) / kFN;
+    trace_begin(c, kKTables);
+    k_format_b16<<<dim3(chunks, c->cfg.n_z), kFN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
+                                                                 c->d_pairs, c->kb, c->basis_rank, c->max_radii,
+                                                                 c->cfg.n_z, chunks, c->d_fscale, c->k16, c->d_b16);
+    trace_end(c);
+    return cudaGetLastError();
+}
+
+void launch_xq_finish(const unsigned long long* xq, int pairs, double* xhi_sum, cudaStream_t s) {
+    k_xq_finish<<<(pairs + 255) / 256, 256, 0, s>>>(xq, pairs, xhi_sum);
+}
+
+cudaError_t launch_basis_ionize_f16(eor_ctx* c) {
+    const int tiles_per_z = (int)(c->n3 / kFM);
+    const int total = tiles_per_z * c->cfg.n_z;
+    F16Args a{c->d_a16, c->d_b16, c->d_ncols, c->d_fwords, c->d_err, c->cfg.n_z, f16_slots(c) / kFN, tiles_per_z,
+              c->k16 / 16, (uint32_t)(kFM * c->k16 * 2), (uint32_t)(kFN * c->k16 * 2), f16_sbo(c->k16),
+              (long long)c->n3, c->dbg_withhold, c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
+    const int grid = total < c->num_sms ? total : c->num_sms;
+    trace_begin(c, kKBasis);
+    k_basis_ionize_f16<<<grid, kFThreads, f16_smem(c->k16), c->stream>>>(a);
     trace_end(c);
     return cudaGetLastError();
 }

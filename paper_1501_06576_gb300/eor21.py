@@ -22,7 +22,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_efficiency", "eor_set_params",
            "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_trace",
+           "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_basis_window", "eor_contraction_info", "eor_debug_withhold", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
            "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
@@ -35,6 +35,7 @@ EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_effici
 EMU_MAX_HIDDEN, EMU_MAX_MEMBERS = 8, 8
 KERNEL_CLASSES = 8
 EOR_METHOD_BASIS, EOR_METHOD_DIRECT, EOR_METHOD_BASIS_SIMT = 0, 1, 2
+EOR_CONTRACT_NONE, EOR_CONTRACT_FP32, EOR_CONTRACT_TF32, EOR_CONTRACT_FP16 = 0, 1, 2, 3
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -114,6 +115,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_autotune": (I, [P, P, I, P, P, I, P, P, P, P, I]),
         "eor_noise_sigma": (I, [P, P, P, D, P, I]),
         "eor_basis_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "eor_basis_window": (I, [P, D, P, I]),
+        "eor_debug_withhold": (I, [P, I, D]),
+        "eor_contraction_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "eor_trace": (I, [P, I]),
         "eor_trace_read": (I, [P, P, P, I]),
         "eor_kernel_class_name": (ctypes.c_char_p, [I]),
@@ -374,6 +378,24 @@ class Context:
         self._check(self.lib.eor_basis_info(self.handle, ctypes.byref(r), ctypes.byref(e)))
         return r.value, e.value
 
+    def eor_basis_window(self, r_mpc: float) -> np.ndarray:
+        """sum_b c_b(R) phi_b on every |m|^2 index 0 .. 3 (n/2)^2 (NaN where no mode has it)."""
+        n = self.cfg.n
+        out = np.empty(3 * (n // 2) ** 2 + 1, dtype=np.float64)
+        self._check(self.lib.eor_basis_window(self.handle, float(r_mpc), out.ctypes.data_as(ctypes.c_void_p),
+                                              EOR_HOST))
+        return out
+
+    def eor_contraction_info(self):
+        """(kind, K slots) of the contraction the current method runs (EOR_CONTRACT_*)."""
+        k, ks = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.eor_contraction_info(self.handle, ctypes.byref(k), ctypes.byref(ks)))
+        return k.value, ks.value
+
+    def eor_debug_withhold(self, chunk: int, wait_ms: float = 1.0):
+        """Test-only: make the contraction withhold one accumulator release (chunk < 0: off)."""
+        self._check(self.lib.eor_debug_withhold(self.handle, int(chunk), float(wait_ms)))
+
     def eor_trace(self, enable: bool = True):
         self._check(self.lib.eor_trace(self.handle, 1 if enable else 0))
 
@@ -408,6 +430,9 @@ class Context:
     autotune = eor_autotune
     noise_sigma = eor_noise_sigma
     basis_info = eor_basis_info
+    basis_window = eor_basis_window
+    debug_withhold = eor_debug_withhold
+    contraction_info = eor_contraction_info
     trace_read = eor_trace_read
     launch_count = eor_launch_count
 
@@ -675,15 +700,41 @@ class Sampler:
     walkers = eor_mcmc_walkers
 
 
+def check_noalloc_tensors(n: int, n_bins: int, box, d2, nmodes, device: int) -> None:
+    """Refuse tensors that eor_box_power_spectrum_noalloc would misread: each must be a
+    contiguous CUDA tensor on `device` with the dtype and element count the call reads or
+    writes (box float32 with n^3 elements; d2 float64 and nmodes int64 with at least n_bins
+    elements). Raises ValueError."""
+    import torch
+    need = [("box", box, torch.float32, n ** 3, True), ("d2", d2, torch.float64, n_bins, False)]
+    if nmodes is not None:
+        need.append(("nmodes", nmodes, torch.int64, n_bins, False))
+    for name, t, dtype, count, exact in need:
+        if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+        if (t.numel() != count) if exact else (t.numel() < count):
+            raise ValueError(f"{name} has {t.numel()} elements; {'exactly' if exact else 'at least'} {count} needed")
+        if t.device.index != device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{device}")
+
+
 def box_power_spectrum_noalloc(n: int, box_mpc: float, box, d2, nmodes=None, n_bins: int = 14, k_lo: float = 0.1,
                                k_hi: float = 1.5, stream=None) -> None:
-    """eor_box_power_spectrum_noalloc on CUDA tensors (box float32 [n,n,n], d2 float64 [n_bins],
-    nmodes int64 [n_bins] or None); ordered on `stream` (a cudaStream_t handle), no wait."""
+    """eor_box_power_spectrum_noalloc on CUDA tensors of the current device: box float32 with
+    n^3 elements, d2 float64 with at least n_bins elements, nmodes int64 with at least n_bins
+    elements or None. The work is ordered on `stream` (a cudaStream_t handle) and the call
+    returns without waiting. The library checks only sizes and ranges, since it sees raw
+    device pointers; this wrapper also checks each tensor's dtype, element count and device
+    (check_noalloc_tensors), so that a mismatched tensor is refused here instead of being
+    read or written out of bounds on the GPU. The first call for each (device, n) does the
+    set-up that the header describes; make it before any stream capture."""
+    import torch
+    n, n_bins = int(n), int(n_bins)
+    check_noalloc_tensors(n, n_bins, box, d2, nmodes, torch.cuda.current_device())
     lib = load_library()
-    for t in (box, d2) + (() if nmodes is None else (nmodes,)):
-        if not _is_torch_cuda(t) or not t.is_contiguous():
-            raise ValueError("box, d2 and nmodes must be contiguous CUDA tensors")
-    rc = lib.eor_box_power_spectrum_noalloc(int(n), float(box_mpc), int(n_bins), float(k_lo), float(k_hi),
+    rc = lib.eor_box_power_spectrum_noalloc(n, float(box_mpc), n_bins, float(k_lo), float(k_hi),
                                             ctypes.c_void_p(box.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                                             None if nmodes is None else ctypes.c_void_p(nmodes.data_ptr()),
                                             ctypes.c_void_p(stream) if stream else None)

@@ -99,6 +99,32 @@ def test_pops_parity(model, walkers, method, boxes):
             assert rel.max() <= PS_TOL, (w, j, rel.max())
 
 
+@pytest.mark.parametrize("model,walker", [(1, MODEL1[0]), (2, MODEL2[0])], ids=["two_populations", "feedback_form"])
+def test_pops_end_to_end_64cube(model, walker):
+    """64^3 at the same 1.95 Mpc cells (L = 125 Mpc, z = 9): enough modes per bin for the
+    1e-3 per-bin tolerance end to end, every cell against the oracle's own realization."""
+    n, box, z = 64, 125.0, 9.0
+    delta = synth.density_boxes(n, box, (z,), seed=43)
+    p, q = walker
+    with eor21.Context(n=n, box_mpc=box, z=(z,), max_walkers=1, efficiency_model=model) as ctx:
+        ctx.init_boxes(delta)
+        ctx.set_efficiency(np.array([q]))
+        ctx.set_params(np.array([p]))
+        xhi, mean = ctx.run_ionization(want_xhi=True)
+        d2, _, cnt = ctx.power_spectrum()
+    o = oracle.Oracle()
+    ion = o.ionize_pops(delta[0], box, z, o.populations(model, p, q, z), p[1])
+    diff = np.abs(xhi[0, 0].astype(np.float64) - ion["xhi"])
+    flipped = diff > 1e-3
+    assert flipped.mean() <= FLIP_TOL, flipped.mean()
+    assert diff[~flipped].max() <= XHI_TOL
+    assert abs(mean[0, 0] - ion["xhi_mean"]) <= XHI_TOL
+    rd2, _, rcnt = oracle.power_spectrum(ion["dtb"], box)
+    ok = rcnt > 0
+    assert np.array_equal(cnt[0, 0], rcnt)
+    assert np.max(np.abs(d2[0, 0][ok] - rd2[ok]) / np.abs(rd2[ok])) <= PS_TOL
+
+
 def test_falling_efficiency_gives_upper_crossings(boxes):
     # with alpha = -0.5 and a large region the weighted fraction rises and falls again: some
     # overdense cells are ionized only at smaller radii; the oracle agrees cell by cell above

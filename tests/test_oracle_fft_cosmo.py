@@ -67,6 +67,58 @@ def test_bbks_small_q_limit():
     assert np.all(np.diff(t) < 0) and np.all(t > 0)
 
 
+# The BBKS fitting form (Bardeen, Bond, Kaiser & Szalay 1986, App. G) is
+#   T(q) = ln(1 + a q)/(a q) [1 + b1 q + (b2' q)^2 + (b3' q)^3 + (b4' q)^4]^(-1/4)
+# with a = 2.34, b1 = 3.89, b2' = 16.1, b3' = 5.46, b4' = 6.71. The two tests below pin the
+# oracle's transcription of all five numbers through routes other than the formula: the
+# first three Taylor coefficients at q -> 0 (expanded by hand: ln(1+x)/x = 1 - x/2 + x^2/3
+# - x^3/4 and (1+u)^(-1/4) = 1 - u/4 + 5u^2/32 - 15u^3/128), read off the oracle's values
+# by a least-squares polynomial fit, and the large-q asymptote T ~ ln(1 + a q)/(a q) /
+# (b4' q) with its first correction -b3'^3/(4 b4'^4 q). A slip of 0.2 % in any number fails
+# at least one of them. The fit's source prints the coefficients, not values of T(q).
+BBKS = dict(a=2.34, b1=3.89, b2=16.1, b3=5.46, b4=6.71)
+
+
+def _bbks_taylor():
+    a, b1 = BBKS["a"], BBKS["b1"]
+    b2, b3 = BBKS["b2"] ** 2, BBKS["b3"] ** 3
+    p2 = -b2 / 4 + 5 * b1 ** 2 / 32                       # q^2 of the bracket^(-1/4)
+    p3 = -b3 / 4 + 10 * b1 * b2 / 32 - 15 * b1 ** 3 / 128  # q^3 of the bracket^(-1/4)
+    c1 = -a / 2 - b1 / 4
+    c2 = a * a / 3 + (a / 2) * (b1 / 4) + p2
+    c3 = -a ** 3 / 4 - (a * a / 3) * (b1 / 4) - (a / 2) * p2 + p3
+    return c1, c2, c3
+
+
+def test_bbks_taylor_coefficients_at_small_q():
+    h, deg, n = 0.016, 9, 400
+    s = 0.5 + 0.5 * np.cos(np.pi * (np.arange(n) + 0.5) / n)   # Chebyshev nodes on [0, 1]
+    t = np.array([oracle.bbks_transfer(v) for v in s * h])
+    co = np.polynomial.polynomial.polyfit(s, t, deg)
+    c1, c2, c3 = _bbks_taylor()
+    assert abs(co[0] - 1.0) < 1e-9
+    assert abs(co[1] / h / c1 - 1.0) < 1e-6          # a/2 + b1/4
+    assert abs(co[2] / h ** 2 / c2 - 1.0) < 1e-5     # fixes b2' given a, b1
+    assert abs(co[3] / h ** 3 / c3 - 1.0) < 1e-3     # fixes b3' given a, b1, b2'
+
+
+def test_bbks_large_q_asymptote():
+    a, b3, b4 = BBKS["a"], BBKS["b3"] ** 3, BBKS["b4"] ** 4
+    for q in (1e4, 1e5, 1e6):
+        ratio = oracle.bbks_transfer(q) * (a * q) * (BBKS["b4"] * q) / np.log1p(a * q)
+        # 1 - b3/(4 b4 q) + O(q^-2): the leading term fixes a and b4', the first correction b3'
+        assert abs(ratio - 1.0) < 3e-6 * (1e4 / q)
+        assert abs((ratio - 1.0) * q / (-b3 / (4 * b4)) - 1.0) < 2e-4 * max(1.0, 1e4 / q)
+
+
+def test_input_generator_spectrum_shape_is_the_oracle_transfer():
+    """synth.py (the seeded input generator both sides read) carries its own BBKS copy."""
+    from paper_1501_06576_gb300 import synth
+    q = np.logspace(-5, 4, 200)
+    ref = np.array([oracle.bbks_transfer(v) for v in q])
+    np.testing.assert_allclose(synth._bbks(q), ref, rtol=1e-10)   # log1p vs log(1 + x) at small q
+
+
 def test_sigma2_white_spectrum_closed_form():
     # P(k) = A (n_s = 0, no transfer): the top-hat smoothed variance is A / V_R. The
     # integrand falls only as 1/k, so the quadrature's cut at k = 1e4/Mpc leaves a
