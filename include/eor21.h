@@ -485,7 +485,10 @@ int eor_mcmc_walkers(eor_mcmc* m, double* params, double* lnp, int mem);
 const char* eor_mcmc_last_error(const eor_mcmc* m);
 void eor_mcmc_destroy(eor_mcmc* m);
 
-/* Message of the last failed call on ctx (ctx may be NULL for eor_create failures). */
+/* Message of the last failed call on ctx. With ctx NULL: the message of the calling host
+ * thread's last failed call that has no context (eor_create, eor_box_power_spectrum_noalloc,
+ * eor_tensor_core_check); that message is kept per thread, so threads that fail such calls
+ * at the same time do not overwrite each other's. */
 const char* eor_last_error(const eor_ctx* ctx);
 const char* eor_version(void);
 void eor_destroy(eor_ctx* ctx);

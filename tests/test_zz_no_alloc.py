@@ -40,9 +40,11 @@ def test_noalloc_power_spectrum_matches_context_entry_point():
         free_after.append(torch.cuda.mem_get_info()[0])
         np.testing.assert_array_equal(nmodes.cpu().numpy(), ref_cnt)
         np.testing.assert_allclose(d2.cpu().numpy(), ref_d2, rtol=1e-9)
-    # the scratch is the library's static array: the first call took less device memory than
-    # the array's size (at most kernel code loaded on first use), the second call none
-    assert free_before - free_after[0] < 8 << 20
+    # the scratch is the library's static array (EOR21_NOALLOC_SCRATCH_BYTES = 9 MiB): the
+    # driver may place it in device memory when the entry point first needs it (in 2 MiB
+    # pages), so the first call may take the array itself and nothing more; the second none
+    scratch, page = 9 << 20, 2 << 20
+    assert free_before - free_after[0] <= (scratch + page - 1) // page * page
     assert free_after[1] >= free_after[0]
 
 
