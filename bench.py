@@ -584,10 +584,11 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
         total = sum(v[0] for v in cls.values()) or 1.0
         share = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total} for k, v in cls.items() if v[1] > 0}
         rank, _ = ctx.basis_info()[:2]
+        kind, kslots = ctx.contraction_info()
         radii = sum(len(ctx.walker_ladder(k)) for k in range(w)) * len(zs)
         launches = ctx.launch_count()
         ctx.close()
-    rates = two_pop_rates(share, rank, radii, n, box, w * len(zs))
+    rates = two_pop_rates(share, rank, radii, n, box, w * len(zs), fp16=kind == eor21.EOR_CONTRACT_FP16)
     return {"value": w / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms, "walkers": w,
             "workload": ("256^3, L = 500 Mpc, z = 8, 9, 10, two populations (efficiency_model 1), alpha in "
                          "[-0.5, 0.5], zeta_i0 in [5, 100], log10 T_vir,i in [4, 6], R_mfp in [5, 20] Mpc") if model else
@@ -597,7 +598,7 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
             "classes_traced_step": share, "rates": rates, "dtype": "f32 (FP64 tables)"}
 
 
-def two_pop_rates(share, rank: int, radii: int, n: int, box: float, pairs: int) -> dict:
+def two_pop_rates(share, rank: int, radii: int, n: int, box: float, pairs: int, fp16: bool = False) -> dict:
     """Achieved rates of the traced replay: the contraction's useful TFLOP/s (2 x rank flop per
     cell and radius task) and the power spectrum's algorithmic GB/s (per (walker, z): the R2C
     pencil pass reads the n^3 delta T_b box and writes the nh n^2 half spectrum; the row pass
@@ -608,7 +609,7 @@ def two_pop_rates(share, rank: int, radii: int, n: int, box: float, pairs: int) 
         c_ms = share.get("basis_ionize", {}).get("ms", 0.0)
         if c_ms > 0:
             tflops = 2.0 * rank * n ** 3 * radii / (c_ms / 1e3) / 1e12
-            peak, kind = tf32_peak_tflops()
+            peak, kind = fp16_peak_tflops() if fp16 else tf32_peak_tflops()
             out["contraction"] = {"achieved": tflops, "unit": "TFLOP/s", "peak": peak, "frac": tflops / peak,
                                   "peak_kind": kind}
         kf = 2.0 * math.pi / box
@@ -674,6 +675,7 @@ def main():
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         # launch schedule picked by the library's autotuner on these walkers (untimed set-up)
         tuned = ctx.autotune(d_params, d_mock, d_sigma, reps=3)
+        schedule = ctx.get_tuning()
         ctx.trace(not args.no_trace)
         for _ in range(args.warmup):
             ctx.likelihood(d_params, d_mock, d_sigma)
@@ -718,12 +720,16 @@ def main():
 
         # ---------------- the per-radius FFT method on the same workload (for comparison)
         ctx.trace(False)
-        direct = simt = None
+        direct = simt = tf32 = None
         for _ in range(0 if args.no_direct else 1):
             direct = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps)
             simt = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps,
                                method=eor21.EOR_METHOD_BASIS_SIMT,
                                note="basis contraction on the FP32 units (EOR_METHOD_BASIS_SIMT), same walkers")
+            tf32 = time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, args.steps,
+                               method=eor21.EOR_METHOD_BASIS_TF32,
+                               note="basis contraction on 3xTF32 tensor-core operands with x_HI and delta T_b in "
+                                    "its epilogue (EOR_METHOD_BASIS_TF32), same walkers")
 
         # ---------------- end to end through host buffers (pinned), D2H of chi^2 every step
         h_params = torch.from_numpy(params).pin_memory().numpy()
@@ -871,8 +877,7 @@ def main():
             "config": {"workload": WORKLOAD, "n": N, "box_mpc": BOX, "z": list(ZS), "walkers_per_gpu": W,
                        "radius_tasks_per_step": tasks_per_step, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"walkers sharded over {world} GPU(s)", "traced": not args.no_trace,
-                       "schedule": {"group": tuned[0], "pairs": tuned[1], "plane_threads": tuned[2],
-                                    "picked_by": "eor_autotune"}},
+                       "schedule": {**schedule, "picked_by": "eor_autotune"}},
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof,
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
@@ -881,7 +886,7 @@ def main():
                                        eor21.EOR_CONTRACT_FP32: "FP32 FMA"}.get(contract_kind, "none"),
                        "k_slots": k_slots},
             "emulator": emulator, "mcmc": mcmc, "two_population": two_pop,
-            "basis_fp32_units": simt, "direct_method": direct,
+            "basis_fp32_units": simt, "basis_tf32": tf32, "direct_method": direct,
             "per_radius_fft_bytes_over_step": {
                 "value": per_radius_rate, "unit": "GB/s", "frac_of_hbm": per_radius_rate / hbm_peak,
                 "peak_kind": hbm_kind,

@@ -209,14 +209,23 @@ int eor_noise_sigma(eor_ctx* ctx, const double* mock_d2, const float* thermal, d
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
 
+/* The plane tiling of the power spectrum's 2D transform at n = 128: split 1 = one CTA per
+ * 128 x 128 plane (132 KB of shared memory), split 2 = a cluster of two CTAs per plane (each
+ * holds 64 rows, transforms them, then 64 columns reading the other half through distributed
+ * shared memory; two such CTAs share an SM). Default 2; EOR_ENOTSUP for 2 at other n. Drops
+ * the captured graph. eor_get_tuning reads the current schedule (each pointer optional). */
+int eor_set_ps_split(eor_ctx* ctx, int split);
+int eor_get_tuning(const eor_ctx* ctx, int* group, int* pairs, int* plane_threads, int* ps_split);
+
 /* Autotuner of the launch schedule (results do not depend on it): times eor_likelihood on
  * these walkers (arguments as there, n_walkers <= max_walkers) with CUDA events on the
  * context's stream, `reps` graph replays per candidate after one warm-up, over the
- * candidates of the current method -- pairs in {4, 8, 16, 32} x plane_threads in {512, 1024}
- * (128^3 grids; 512 otherwise), and for EOR_METHOD_DIRECT also group in {4, 8, 16} -- and
- * keeps the fastest (eor_set_tuning). group, pairs, plane_threads and ms (mean milliseconds
- * of one call) receive the choice; each optional. Tracing is off while it runs and is
- * restored afterwards. */
+ * candidates of the current method -- pairs in {4, 8, 16, 32} x the spectrum's plane tiling
+ * (128^3 grids: split 2, or split 1 with plane_threads 512 or 1024; split 1 and 512
+ * otherwise), and for EOR_METHOD_DIRECT also group in {4, 8, 16} and plane_threads with
+ * both splits -- and keeps the fastest (eor_set_tuning, eor_set_ps_split). group, pairs,
+ * plane_threads and ms (mean milliseconds of one call) receive the choice, each optional;
+ * eor_get_tuning gives the split. Tracing is off while it runs and is restored afterwards. */
 int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2, const double* sigma,
                  int reps, int* group, int* pairs, int* plane_threads, double* ms, int mem);
 
@@ -225,16 +234,18 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
  *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
  *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-6 on the grid's |k| for every R in
  *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
- *   that contraction, which runs on the tensor cores (tcgen05) with FP32 accumulation:
- *   with the step-function efficiency on power-of-two-scaled FP16 operands split into
- *   hi + lo parts (three products side by side along K, basis of at most 31 functions),
- *   with a mass-dependent efficiency on TF32 hi + lo operands (three products per step,
- *   basis of at most 31 functions); else on the FP32 units.
+ *   that contraction, which runs on the tensor cores (tcgen05, FP32 accumulation) on
+ *   power-of-two-scaled FP16 operands split into hi + lo parts (three products side by side
+ *   along K) when the basis has at most 31 functions, else on the FP32 units; it yields the
+ *   Eq. 1 flags, and x_HI, delta T_b and the spectrum follow in the pencil and plane passes.
+ * EOR_METHOD_BASIS_TF32: the same contraction on TF32 hi + lo operands (three products per
+ *   K step of 8, x_HI and delta T_b in its epilogue): the previous form, kept for comparison
+ *   (its operands are allocated when it is chosen).
  * EOR_METHOD_BASIS_SIMT: the same contraction on the FP32 units only.
  * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius.
  * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. A bounded
  * tensor-core wait that runs out makes the call return EOR_ETIMEOUT. */
-enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2 };
+enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2, EOR_METHOD_BASIS_TF32 = 3 };
 int eor_set_method(eor_ctx* ctx, int method);
 int eor_basis_info(const eor_ctx* ctx, int* rank, double* max_residual);
 /* The contraction the current method runs: *kind = EOR_CONTRACT_NONE (the direct method),

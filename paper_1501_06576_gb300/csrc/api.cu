@@ -154,29 +154,33 @@ void set_global_error(const std::string& msg) { g_create_error = msg; }
 
 // Record on the context's stream; while the stream is being captured, as an external event
 // node so the graph records it on every replay.
-static void trace_record(eor_ctx* c, cudaEvent_t e) {
+static void trace_record(cudaStream_t s, cudaEvent_t e) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(c->stream, &st);
-    if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
-    else cudaEventRecord(e, c->stream);
+    cudaStreamIsCapturing(s, &st);
+    if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
 }
 
-void trace_begin(eor_ctx* c, int cls) {
+// The pair of events of one launch on stream s (the launch it brackets runs between them).
+void trace_begin_on(eor_ctx* c, int cls, cudaStream_t s) {
     if (!c->trace_on) return;
     const size_t i = 2 * (size_t)c->trace_used;
     if (i + 1 >= c->trace_events.size()) return;   // pool sized beforehand; beyond it, untraced
-    trace_record(c, c->trace_events[i]);
+    trace_record(s, c->trace_events[i]);
     c->trace_class.push_back(cls);
 }
 
-void trace_end(eor_ctx* c) {
+void trace_end_on(eor_ctx* c, cudaStream_t s) {
     c->launches++;
     if (!c->trace_on) return;
     const size_t i = 2 * (size_t)c->trace_used;
     if (i + 1 >= c->trace_events.size() || c->trace_class.size() != (size_t)c->trace_used + 1) return;
-    trace_record(c, c->trace_events[i + 1]);
+    trace_record(s, c->trace_events[i + 1]);
     c->trace_used++;
 }
+
+void trace_begin(eor_ctx* c, int cls) { trace_begin_on(c, cls, c->stream); }
+void trace_end(eor_ctx* c) { trace_end_on(c, c->stream); }
 
 }  // namespace eor
 
@@ -225,6 +229,9 @@ void eor_destroy(eor_ctx* c) {
                     c->d_cols, c->d_gmeta, c->d_goff, c->d_ncols, c->d_tcA, c->d_tcB, c->d_xq, c->d_err,
                     c->d_a16, c->d_b16, c->d_fscale, c->d_dcell, c->d_fwords, c->d_effp, c->d_ftab};
     for (void* p : bufs) dev_free(c, p);
+    for (cudaEvent_t e : {c->ev_fork, c->ev_pencil[0], c->ev_pencil[1], c->ev_plane[0], c->ev_plane[1]})
+        if (e) cudaEventDestroy(e);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -270,6 +277,16 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
         }
         c->own_stream = true;
     }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking);
+        for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_pencil[0], &c->ev_pencil[1], &c->ev_plane[0], &c->ev_plane[1]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("second stream: ") + cudaGetErrorString(e);
+            eor_destroy(c);
+            return EOR_ECUDA;
+        }
+    }
     c->n = g.n;
     c->nh = g.n / 2 + 1;
     c->n3 = (size_t)g.n * g.n * g.n;
@@ -290,7 +307,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_walkers, W) && alloc_n(c, &c->d_pairs, pairs) &&
               alloc_n(c, &c->d_wtab, (size_t)W * c->max_radii * c->n_m2) &&
               alloc_n(c, &c->d_inter, (size_t)P * G * c->nspec) &&
-              alloc_n(c, &c->d_flags, (size_t)P * c->flag_words) && alloc_n(c, &c->d_psinter, (size_t)P * c->nspec) &&
+              alloc_n(c, &c->d_flags, (size_t)P * c->flag_words) && alloc_n(c, &c->d_psinter, 2 * (size_t)P * c->nspec) &&
               alloc_n(c, &c->d_ps_sum, pairs * B) && alloc_n(c, &c->d_xhi_sum, pairs) &&
               alloc_n(c, &c->d_xhi_mean, pairs) && alloc_n(c, &c->d_chi2, W) && alloc_n(c, &c->d_mock, 2 * Z * B) &&
               alloc_n(c, &c->d_d2, pairs * B) && alloc_n(c, &c->d_kmean, pairs * B) &&
@@ -324,8 +341,8 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
     // split operands with a mass-dependent efficiency (interval flags, partial-ionization tables)
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (c->num_sms < 1) c->num_sms = 1;
-    c->f16 = g.efficiency_model == 0 && eor::basis_f16_fits(c->basis_rank);
-    if (ok && c->f16) {
+    c->f16 = eor::basis_f16_fits(c->basis_rank);
+    if (ok && c->f16) {   // (the TF32 contraction's operands are allocated when that method is chosen)
         c->k16 = eor::basis_f16_kslots(c->basis_rank);
         ok = alloc_n(c, &c->d_a16, eor::basis_f16_a_bytes((long long)c->n3, Z, c->basis_rank)) &&
              alloc_n(c, &c->d_b16, eor::basis_f16_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
@@ -333,11 +350,6 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
              alloc_n(c, &c->d_fwords, pairs * (c->n3 / 32)) &&
              alloc_n(c, &c->d_cols, eor::basis_f16_column_slots(c)) &&
              alloc_n(c, &c->d_gmeta, eor::basis_f16_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
-    } else if (ok && eor::basis_tc_fits(c->basis_rank)) {
-        ok = alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, Z)) &&
-             alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c)) && alloc_n(c, &c->d_xq, pairs) &&
-             alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
-             alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) && alloc_n(c, &c->d_goff, (size_t)W + 1);
     }
     if (ok && g.rsd) ok = alloc_n(c, &c->d_bright, (size_t)Z * c->n3);
     if (ok && g.efficiency_model)
@@ -393,7 +405,8 @@ int eor_init_boxes(eor_ctx* c, const float* delta, int mem) {
         }
     }
     if (c->d_tcA || c->f16) {
-        cudaError_t e = c->f16 ? eor::format_basis_f16(c) : eor::format_basis_tc(c);
+        cudaError_t e = c->f16 ? eor::format_basis_f16(c) : cudaSuccess;
+        if (e == cudaSuccess && c->d_tcA) e = eor::format_basis_tc(c);
         if (e != cudaSuccess) {
             dev_free(c, zwork);
             return cuda_fail(c, e, "tensor-core operands");
@@ -665,7 +678,7 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     uint32_t* flags = nullptr;
     float2* psinter = nullptr;
     if (!alloc_n(c, &inter, (size_t)pairs * group * c->nspec) || !alloc_n(c, &flags, (size_t)pairs * c->flag_words) ||
-        !alloc_n(c, &psinter, (size_t)pairs * c->nspec)) {
+        !alloc_n(c, &psinter, 2 * (size_t)pairs * c->nspec)) {
         dev_free(c, inter);
         dev_free(c, flags);
         dev_free(c, psinter);
@@ -677,7 +690,7 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     c->d_inter = inter;
     c->d_flags = flags;
     c->d_psinter = psinter;
-    c->tune = eor::Tuning{group, pairs, plane_threads, c->tune.method};
+    c->tune = eor::Tuning{group, pairs, plane_threads, c->tune.method, c->tune.ps_split};
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -691,18 +704,22 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     if (!c) return EOR_EINVAL;
     if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
     if (reps < 1 || reps > 1000) return fail(c, EOR_EINVAL, "reps outside 1..1000");
-    struct Cand { int group, pairs, threads; };
+    struct Cand { int group, pairs, threads, split; };
     std::vector<Cand> cands;
     const int groups_direct[] = {4, 8, 16};
     const int pairs_list[] = {4, 8, 16, 32};
     const bool direct = c->tune.method == eor::kMethodDirect;
-    for (int th : {512, 1024}) {
-        if (th == 1024 && c->n != 128) continue;
-        for (int p : pairs_list) {
-            if (direct)
-                for (int gsz : groups_direct) cands.push_back({gsz, p, th});
-            else
-                cands.push_back({c->tune.group, p, th});
+    for (int split : {2, 1}) {
+        if (split == 2 && c->n != 128) continue;   // the cluster form of the spectrum's plane pass
+        for (int th : {512, 1024}) {
+            if (th == 1024 && c->n != 128) continue;
+            if (th == 1024 && split == 2 && !direct) continue;   // the CTA size then changes no kernel of the step
+            for (int p : pairs_list) {
+                if (direct)
+                    for (int gsz : groups_direct) cands.push_back({gsz, p, th, split});
+                else
+                    cands.push_back({c->tune.group, p, th, split});
+            }
         }
     }
     const bool traced = c->trace_on;
@@ -713,7 +730,7 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
         c->trace_on = traced;
         return fail(c, EOR_ECUDA, "autotune events");
     }
-    const Cand start{c->tune.group, c->tune.pairs, c->tune.plane_threads};
+    const Cand start{c->tune.group, c->tune.pairs, c->tune.plane_threads, c->tune.ps_split};
     Cand best = start;
     double best_ms = INFINITY;
     std::vector<double> chi2_host;
@@ -732,6 +749,7 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     int r = EOR_OK;
     for (const Cand& k : cands) {
         if ((r = eor_set_tuning(c, k.group, k.pairs, k.threads)) != EOR_OK) break;
+        c->tune.ps_split = k.split;
         // warm-up: captures this schedule's graph and checks the arguments
         if ((r = eor_likelihood(c, params, n_walkers, mock_d2, sigma, chi2, nullptr, mem)) != EOR_OK) break;
         cudaEventRecord(e0, c->stream);
@@ -758,9 +776,11 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     if (r != EOR_OK) {
         const std::string msg = c->err;
         eor_set_tuning(c, start.group, start.pairs, start.threads);
+        c->tune.ps_split = start.split;
         return fail(c, r, "autotune: " + msg);
     }
     if ((r = eor_set_tuning(c, best.group, best.pairs, best.threads)) != EOR_OK) return r;
+    c->tune.ps_split = best.split;
     if (group) *group = best.group;
     if (pairs) *pairs = best.pairs;
     if (plane_threads) *plane_threads = best.threads;
@@ -768,17 +788,65 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     return EOR_OK;
 }
 
-int eor_set_method(eor_ctx* c, int method) {
+int eor_set_ps_split(eor_ctx* c, int split) {
     if (!c) return EOR_EINVAL;
-    if (method != EOR_METHOD_BASIS && method != EOR_METHOD_DIRECT && method != EOR_METHOD_BASIS_SIMT)
-        return fail(c, EOR_EINVAL, "unknown method");
-    CK(cudaStreamSynchronize(c->stream), "method");
-    c->tune.method = method == EOR_METHOD_BASIS ? eor::kMethodBasis
-                     : method == EOR_METHOD_DIRECT ? eor::kMethodDirect : eor::kMethodBasisSimt;
+    if (split != 1 && split != 2) return fail(c, EOR_EINVAL, "ps_split must be 1 or 2");
+    if (split == 2 && c->n != 128) return fail(c, EOR_ENOTSUP, "the two-CTA plane pass serves n = 128 only");
+    CK(cudaStreamSynchronize(c->stream), "ps split");
+    c->tune.ps_split = split;
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
         c->graph_walkers = -1;
+    }
+    return EOR_OK;
+}
+
+int eor_get_tuning(const eor_ctx* c, int* group, int* pairs, int* plane_threads, int* ps_split) {
+    if (!c) return EOR_EINVAL;
+    if (group) *group = c->tune.group;
+    if (pairs) *pairs = c->tune.pairs;
+    if (plane_threads) *plane_threads = c->tune.plane_threads;
+    if (ps_split) *ps_split = c->n == 128 ? c->tune.ps_split : 1;
+    return EOR_OK;
+}
+
+int eor_set_method(eor_ctx* c, int method) {
+    if (!c) return EOR_EINVAL;
+    if (method != EOR_METHOD_BASIS && method != EOR_METHOD_DIRECT && method != EOR_METHOD_BASIS_SIMT &&
+        method != EOR_METHOD_BASIS_TF32)
+        return fail(c, EOR_EINVAL, "unknown method");
+    CK(cudaStreamSynchronize(c->stream), "method");
+    if (method == EOR_METHOD_BASIS_TF32 && !c->d_tcA && eor::basis_tc_fits(c->basis_rank)) {
+        // the TF32 contraction's operands, formatted now if the boxes are already in place
+        if (!alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, c->cfg.n_z)) ||
+            !alloc_n(c, &c->d_tcB, eor::basis_tc_b_bytes(c))) {
+            dev_free(c, c->d_tcA);
+            c->d_tcA = nullptr;
+            return fail(c, EOR_ENOMEM, "TF32 contraction operands");
+        }
+        if (!c->d_xq && !alloc_n(c, &c->d_xq, (size_t)c->cfg.max_walkers * c->cfg.n_z))
+            return fail(c, EOR_ENOMEM, "TF32 contraction sums");
+        if (!c->d_cols &&
+            !(alloc_n(c, &c->d_cols, eor::basis_tc_column_slots(c)) &&
+              alloc_n(c, &c->d_gmeta, eor::basis_tc_column_slots(c) / 32) &&
+              alloc_n(c, &c->d_goff, (size_t)c->cfg.max_walkers + 1)))
+            return fail(c, EOR_ENOMEM, "TF32 contraction columns");
+        if (c->stage >= 1) CK(eor::format_basis_tc(c), "TF32 contraction operands");
+    }
+    c->tune.method = method == EOR_METHOD_BASIS        ? eor::kMethodBasis
+                     : method == EOR_METHOD_DIRECT     ? eor::kMethodDirect
+                     : method == EOR_METHOD_BASIS_SIMT ? eor::kMethodBasisSimt
+                                                       : eor::kMethodBasisTf32;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_walkers = -1;
+    }
+    if (c->stage >= 2) {   // the walker tables of the chosen contraction (column layout)
+        CK(eor::build_walker_tables(c, c->n_walkers), "walker tables");
+        CK(cudaStreamSynchronize(c->stream), "walker tables");
+        if (c->stage > 2) c->stage = 2;
     }
     return EOR_OK;
 }
@@ -798,7 +866,7 @@ int eor_contraction_info(const eor_ctx* c, int* kind, int* k_slots) {
     } else if (c->tune.method == eor::kMethodBasis && c->f16) {
         *kind = EOR_CONTRACT_FP16;
         *k_slots = c->k16;
-    } else if (c->tune.method == eor::kMethodBasis && c->d_tcA) {
+    } else if (c->tune.method == eor::kMethodBasisTf32 && c->d_tcA) {
         *kind = EOR_CONTRACT_TF32;
         *k_slots = (c->basis_rank + 1 + 7) / 8 * 8;
     } else {

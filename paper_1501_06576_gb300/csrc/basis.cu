@@ -523,7 +523,7 @@ cudaError_t launch_kb_any(eor_ctx* c, const BasisArgs& a, size_t smem) { EOR_KB_
 cudaError_t launch_basis_ionize(eor_ctx* c, float* xhi_out) {
     const int n_z = c->cfg.n_z;
     if (c->tune.method == kMethodBasis && c->f16) return launch_basis_ionize_f16(c);   // x_HI: pencil pass
-    if (c->tune.method == kMethodBasis && c->d_tcA) return launch_basis_ionize_tc(c, xhi_out);
+    if (c->tune.method == kMethodBasisTf32 && c->d_tcA) return launch_basis_ionize_tc(c, xhi_out);
     BasisArgs a{c->d_F, c->d_coef, c->d_pairs, brightness_base(c), c->d_dtb, xhi_out, c->d_xpart, pop_tables(c), c->n_walkers, n_z,
                 c->max_radii, (long long)c->n3, (float)c->cfg.delta_c};
     const size_t smem = basis_ionize_smem(c->kb, c->max_radii);

@@ -44,6 +44,24 @@ struct PairInfo {
     float delta_hi[kMaxRadii];     // ... and delta_R <= delta_hi (+inf except for a falling efficiency)
 };
 
+// erfc(x) for x >= 0 from the Chebyshev fit of Numerical Recipes (Press et al. 1992, Sec. 6.2,
+// "erfcc"; fractional error below 1.2e-7 everywhere): t = 1 / (1 + x/2) and
+// erfc(x) = t exp(-x^2 + P(t)) with P a degree-9 polynomial. Branch-free.
+__device__ __forceinline__ float erfc_cheb(float x) {
+    const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    return t * expf(fmaf(-x, x, p));
+}
+
 // Efficiency-weighted collapsed fraction at nu = delta_c - delta_R from a pair's table
 // (kFTab values at nu = i / inv_h; nu <= 0: the collapsed-region value in entry 0), by
 // Catmull-Rom cubic interpolation (end intervals use a linearly extrapolated neighbour),
@@ -87,13 +105,14 @@ enum KernelClass : int {
     kKClasses = 8
 };
 
-enum Method : int { kMethodBasis = 0, kMethodDirect = 1, kMethodBasisSimt = 2 };
+enum Method : int { kMethodBasis = 0, kMethodDirect = 1, kMethodBasisSimt = 2, kMethodBasisTf32 = 3 };
 
 struct Tuning {
     int group;          // radii per pencil launch (G)
     int pairs;          // (walker, redshift) pairs in flight (P)
     int plane_threads;  // CTA size of the 128^3 plane kernels (512 or 1024)
-    int method;         // kMethodBasis or kMethodDirect
+    int method;         // kMethodBasis, kMethodDirect, kMethodBasisSimt or kMethodBasisTf32
+    int ps_split;       // CTAs per 128 x 128 plane of the power spectrum: 1, or 2 (a cluster)
 };
 
 }  // namespace eor
@@ -102,11 +121,14 @@ struct eor_ctx {
     eor_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the power spectrum's plane passes run on stream2, overlapping the next batch's pencil pass
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_pencil[2] = {nullptr, nullptr}, ev_plane[2] = {nullptr, nullptr};
     int device = 0;
     int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
     size_t n3 = 0, nspec = 0;
     eor::CosmoParams cosmo{};
-    eor::Tuning tune{8, 16, 512, eor::kMethodBasis};
+    eor::Tuning tune{8, 16, 512, eor::kMethodBasis, 2};
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]
@@ -128,7 +150,7 @@ struct eor_ctx {
     float* d_wtab = nullptr;         // [max_walkers][max_radii][n_m2]
     float2* d_inter = nullptr;       // [G*P][nspec]
     uint32_t* d_flags = nullptr;     // [P][flag words per pair]
-    float2* d_psinter = nullptr;     // [P][nspec]
+    float2* d_psinter = nullptr;     // [2][P][nspec] (two halves: pencil and plane passes overlap)
     double* d_ps_sum = nullptr;      // [max_walkers][n_z][n_bins]
     double* d_xhi_sum = nullptr;     // [max_walkers][n_z]
     double* d_chi2 = nullptr;        // [max_walkers]
@@ -205,6 +227,8 @@ namespace eor {
 // api.cu (tracing)
 void trace_begin(eor_ctx* c, int cls);
 void trace_end(eor_ctx* c);
+void trace_begin_on(eor_ctx* c, int cls, cudaStream_t s);
+void trace_end_on(eor_ctx* c, cudaStream_t s);
 size_t estimate_launches(const eor_ctx* c);
 
 // tables.cu

@@ -883,6 +883,7 @@ struct BrightArgs {
     float* xhi_out;             // optional [pair][n3]
     unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
     float2* dst;                // [slot][nh][n][n]
+    const float* ftab;          // [pair][kFTab] with a mass-dependent efficiency, else nullptr
     int pair0, n_pairs;
     float delta_c;
 };
@@ -890,7 +891,9 @@ struct BrightArgs {
 // The flag contraction's pencil pass, for pairs pair0 .. pair0 + gridDim.y - 1: per cell of
 // the tile's pencils x_HI = 0 where a radius above R_cell flagged it (Eq. 1), else
 // 1 - min(1, zeta f_coll(R_cell)) with f_coll = erfc((delta_c - delta_Rcell) / sqrt(2 s^2))
-// (1 where delta_Rcell >= delta_c; x_HI = 1 where s^2 <= 0) (Sec. 2.1); delta T_b =
+// (1 where delta_Rcell >= delta_c; x_HI = 1 where s^2 <= 0) (Sec. 2.1), or with a
+// mass-dependent efficiency 1 - min(1, F) from the pair's table of the efficiency-weighted
+// collapsed fraction F at nu = delta_c - delta_Rcell (staged in shared memory); delta T_b =
 // T0 x_HI (1 + delta) (Sec. 2.2), never stored; then its R2C along z into dst. The x_HI sum
 // of the pair is exact: fixed point 2^-23, integer warp sums and 64-bit atomics.
 template <int N>
@@ -901,6 +904,7 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_brightness(Bright
     constexpr int PER = (V + P::THREADS - 1) / P::THREADS;
     extern __shared__ __align__(16) float2 smem[];
     const PencilSmem<N> s(smem);
+    float* ftab = reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + Pencil<N>::SMEM);   // [kFTab]
     const int tile = blockIdx.x, slot = blockIdx.y, pair = a.pair0 + slot;
     if (pair >= a.n_pairs) return;
     const PairInfo& pi = a.pairs[pair];
@@ -908,6 +912,10 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_brightness(Bright
     const int x = tile / (N / P::TY), y0 = (tile % (N / P::TY)) * P::TY;
     const size_t n3 = (size_t)N * N * N, cell0 = ((size_t)x * N + y0) * N;
     fill_twiddles<N>(s.tw);
+    if (a.ftab) {
+        for (int e = t; e < kFTab; e += P::THREADS) ftab[e] = __ldg(a.ftab + (size_t)pair * kFTab + e);
+        __syncthreads();
+    }
     const float4* d4 = reinterpret_cast<const float4*>(a.delta + (size_t)pi.zi * n3 + cell0);
     const float4* c4 = reinterpret_cast<const float4*>(a.dcell + (size_t)pi.zi * n3 + cell0);
     const uint32_t* fw = a.fwords + (size_t)pair * (n3 / 32) + cell0 / 32;
@@ -932,10 +940,17 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_brightness(Bright
         float xh[4], tb[4];
 #pragma unroll
         for (int h = 0; h < 4; h++) {
+            const bool flagged = (bits[k] >> h) & 1u;
             const float nu = a.delta_c - dc[h];
-            const float f = nu <= 0.0f ? 1.0f : erfcf(nu * inv);
-            float v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
-            v = ((bits[k] >> h) & 1u) ? 0.0f : v;
+            float v = 0.0f;
+            if (!flagged) {   // (ionized regions are coherent: a warp's 128 cells are one z-pencil)
+                if (a.ftab) {
+                    v = 1.0f - fminf(1.0f, pop_table_f(ftab, nu, pi.f_inv_h));
+                } else {
+                    const float f = nu <= 0.0f ? 1.0f : erfc_cheb(nu * inv);
+                    v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+                }
+            }
             xh[h] = v;
             tb[h] = t0 * v * (1.0f + dd[h]);
             xq += __float2int_rn(v * 8388608.0f);
@@ -1091,28 +1106,28 @@ cudaError_t plane_filter_inverse(eor_ctx* c, const Pass1Args& a1, int P, int cls
     return cudaGetLastError();
 }
 
-// Shell sums of `planes` kz planes of P slots of z-transformed boxes, as k_plane_ps.
+// Shell sums of `planes` kz planes of P slots of z-transformed boxes, as k_plane_ps, on stream s.
 template <int N, int T>
-cudaError_t plane_ps(eor_ctx* c, const PSArgs& ap, int planes, int P) {
+cudaError_t plane_ps(eor_ctx* c, const PSArgs& ap, int planes, int P, cudaStream_t s) {
     if constexpr (N == kL) {
         LineArgs la{};
         la.src = ap.ps_inter; la.dst = const_cast<float2*>(ap.ps_inter); la.G = 1;
         la.pairs = ap.pairs; la.pair0 = ap.pair0; la.n_pairs = ap.n_pairs;
         la.bin_of_m2 = ap.bin_of_m2; la.ps_sum = ap.ps_sum; la.n_bins = ap.n_bins; la.kf3 = ap.kf3;
-        trace_begin(c, kKPsPlane);
-        k_lines_rows<-1><<<dim3(planes * 16, 1, P), kLThreads, kLSmemRows, c->stream>>>(la);
-        trace_end(c);
-        trace_begin(c, kKPsPlane);
-        k_lines_cols<-1, kLinePs><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, c->stream>>>(la);
-        trace_end(c);
-    } else if constexpr (N == 128) {
-        trace_begin(c, kKPsPlane);
-        k_plane_ps2<<<dim3(2 * planes, P), kPs2Threads, kPs2Smem, c->stream>>>(ap);
-        trace_end(c);
+        trace_begin_on(c, kKPsPlane, s);
+        k_lines_rows<-1><<<dim3(planes * 16, 1, P), kLThreads, kLSmemRows, s>>>(la);
+        trace_end_on(c, s);
+        trace_begin_on(c, kKPsPlane, s);
+        k_lines_cols<-1, kLinePs><<<dim3(planes * 16, 1, P), kLThreads, kLSmem, s>>>(la);
+        trace_end_on(c, s);
+    } else if (N == 128 && c->tune.ps_split == 2) {
+        trace_begin_on(c, kKPsPlane, s);
+        k_plane_ps2<<<dim3(2 * planes, P), kPs2Threads, kPs2Smem, s>>>(ap);
+        trace_end_on(c, s);
     } else {
-        trace_begin(c, kKPsPlane);
-        k_plane_ps<N, T><<<dim3(planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, c->stream>>>(ap);
-        trace_end(c);
+        trace_begin_on(c, kKPsPlane, s);
+        k_plane_ps<N, T><<<dim3(planes, P), Plane<N, T>::THREADS, Plane<N, T>::SMEM_PS, s>>>(ap);
+        trace_end_on(c, s);
     }
     return cudaGetLastError();
 }
@@ -1137,7 +1152,7 @@ cudaError_t prepare_n() {
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_forward_batch<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
-    if ((e = set_smem(k_pencil_brightness<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_pencil_brightness<N>, Pencil<N>::SMEM + kFTab * sizeof(float))) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1151,22 +1166,37 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
     const bool flags = c->f16 && c->tune.method == kMethodBasis;   // the flag contraction's pencil pass
     if (flags) cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * n_pairs, c->stream);
     const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
-    for (int pair0 = 0; pair0 < n_pairs; pair0 += P) {
+    // batches of P pairs: the pencil pass of batch b (c->stream) fills half b % 2 of the
+    // intermediate buffer; the plane pass of batch b (stream2) reads it while the pencil pass of
+    // batch b + 1 fills the other half; batch b + 2 waits for the plane pass of batch b
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    for (int pair0 = 0; pair0 < n_pairs; pair0 += P, b++) {
+        const int h = b & 1;
+        float2* half = c->d_psinter + (size_t)h * P * c->nspec;
+        if (b >= 2 && (e = cudaStreamWaitEvent(c->stream, c->ev_plane[h], 0)) != cudaSuccess) return e;
         trace_begin(c, kKForward);
         if (flags) {
-            BrightArgs ba{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, c->d_psinter,
-                          pair0, n_pairs, (float)c->cfg.delta_c};
-            k_pencil_brightness<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(ba);
+            BrightArgs ba{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, half,
+                          pop_tables(c), pair0, n_pairs, (float)c->cfg.delta_c};
+            k_pencil_brightness<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS,
+                                     Pencil<N>::SMEM + (ba.ftab ? kFTab * sizeof(float) : 0), c->stream>>>(ba);
         } else {
             k_pencil_forward_batch<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(
-                c->d_dtb, c->d_psinter, pair0, n_pairs);
+                c->d_dtb, half, pair0, n_pairs);
         }
         trace_end(c);
-        PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
-                  kf * kf * kf};
-        cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P);
-        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_pencil[h], c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->stream2, c->ev_pencil[h], 0)) != cudaSuccess) return e;
+        PSArgs ap{half, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins, kf * kf * kf};
+        if ((e = plane_ps<N, T>(c, ap, c->ps_planes, P, c->stream2)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_plane[h], c->stream2)) != cudaSuccess) return e;
     }
+    // join: the last plane pass of each half
+    for (int h = 0; h < 2 && h < b; h++)
+        if ((e = cudaStreamWaitEvent(c->stream, c->ev_plane[(b - 1 - h) & 1], 0)) != cudaSuccess) return e;
     if (flags) {
         trace_begin(c, kKFinish);
         launch_xq_finish(c->d_xq, n_pairs, c->d_xhi_sum, c->stream);
@@ -1208,7 +1238,7 @@ cudaError_t ionization_n(eor_ctx* c, float* xhi_out) {
         }
         PSArgs ap{c->d_psinter, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins,
                   kf * kf * kf};
-        cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P);
+        cudaError_t e = plane_ps<N, T>(c, ap, c->ps_planes, P, c->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1291,7 +1321,7 @@ cudaError_t box_power_spectrum_n(eor_ctx* c, const float* box) {
     k_pencil_forward<N><<<Pencil<N>::TILES, Pencil<N>::THREADS, Pencil<N>::SMEM, c->stream>>>(box, c->d_psinter);
     trace_end(c);
     PSArgs ap{c->d_psinter, c->d_diag_pair, c->d_bin_of_m2, c->d_diag_ps, 0, 1, nb, kf * kf * kf};
-    if ((e = plane_ps<N, T>(c, ap, NH, 1)) != cudaSuccess) return e;
+    if ((e = plane_ps<N, T>(c, ap, NH, 1, c->stream)) != cudaSuccess) return e;
     const double dx = c->cfg.box_mpc / c->n;
     const double vol = c->cfg.box_mpc * c->cfg.box_mpc * c->cfg.box_mpc;
     const double scale = dx * dx * dx * dx * dx * dx / (2.0 * kPi * kPi * vol);
@@ -1536,7 +1566,7 @@ bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 ||
 cudaError_t launch_forward_spectrum(eor_ctx* c, int zi) { EOR_DISPATCH(c, forward_spectrum_n, c, zi) }
 
 cudaError_t launch_ionization(eor_ctx* c, float* xhi_out) {
-    if (c->tune.method == kMethodBasis || c->tune.method == kMethodBasisSimt) {
+    if (c->tune.method != kMethodDirect) {
         cudaError_t e = launch_basis_ionize(c, xhi_out);
         if (e != cudaSuccess) return e;
         return launch_ps_from_boxes(c, xhi_out);

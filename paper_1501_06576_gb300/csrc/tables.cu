@@ -653,17 +653,19 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
         k_pop_tables<<<(unsigned)((tasks + kPopWarps - 1) / kPopWarps), 32 * kPopWarps, 0, c->stream>>>(pa);
         trace_end(c);
     }
-    dim3 grid((c->n_m2 + 255) / 256, n_walkers * c->max_radii);
-    trace_begin(c, kKTables);
-    k_window_tables<<<grid, 256, 0, c->stream>>>(c->d_walkers, c->max_radii, c->n_m2,
-                                                  (float)(2.0 * kPi / g.box_mpc), c->d_wtab);
-    trace_end(c);
+    if (c->tune.method == kMethodDirect) {   // the per-radius windows only the direct method reads
+        dim3 grid((c->n_m2 + 255) / 256, n_walkers * c->max_radii);
+        trace_begin(c, kKTables);
+        k_window_tables<<<grid, 256, 0, c->stream>>>(c->d_walkers, c->max_radii, c->n_m2,
+                                                      (float)(2.0 * kPi / g.box_mpc), c->d_wtab);
+        trace_end(c);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = build_walker_coefs(c, n_walkers)) != cudaSuccess) return e;
+    if (c->tune.method == kMethodBasisTf32 && c->d_tcB) return build_columns(c, n_walkers);
     if (c->f16) return build_columns_f16(c, n_walkers);
-    if (!c->d_tcB) return cudaSuccess;
-    return build_columns(c, n_walkers);
+    return cudaSuccess;
 }
 
 cudaError_t launch_window_table(eor_ctx* c, double r, float* wtab) {

@@ -123,15 +123,27 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // One test of the mbarrier phase `parity`; the thread may be suspended for at most about
-// kSuspendNs while the phase is incomplete (explicit suspend-time hint).
-constexpr uint32_t kSuspendNs = 1000;
+// kSuspendNs while the phase is incomplete (explicit suspend-time hint; 0: the hardware's own
+// time limit).
+#ifndef EOR_MBAR_SUSPEND_NS
+#define EOR_MBAR_SUSPEND_NS 1000
+#endif
+constexpr uint32_t kSuspendNs = EOR_MBAR_SUSPEND_NS;
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
-        : "memory");
+    if constexpr (kSuspendNs > 0) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+    }
     return done != 0;
 }
 

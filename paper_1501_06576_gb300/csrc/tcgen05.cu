@@ -223,24 +223,6 @@ __device__ __forceinline__ uint32_t and31(const float (&v)[32]) {
     return (m[0] & m[1] & m[2]) & (m[3] & m[4] & m[5]) & (m[6] & m[7]);
 }
 
-// erfc(x) for x >= 0 from the Chebyshev fit of Numerical Recipes (Press et al. 1992, Sec. 6.2,
-// "erfcc"; fractional error below 1.2e-7 everywhere): t = 1 / (1 + x/2) and
-// erfc(x) = t exp(-x^2 + P(t)) with P a degree-9 polynomial. Branch-free.
-__device__ __forceinline__ float erfc_cheb(float x) {
-    const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
-    float p = 0.17087277f;
-    p = fmaf(p, t, -0.82215223f);
-    p = fmaf(p, t, 1.48851587f);
-    p = fmaf(p, t, -1.13520398f);
-    p = fmaf(p, t, 0.27886807f);
-    p = fmaf(p, t, -0.18628806f);
-    p = fmaf(p, t, 0.09678418f);
-    p = fmaf(p, t, 0.37409196f);
-    p = fmaf(p, t, 1.00002368f);
-    p = fmaf(p, t, -1.26551223f);
-    return t * expf(fmaf(-x, x, p));
-}
-
 struct TcArgs {
     const unsigned char* A;     // [n_z][cta][kABytes]
     const unsigned char* B;     // [n_z][chunk][kChunkBytes]
@@ -662,13 +644,23 @@ constexpr int kFN = 256;                        // coefficient columns per chunk
 constexpr int kFKMax = 96;                      // FP16 K slots at most (six MMA steps of 16)
 constexpr int kFStages = 3;                     // coefficient chunks in flight
 constexpr int kFGroups = kFN / kGroup;          // walker groups per chunk
-constexpr uint32_t kFMetaBytes = kFGroups * 16;
+constexpr uint32_t kFRecBytes = kFGroups * 16;  // group records
+constexpr uint32_t kFWidthBytes = kFN * 4;      // per column t (delta_hi - delta_crit) (mass-dependent efficiency)
+constexpr uint32_t f16_meta_bytes(bool pops) { return kFRecBytes + (pops ? kFWidthBytes : 0u); }
 constexpr int kFEpiWarps = 16;                  // four per tensor-memory lane quarter
+#ifndef EOR_F16_EPI_SETS
+#define EOR_F16_EPI_SETS 2
+#endif
+constexpr int kFEpiSets = EOR_F16_EPI_SETS;     // epilogue warp sets, alternating chunks (1 or 2)
+constexpr int kFSetThreads = 32 * kFEpiWarps / kFEpiSets;   // threads of one set
+constexpr int kFRounds = 2 * kFEpiSets / 2;     // 64-column rounds of a warp per chunk
 constexpr int kFThreads = 128 + 32 * kFEpiWarps;
 constexpr uint32_t kFTmemCols = 2 * kFN;        // two accumulator buffers
 constexpr float kFScale = 16384.0f;             // 2^14
 static_assert(kFTmemCols <= 512, "tensor memory");
-static_assert(kFN == 8 * kGroup && kFEpiWarps == 16, "epilogue: warp (q, p) reads groups 2p, 2p + 1 of lane quarter q");
+static_assert(kFEpiSets == 1 || kFEpiSets == 2, "one set, or two sets each on its own accumulator buffer");
+static_assert(kFN == 8 * kGroup && kFEpiWarps == 16,
+              "epilogue: a set's warp (q, p) reads 64 kFRounds columns of lane quarter q, 64 per round");
 
 __host__ __device__ constexpr int f16_kslots(int rank) { return (3 * (rank + 1) + 15) / 16 * 16; }
 __host__ __device__ constexpr uint32_t f16_sbo(int k) { return (uint32_t)(k / 8) * 128u; }
@@ -744,27 +736,31 @@ __global__ void k_format_a16(const float* F, int kb, int rank, long long n3, int
 __global__ void __launch_bounds__(kFN) k_format_b16(const int* cols, const int* gmeta, const int* ncols,
                                                     const float* coef, const PairInfo* pairs, int kb, int rank,
                                                     int max_radii, int n_z, int chunks_per_z, const float* fscale,
-                                                    int kslots, unsigned char* out) {
+                                                    int kslots, int pops, unsigned char* out) {
     const int row = threadIdx.x, zi = blockIdx.y, slot = blockIdx.x * kFN + row;
     const int nc = *ncols, ls = rank + 1;
     const uint32_t sbo = f16_sbo(kslots);
     const size_t bbytes = (size_t)kFN * kslots * 2;
-    unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * (bbytes + kFMetaBytes);
+    unsigned char* chunk = out + ((size_t)zi * chunks_per_z + blockIdx.x) * (bbytes + f16_meta_bytes(pops != 0));
     float v[kBasisMax + 1];
     const int cw = slot < nc ? cols[slot] : -1;
-    float mx = 0.0f;
+    float mx = 0.0f, width = INFINITY;
     if (cw >= 0) {
         const int w = cw >> 8, j = cw & 255;
         const float* src = coef + ((size_t)w * max_radii + j) * kb;
-        const float dcrit = pairs[(size_t)w * n_z + zi].delta_crit[j];
+        const PairInfo& pi = pairs[(size_t)w * n_z + zi];
+        const float dcrit = pi.delta_crit[j];
         for (int b = 0; b < rank; b++) v[b] = src[b] * (fscale[zi * 32 + b] / kFScale);
         v[rank] = -(isfinite(dcrit) ? dcrit : kNever) / kFScale;
+        if (isfinite(dcrit) && isfinite(pi.delta_hi[j])) width = pi.delta_hi[j] - dcrit;
     } else {
         for (int b = 0; b < rank; b++) v[b] = 0.0f;
         v[rank] = -1.0f;
     }
     for (int b = 0; b <= rank; b++) mx = fmaxf(mx, fabsf(v[b]));
     const float t = mx > 0.0f ? exp2f((float)(13 - ilogbf(mx))) : 1.0f;   // mx t in [2^13, 2^14)
+    // the flag interval delta_crit <= delta_R <= delta_hi in the units of D = t (delta_R - delta_crit)
+    if (pops) reinterpret_cast<float*>(chunk + bbytes + kFRecBytes)[row] = width * t;
     for (int q = 0; q < kslots / 8; q++) {
         __align__(16) __half h[8];
 #pragma unroll
@@ -802,12 +798,13 @@ __device__ __forceinline__ uint32_t and32(const float (&v)[32]) {
 
 struct F16Args {
     const unsigned char* A;     // [n_z][tiles_per_z][a_bytes]
-    const unsigned char* B;     // [n_z][chunks_per_z][b_bytes + kFMetaBytes]
+    const unsigned char* B;     // [n_z][chunks_per_z][b_bytes + meta_bytes]
     const int* ncols;           // [1] number of columns
     uint32_t* flags;            // [pair][n3 / 32] Eq. 1 flags above R_cell, bit = cell % 32
     int* err;
     int n_z, chunks_per_z, tiles_per_z, ksteps;
     uint32_t a_bytes, b_bytes, sbo;
+    uint32_t meta_bytes;        // group records (and with POPS the columns' interval widths)
     long long n3;
     int withhold;               // test-only failure injection (see TcArgs), -1 off
     uint64_t free_wait_ns;
@@ -824,15 +821,17 @@ struct F16Args {
 // walkers of groups 2p, 2p + 1, stores the Eq. 1 flags of its 32 cells as one word (a walker's
 // flag: the AND of the sign bits of its columns is clear). x_HI, delta T_b and the power
 // spectrum follow in the pencil pass. Chunk counters g run over all chunks of the CTA's
-// tiles. Every wait is bounded in GPU time; on a timeout the CTA records where (err[1]:
-// role, barrier, g), stops, waits for its MMAs and copies in flight and frees its tensor
-// memory.
+// tiles. POPS (a mass-dependent efficiency): a column flags where 0 <= D <= t (delta_hi -
+// delta_crit), the width staged with the group records. Every wait is bounded in GPU time;
+// on a timeout the CTA records where (err[1]: role, barrier, g), stops, waits for its MMAs
+// and copies in flight and frees its tensor memory.
+template <bool POPS>
 __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* As = sm;                                    // [2][a_bytes]
     unsigned char* Bs = As + 2 * a.a_bytes;                    // [kFStages][b_bytes]
-    unsigned char* Ms = Bs + kFStages * a.b_bytes;             // [kFStages][kFMetaBytes]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFStages * kFMetaBytes);
+    unsigned char* Ms = Bs + kFStages * a.b_bytes;             // [kFStages][meta_bytes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFStages * a.meta_bytes);
     uint64_t* barA = bars;                   // [2] A stage landed
     uint64_t* barAe = barA + 2;              // [2] A stage free (MMAs of its tile done)
     uint64_t* barB = barAe + 2;              // [kFStages] chunk (coefficients + meta) landed
@@ -857,12 +856,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             tc::mbar_init(barA + s, 1);
             tc::mbar_init(barAe + s, 1);
             tc::mbar_init(barD + s, 1);
-            tc::mbar_init(barE + s, 32 * kFEpiWarps);
+            tc::mbar_init(barE + s, kFSetThreads);
         }
         for (int s = 0; s < kFStages; s++) {
             tc::mbar_init(barB + s, 1);
             tc::mbar_init(barBe + s, 1);
-            tc::mbar_init(barMe + s, 32 * kFEpiWarps);
+            tc::mbar_init(barMe + s, kFSetThreads);
         }
         tc::mbar_init(barF, 1);
         *abort = 0;
@@ -895,7 +894,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
         for (int it = 0; it < my_tiles && ok; it++) {
             const int tile = (int)blockIdx.x + it * (int)gridDim.x;
             const int zi = tile / a.tiles_per_z;
-            const unsigned char* Bz = a.B + (size_t)zi * a.chunks_per_z * (a.b_bytes + kFMetaBytes);
+            const unsigned char* Bz = a.B + (size_t)zi * a.chunks_per_z * (a.b_bytes + a.meta_bytes);
             for (int c = 0; c < nch; c++) {
                 // the next tile's A operands half-way through this tile's chunks
                 if (c == nch / 2 && it + 1 < my_tiles && !(ok = issue_a(it + 1))) break;
@@ -907,10 +906,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                     ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kWaitNs, abort);
                     if (!ok) { record_timeout(a.err, 1, 5, g); break; }
                 }
-                const unsigned char* src = Bz + (size_t)c * (a.b_bytes + kFMetaBytes);
-                tc::mbar_expect_tx(barB + st, a.b_bytes + kFMetaBytes);
+                const unsigned char* src = Bz + (size_t)c * (a.b_bytes + a.meta_bytes);
+                tc::mbar_expect_tx(barB + st, a.b_bytes + a.meta_bytes);
                 tc::bulk_g2s(Bs + (size_t)st * a.b_bytes, src, a.b_bytes, barB + st);
-                tc::bulk_g2s(Ms + st * kFMetaBytes, src + a.b_bytes, kFMetaBytes, barB + st);
+                tc::bulk_g2s(Ms + st * a.meta_bytes, src + a.b_bytes, a.meta_bytes, barB + st);
                 owedB[st] = (int)(use & 1u);
             }
         }
@@ -947,15 +946,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
         }
         if (!ok) *abort = 1;
     } else if (warp >= 4 && work) {
-        // ---------------- epilogue warps
-        const int e = warp - 4, q = warp & 3, p = e >> 2;
+        // ---------------- epilogue warps: set `set` takes the chunks g = set (mod kFEpiSets);
+        // its warp (q = lane quarter, p) reads columns (64 p + 64 r) (r < kFRounds) of the buffer
+        const int e = warp - 4, q = warp & 3, set = e / (kFEpiWarps / kFEpiSets), p = (e % (kFEpiWarps / kFEpiSets)) >> 2;
         const long long words = a.n3 / 32;
         bool ok = true;
         for (int it = 0; it < my_tiles && ok; it++) {
             const int tile = (int)blockIdx.x + it * (int)gridDim.x;
             const int zi = tile / a.tiles_per_z;
             const long long word = (long long)(tile % a.tiles_per_z) * (kFM / 32) + q;   // cells 32 word .. + 31
-            for (int c = 0; c < nch; c++) {
+            // the first chunk of this tile that the set takes (chunk counters continue across tiles)
+            int c = (set - (it * nch) % kFEpiSets + kFEpiSets) % kFEpiSets;
+            for (; c < nch; c += kFEpiSets) {
                 const int g = it * nch + c, st = g % kFStages, tb = g & 1;
                 const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(g >> 1) & 1u, kWaitNs, abort);
                 const bool okB = okD && tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / kFStages) & 1u, kWaitNs, abort);
@@ -966,22 +968,45 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                     break;
                 }
                 tc::fence_after_sync();
-                float v0[32], v1[32];
-                tc::tmem_ld32x2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kFN + p * 2 * kGroup), v0, v1);
-                tc::fence_before_sync();
-                if (g != a.withhold) tc::mbar_arrive(barE + tb);   // accumulators in registers: buffer free
-                const int4* gm = reinterpret_cast<const int4*>(Ms + st * kFMetaBytes) + 2 * p;
-                const int m0 = gm[0].x, m1 = gm[1].x;
-                tc::mbar_arrive(barMe + st);
-                // Eq. 1 flags: AND of the sign bits over the walker's radii above R_cell; group
-                // 2p + 1 continues the walker of group 2p when it is not a first group
-                const uint32_t a0 = and32(v0), a1 = and32(v1);
-                const uint32_t w0 = __ballot_sync(0xffffffffu, (a0 >> 31) == 0u);
-                const uint32_t w1 = __ballot_sync(0xffffffffu, (((m1 & 2) == 0 ? (a0 & a1) : a1) >> 31) == 0u);
-                if (lane == 0) {
-                    if (m0 >= 0 && (m0 & 1)) a.flags[((size_t)(m0 >> 2) * a.n_z + zi) * words + word] = w0;
-                    if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
+#pragma unroll 1
+                for (int r = 0; r < kFRounds; r++) {
+                    const int col = p * 64 * kFRounds + r * 64;   // first column of this round
+                    float v0[32], v1[32];
+                    tc::tmem_ld32x2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kFN + col), v0, v1);
+                    if (r == kFRounds - 1) {
+                        tc::fence_before_sync();
+                        if (g != a.withhold) tc::mbar_arrive(barE + tb);   // accumulators read: buffer free
+                    }
+                    const int4* gm = reinterpret_cast<const int4*>(Ms + st * a.meta_bytes) + col / kGroup;
+                    const int m0 = gm[0].x, m1 = gm[1].x;
+                    if constexpr (POPS) {
+                        // a column does not flag iff D < 0 or D > width: the sign bit of D | (width - D)
+                        // (+inf for an infinite width), then the same AND of sign bits
+                        const float4* wd = reinterpret_cast<const float4*>(Ms + st * a.meta_bytes + kFRecBytes) + col / 4;
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const float4 wa = wd[k], wb = wd[8 + k];
+                            const float xa[4] = {wa.x, wa.y, wa.z, wa.w}, xb[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                const int i = 4 * k + h;
+                                v0[i] = __uint_as_float(__float_as_uint(v0[i]) | __float_as_uint(xa[h] - v0[i]));
+                                v1[i] = __uint_as_float(__float_as_uint(v1[i]) | __float_as_uint(xb[h] - v1[i]));
+                            }
+                        }
+                    }
+                    // Eq. 1 flags: AND of the sign bits over the walker's radii above R_cell; the
+                    // second group of the pair continues the walker of the first when it is not a
+                    // first group (a two-group walker starts on an even group)
+                    const uint32_t a0 = and32(v0), a1 = and32(v1);
+                    const uint32_t w0 = __ballot_sync(0xffffffffu, (a0 >> 31) == 0u);
+                    const uint32_t w1 = __ballot_sync(0xffffffffu, (((m1 & 2) == 0 ? (a0 & a1) : a1) >> 31) == 0u);
+                    if (lane == 0) {
+                        if (m0 >= 0 && (m0 & 1)) a.flags[((size_t)(m0 >> 2) * a.n_z + zi) * words + word] = w0;
+                        if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
+                    }
                 }
+                tc::mbar_arrive(barMe + st);   // the group records (and widths) of this chunk are read
             }
         }
     }
@@ -1014,9 +1039,10 @@ int f16_slots(const eor_ctx* c) {
 
 // Dynamic shared memory of the contraction: at least 120 KB, so that one CTA holds an SM (and
 // all of its tensor memory) at every basis size.
-size_t f16_smem(int kslots) {
+size_t f16_smem(int kslots, bool pops) {
     const size_t a = (size_t)kFM * kslots * 2, b = (size_t)kFN * kslots * 2;
-    const size_t need = 2 * a + kFStages * (b + kFMetaBytes) + (4 + 3 * kFStages + 4 + 1) * sizeof(uint64_t) + 16;
+    const size_t need =
+        2 * a + kFStages * (b + f16_meta_bytes(pops)) + (4 + 3 * kFStages + 4 + 1) * sizeof(uint64_t) + 16;
     return need > (120u << 10) ? need : (120u << 10);
 }
 
@@ -1026,13 +1052,19 @@ bool basis_f16_fits(int rank) { return rank >= 1 && f16_kslots(rank) <= kFKMax; 
 int basis_f16_kslots(int rank) { return f16_kslots(rank); }
 size_t basis_f16_a_bytes(long long n3, int n_z, int rank) { return (size_t)n_z * (size_t)n3 * f16_kslots(rank) * 2; }
 size_t basis_f16_b_bytes(const eor_ctx* c) {
-    return (size_t)c->cfg.n_z * (size_t)(f16_slots(c) / kFN) * ((size_t)kFN * c->k16 * 2 + kFMetaBytes);
+    return (size_t)c->cfg.n_z * (size_t)(f16_slots(c) / kFN) *
+           ((size_t)kFN * c->k16 * 2 + f16_meta_bytes(c->cfg.efficiency_model != 0));
 }
 size_t basis_f16_column_slots(const eor_ctx* c) { return (size_t)f16_slots(c); }
 
 cudaError_t prepare_basis_f16(eor_ctx* c) {
     if (!c->f16) return cudaSuccess;
-    return cudaFuncSetAttribute(k_basis_ionize_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f16_smem(c->k16));
+    cudaError_t e = cudaFuncSetAttribute(k_basis_ionize_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)f16_smem(c->k16, false));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_basis_ionize_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)f16_smem(c->k16, true));
+    return e;
 }
 
 // At eor_init_boxes: the power-of-two bounds of the basis fields, delta at R_cell of every box
@@ -1071,7 +1103,8 @@ cudaError_t build_columns_f16(eor_ctx* c, int n_walkers) {
     trace_begin(c, kKTables);
     k_format_b16<<<dim3(chunks, c->cfg.n_z), kFN, 0, c->stream>>>(c->d_cols, c->d_gmeta, c->d_ncols, c->d_coef,
                                                                  c->d_pairs, c->kb, c->basis_rank, c->max_radii,
-                                                                 c->cfg.n_z, chunks, c->d_fscale, c->k16, c->d_b16);
+                                                                 c->cfg.n_z, chunks, c->d_fscale, c->k16,
+                                                                 c->cfg.efficiency_model != 0, c->d_b16);
     trace_end(c);
     return cudaGetLastError();
 }
@@ -1083,12 +1116,16 @@ void launch_xq_finish(const unsigned long long* xq, int pairs, double* xhi_sum, 
 cudaError_t launch_basis_ionize_f16(eor_ctx* c) {
     const int tiles_per_z = (int)(c->n3 / kFM);
     const int total = tiles_per_z * c->cfg.n_z;
+    const bool pops = c->cfg.efficiency_model != 0;
     F16Args a{c->d_a16, c->d_b16, c->d_ncols, c->d_fwords, c->d_err, c->cfg.n_z, f16_slots(c) / kFN, tiles_per_z,
               c->k16 / 16, (uint32_t)(kFM * c->k16 * 2), (uint32_t)(kFN * c->k16 * 2), f16_sbo(c->k16),
-              (long long)c->n3, c->dbg_withhold, c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
+              f16_meta_bytes(pops), (long long)c->n3, c->dbg_withhold, c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
     const int grid = total < c->num_sms ? total : c->num_sms;
     trace_begin(c, kKBasis);
-    k_basis_ionize_f16<<<grid, kFThreads, f16_smem(c->k16), c->stream>>>(a);
+    if (pops)
+        k_basis_ionize_f16<true><<<grid, kFThreads, f16_smem(c->k16, true), c->stream>>>(a);
+    else
+        k_basis_ionize_f16<false><<<grid, kFThreads, f16_smem(c->k16, false), c->stream>>>(a);
     trace_end(c);
     return cudaGetLastError();
 }

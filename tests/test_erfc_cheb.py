@@ -1,5 +1,5 @@
-"""The Chebyshev-fitted erfc used by the tensor-core epilogue for f_coll at R_cell (Eq. 1's
-erfc), checked on the CPU: its coefficients are read from the CUDA source and the formula,
+"""The Chebyshev-fitted erfc used for f_coll at R_cell (Eq. 1's erfc) by the TF32 contraction's
+epilogue and the flag contraction's pencil pass, checked on the CPU: its coefficients are read from the CUDA source and the formula,
 evaluated in FP64, must stay within the published fractional error bound (1.2e-7) of erfc
 over the whole non-negative axis, and reduce to 1 at x = 0."""
 import os
@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                   "paper_1501_06576_gb300", "csrc", "tcgen05.cu")
+                   "paper_1501_06576_gb300", "csrc", "eor_internal.cuh")
 
 
 def coefficients():

@@ -54,7 +54,8 @@ def step_ref(box9):
     return oracle.Oracle().ionize(box9[0], BOX, 9.0, *STEP_PARAMS)
 
 
-@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT], ids=["basis_tensor_cores", "direct"])
+@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_TF32],
+                         ids=["basis_fp16_tensor_cores", "direct", "basis_tf32_tensor_cores"])
 def test_step_efficiency_256_matches_oracle(box9, step_ref, method):
     params = np.array([STEP_PARAMS])
     with eor21.Context(n=N, box_mpc=BOX, z=(9.0,), max_walkers=1) as ctx:

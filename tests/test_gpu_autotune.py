@@ -52,3 +52,30 @@ def test_autotune_device_buffers_and_errors():
     chi = ctx.likelihood(synth.walker_params(4, seed=1), np.full((1, 14), 5.0), np.ones((1, 14)))
     assert np.all(np.isfinite(chi))
     ctx.close()
+
+
+def test_power_spectrum_plane_tiling_does_not_change_results():
+    """At 128^3 the spectrum's plane pass runs as one CTA per plane or as a two-CTA cluster
+    (eor_set_ps_split); the spectra agree to the FP32 rounding of the per-thread partial
+    sums, and the autotuner reports the tiling it kept."""
+    n, box, zs = 128, 250.0, (9.0,)
+    ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=4)
+    ctx.init_boxes(synth.density_boxes(n, box, zs, seed=12))
+    params = synth.walker_params(4, seed=13)
+    mock = np.full((1, 14), 20.0)
+    sigma = 0.2 * mock
+    out = {}
+    for split in (1, 2):
+        ctx.set_ps_split(split)
+        assert ctx.get_tuning()["ps_split"] == split
+        out[split] = ctx.likelihood(params, mock, sigma, want_d2=True)
+    np.testing.assert_allclose(out[2][1], out[1][1], rtol=2e-6, equal_nan=True)
+    np.testing.assert_allclose(out[2][0], out[1][0], rtol=1e-5)
+    ctx.autotune(params, mock, sigma, reps=1)
+    assert ctx.get_tuning()["ps_split"] in (1, 2)
+    ctx.close()
+    small = eor21.Context(n=64, box_mpc=100.0, z=zs, max_walkers=1)
+    with pytest.raises(eor21.EorError) as ei:
+        small.set_ps_split(2)
+    assert ei.value.code == eor21.EOR_ENOTSUP
+    small.close()

@@ -24,8 +24,8 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_SIMT]
-METHOD_IDS = ["basis_tensor_cores", "direct", "basis_fp32_units"]
+METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_SIMT, eor21.EOR_METHOD_BASIS_TF32]
+METHOD_IDS = ["basis_fp16_tensor_cores", "direct", "basis_fp32_units", "basis_tf32_tensor_cores"]
 
 
 def make_ctx(n, box, zs, max_walkers=1, method=eor21.EOR_METHOD_BASIS, **kw):
@@ -358,8 +358,8 @@ def test_basis_window_rejects_radii_outside_its_range():
             assert e.value.code == eor21.EOR_EINVAL
 
 
-@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_BASIS_SIMT],
-                         ids=["basis_tensor_cores", "basis_fp32_units"])
+@pytest.mark.parametrize("method", [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_BASIS_SIMT, eor21.EOR_METHOD_BASIS_TF32],
+                         ids=["basis_fp16_tensor_cores", "basis_fp32_units", "basis_tf32_tensor_cores"])
 def test_basis_and_direct_methods_agree(method):
     n, box, zs = 64, 100.0, (8.0, 9.5)
     params = synth.walker_params(6, seed=12)

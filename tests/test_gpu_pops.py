@@ -27,8 +27,8 @@ MODEL1 = [((30.0, 12.0, 4.7), (0.3, 10.0, -0.4, 5.3)),
 MODEL2 = [((70.0, 15.0, 4.7), (4.0 / 3.0, -1.0 / 3.0, 0.0, 0.0)),
           ((30.0, 10.0, 5.0), (1.0, 0.0, 0.0, 0.0))]
 
-METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_SIMT]
-METHOD_IDS = ["basis_tensor_cores", "direct", "basis_fp32_units"]
+METHODS = [eor21.EOR_METHOD_BASIS, eor21.EOR_METHOD_DIRECT, eor21.EOR_METHOD_BASIS_SIMT, eor21.EOR_METHOD_BASIS_TF32]
+METHOD_IDS = ["basis_fp16_tensor_cores", "direct", "basis_fp32_units", "basis_tf32_tensor_cores"]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -52,8 +52,11 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    box = torch.zeros((8, 8, 8), dtype=torch.float32, device="cuda")
+    # buffers of the size n = 256 needs, so that the C entry point itself refuses the size
+    box = torch.zeros((256, 256, 256), dtype=torch.float32, device="cuda")
     d2 = torch.zeros(14, dtype=torch.float64, device="cuda")
     with pytest.raises(eor21.EorError) as e:
         eor21.box_power_spectrum_noalloc(256, 500.0, box, d2)
     assert e.value.code == eor21.EOR_EINVAL
+    with pytest.raises(ValueError):   # a box that does not match n is refused before the call
+        eor21.box_power_spectrum_noalloc(64, 100.0, box, d2)
