@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule (profiling runs)")
+    ap.add_argument("--ps-split", type=int, default=0, choices=[0, 1, 2],
+                    help="force the power spectrum's plane tiling after the autotuner (0: keep its choice)")
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
     ap.add_argument("--mcmc-steps", type=int, default=10)
@@ -256,14 +259,6 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for name in ("kernels.cu", "fft_core.cuh", "eor_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
-
-
 def basis_source_hash() -> str:
     """Hash of the sources of the contraction kernels (a stale traffic record is not used)."""
     h = hashlib.sha256()
@@ -271,20 +266,6 @@ def basis_source_hash() -> str:
         with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
-
-
-def ncu_traffic(kernel_class: str):
-    """DRAM bytes per task of a kernel class from the committed ncu summary, or None if the
-    kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        if d.get("source_hash") != kernel_source_hash():
-            return None
-        return d["bytes_per_task"].get(kernel_class)
-    except Exception:
-        return None
 
 
 def ncu_launch_traffic(kernel_class: str, walkers: int):
@@ -345,14 +326,6 @@ def f16_column_chunks(ladders) -> int:
             g += 1
         g += ng
     return -(-g * 32 // 256)
-
-
-def algorithmic_bytes(n: int):
-    """HBM bytes each FFT-pass kernel class must move per unit (one (walker, redshift,
-    radius) task): complex64 half spectrum nh*n*n*8."""
-    nspec = (n // 2 + 1) * n * n * 8
-    return {"filter_plane": 2 * nspec,       # read the density spectrum, write the plane-transformed task
-            "pencil_ionize": nspec}          # read it back (flags, delta and delta T_b extra per pair)
 
 
 def time_direct(ctx, eor21, torch, stream, flush, d_params, d_mock, d_sigma, W, steps, method=None, note=None):
@@ -565,6 +538,8 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
         d_params = torch.from_numpy(base).cuda()
         d_mock = torch.from_numpy(mock).cuda()
         d_sigma = torch.from_numpy(0.2 * mock).cuda()
+        ctx.autotune(d_params, d_mock, d_sigma, reps=1)   # launch schedule for this workload (untimed)
+        schedule = ctx.get_tuning()
         for _ in range(2):
             ctx.likelihood(d_params, d_mock, d_sigma)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -595,6 +570,7 @@ def time_two_pop(eor21, synth, torch, stream, flush, args):
                         "256^3, L = 500 Mpc, z = 8, 9, 10, step-function efficiency (comparison), zeta in [5, 100], "
                         "log10 T_vir in [4, 6], R_mfp in [5, 20] Mpc",
             "radius_tasks_per_step": radii, "basis_rank": rank, "gpu_launches_per_step": launches,
+            "schedule": schedule,
             "classes_traced_step": share, "rates": rates, "dtype": "f32 (FP64 tables)"}
 
 
@@ -674,8 +650,13 @@ def main():
         d_sigma = torch.from_numpy(np.ascontiguousarray(sigma)).cuda()
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         # launch schedule picked by the library's autotuner on these walkers (untimed set-up)
-        tuned = ctx.autotune(d_params, d_mock, d_sigma, reps=3)
+        if not args.no_autotune:
+            ctx.autotune(d_params, d_mock, d_sigma, reps=3)
+        if args.ps_split:
+            ctx.set_ps_split(args.ps_split)
         schedule = ctx.get_tuning()
+        if args.ps_split:
+            schedule["forced"] = "ps_split"
         ctx.trace(not args.no_trace)
         for _ in range(args.warmup):
             ctx.likelihood(d_params, d_mock, d_sigma)
@@ -800,54 +781,59 @@ def main():
     if rank != 0:
         return 0
 
-    # ---------------- roofline of the dominant kernel class
-    roof = None
+    # ---------------- roofline of each kernel class of the step, and of the dominant one
+    roof, kernel_rates = None, {}
     if class_ms:
-        dom = max(class_ms, key=lambda k: class_ms[k])
-        launches_dom = max(class_launches[dom], 1)
-        avg_launch_ms = class_ms[dom] / launches_dom
         share = {k: class_ms[k] / sum(class_ms.values()) for k in class_ms if class_ms[k] > 0}
-        if dom == "basis_ionize":
-            # contraction: useful flops = 2 x rank per (cell, walker, redshift, radius)
-            flops_per_unit = 2.0 * basis_rank * N ** 3
-            units_per_launch = tasks_per_step * args.steps / launches_dom
-            achieved = flops_per_unit * units_per_launch / (avg_launch_ms / 1e3) / 1e12
-            if contract_kind == eor21.EOR_CONTRACT_FP16:
-                peak, peak_kind = fp16_peak_tflops()
-                # executed: the three products side by side along K (k_slots FP16 values), every
-                # cell against 256-column chunks of radii above R_cell
-                executed = 2 * k_slots * N ** 3 * f16_column_chunks(ladders) * 256 * len(ZS)
-                tf32, _ = tf32_peak_tflops()
-                extra = {"executed_fp16_tflops": executed * args.steps / launches_dom / (avg_launch_ms / 1e3) / 1e12,
-                         "frac_of_tf32_peak": achieved / tf32, "k_slots": k_slots}
-                bound = "tensor"
-            elif contract_kind == eor21.EOR_CONTRACT_TF32:
-                peak, peak_kind = tf32_peak_tflops()
-                # executed: 3 TF32 products (hi*hi, hi*lo, lo*hi) over K = rank + 1 rounded up to
-                # whole MMA steps of 8, and 64-column chunks
-                cols_per_z = tasks_per_step // len(ZS)
-                k_exec = (basis_rank + 1 + 7) // 8 * 8
-                executed = 3 * 2 * k_exec * N ** 3 * (-(-cols_per_z // 64) * 64) * len(ZS)
-                extra = {"executed_tf32_tflops": executed * args.steps / launches_dom / (avg_launch_ms / 1e3) / 1e12}
-                bound = "tensor"
-            else:
-                peak, peak_kind = fp32_peak_tflops(), "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
-                extra, bound = {}, "alu"
-            roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": ncu_launch_traffic(dom, W), "kernel": dom, "peak_kind": peak_kind,
-                    "flops_per_unit": flops_per_unit, "unit_def": "one (walker, redshift, radius) over all cells",
-                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share, **extra}
-        else:
-            peak, peak_kind = measured_peak()
-            per_unit = algorithmic_bytes(N)
-            units_per_launch = tasks_per_step * args.steps / launches_dom
-            bytes_per_launch = per_unit.get(dom, 0) * units_per_launch
-            achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
-            traffic = ncu_traffic(dom)
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None if traffic is None else traffic * units_per_launch, "kernel": dom,
-                    "peak_kind": peak_kind, "bytes_per_unit": per_unit.get(dom, 0),
-                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_launch_ms, "share": share}
+        pairs_per_step = W * len(ZS)
+        hbm_peak_v, hbm_kind_v = measured_peak()
+        nspec_b = (N // 2 + 1) * N * N * 8
+        kf = 2.0 * math.pi / BOX
+        planes = sum(1 for kz in range(N // 2 + 1) if kf * kz < 1.5)
+        for cls, ms_total in class_ms.items():
+            launches_c = max(class_launches.get(cls, 0), 1)
+            avg_ms = ms_total / launches_c
+            if cls == "basis_ionize":
+                # useful flops = 2 x rank per (cell, walker, redshift, radius)
+                flops_per_unit = 2.0 * basis_rank * N ** 3
+                units = tasks_per_step * args.steps / launches_c
+                achieved = flops_per_unit * units / (avg_ms / 1e3) / 1e12
+                if contract_kind == eor21.EOR_CONTRACT_FP16:
+                    peak, peak_kind = fp16_peak_tflops()
+                    executed = 2 * k_slots * N ** 3 * f16_column_chunks(ladders) * 256 * len(ZS)
+                    tf32, _ = tf32_peak_tflops()
+                    extra = {"executed_fp16_tflops": executed * args.steps / launches_c / (avg_ms / 1e3) / 1e12,
+                             "frac_of_tf32_peak": achieved / tf32, "k_slots": k_slots}
+                    bound = "tensor"
+                elif contract_kind == eor21.EOR_CONTRACT_TF32:
+                    peak, peak_kind = tf32_peak_tflops()
+                    extra, bound = {}, "tensor"
+                else:
+                    peak, peak_kind = fp32_peak_tflops(), "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                    extra, bound = {}, "alu"
+                kernel_rates[cls] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak, "traffic": ncu_launch_traffic(cls, W), "kernel": cls,
+                                     "peak_kind": peak_kind, "flops_per_unit": flops_per_unit,
+                                     "unit_def": "one (walker, redshift, radius) over all cells",
+                                     "units_per_launch": units, "avg_launch_ms": avg_ms, **extra}
+            elif cls in ("forward_fft", "ps_plane"):
+                # per (walker, redshift): the pencil pass writes the half spectrum and reads the flag
+                # words and its share of delta and delta at R_cell; the plane pass reads the planes
+                # that hold a binned mode
+                if cls == "forward_fft":
+                    per_unit = nspec_b + N ** 3 // 8 + 2 * N ** 3 * 4 // W
+                    udef = "one (walker, redshift): half spectrum write + flag words + delta, delta_Rcell share"
+                else:
+                    per_unit = planes * N * N * 8
+                    udef = f"one (walker, redshift): read of the {planes} kz planes with a binned mode"
+                units = pairs_per_step * args.steps / launches_c
+                achieved = per_unit * units / (avg_ms / 1e3) / 1e9
+                kernel_rates[cls] = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak_v, "unit": "GB/s",
+                                     "frac": achieved / hbm_peak_v, "traffic": None, "kernel": cls,
+                                     "peak_kind": hbm_kind_v, "bytes_per_unit": per_unit, "unit_def": udef,
+                                     "units_per_launch": units, "avg_launch_ms": avg_ms}
+        dom = max((k for k in class_ms if k in kernel_rates), key=lambda k: class_ms[k])
+        roof = dict(kernel_rates[dom], share=share)
     hbm_peak, hbm_kind = measured_peak()
     # the excursion-set path's algorithmic HBM bytes per (walker, z, radius) of a per-radius FFT
     # design: read the density spectrum (nh n^2 complex64) and read + write the cell's flag byte
@@ -879,7 +865,7 @@ def main():
                        "parallelism": f"walkers sharded over {world} GPU(s)", "traced": not args.no_trace,
                        "schedule": {**schedule, "picked_by": "eor_autotune"}},
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof,
+            "gpu_launches": launches, "roofline": roof, "kernel_rates": kernel_rates,
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
                        "contraction": {eor21.EOR_CONTRACT_FP16: "tcgen05 FP16 hi/lo, 3 products along K",
                                        eor21.EOR_CONTRACT_TF32: "tcgen05 3xTF32",

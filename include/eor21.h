@@ -215,17 +215,24 @@ int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
  * shared memory; two such CTAs share an SM). Default 2; EOR_ENOTSUP for 2 at other n. Drops
  * the captured graph. eor_get_tuning reads the current schedule (each pointer optional). */
 int eor_set_ps_split(eor_ctx* ctx, int split);
-int eor_get_tuning(const eor_ctx* ctx, int* group, int* pairs, int* plane_threads, int* ps_split);
+/* Streams of the basis methods' power spectrum: 2 (default) = the plane pass of a batch of
+ * (walker, redshift) pairs runs on a second stream of the context while the pencil pass of the
+ * next batch runs (a double-buffered intermediate; the two streams fork and join by events,
+ * also inside the captured graph); 1 = the two passes in turn on the context's stream. Drops
+ * the captured graph. */
+int eor_set_ps_streams(eor_ctx* ctx, int streams);
+int eor_get_tuning(const eor_ctx* ctx, int* group, int* pairs, int* plane_threads, int* ps_split, int* ps_streams);
 
 /* Autotuner of the launch schedule (results do not depend on it): times eor_likelihood on
  * these walkers (arguments as there, n_walkers <= max_walkers) with CUDA events on the
  * context's stream, `reps` graph replays per candidate after one warm-up, over the
  * candidates of the current method -- pairs in {4, 8, 16, 32} x the spectrum's plane tiling
  * (128^3 grids: split 2, or split 1 with plane_threads 512 or 1024; split 1 and 512
- * otherwise), and for EOR_METHOD_DIRECT also group in {4, 8, 16} and plane_threads with
- * both splits -- and keeps the fastest (eor_set_tuning, eor_set_ps_split). group, pairs,
- * plane_threads and ms (mean milliseconds of one call) receive the choice, each optional;
- * eor_get_tuning gives the split. Tracing is off while it runs and is restored afterwards. */
+ * otherwise) x ps_streams in {2, 1}, and for EOR_METHOD_DIRECT (one stream) also group in
+ * {4, 8, 16} and plane_threads with both splits -- and keeps the fastest (eor_set_tuning,
+ * eor_set_ps_split, eor_set_ps_streams). group, pairs, plane_threads and ms (mean
+ * milliseconds of one call) receive the choice, each optional; eor_get_tuning gives the
+ * rest. Tracing is off while it runs and is restored afterwards. */
 int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double* mock_d2, const double* sigma,
                  int reps, int* group, int* pairs, int* plane_threads, double* ms, int mem);
 

@@ -690,7 +690,7 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     c->d_inter = inter;
     c->d_flags = flags;
     c->d_psinter = psinter;
-    c->tune = eor::Tuning{group, pairs, plane_threads, c->tune.method, c->tune.ps_split};
+    c->tune = eor::Tuning{group, pairs, plane_threads, c->tune.method, c->tune.ps_split, c->tune.ps_streams};
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -704,21 +704,24 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     if (!c) return EOR_EINVAL;
     if (c->stage < 1) return fail(c, EOR_ESTATE, "eor_init_boxes first");
     if (reps < 1 || reps > 1000) return fail(c, EOR_EINVAL, "reps outside 1..1000");
-    struct Cand { int group, pairs, threads, split; };
+    struct Cand { int group, pairs, threads, split, streams; };
     std::vector<Cand> cands;
     const int groups_direct[] = {4, 8, 16};
     const int pairs_list[] = {4, 8, 16, 32};
     const bool direct = c->tune.method == eor::kMethodDirect;
-    for (int split : {2, 1}) {
-        if (split == 2 && c->n != 128) continue;   // the cluster form of the spectrum's plane pass
-        for (int th : {512, 1024}) {
-            if (th == 1024 && c->n != 128) continue;
-            if (th == 1024 && split == 2 && !direct) continue;   // the CTA size then changes no kernel of the step
-            for (int p : pairs_list) {
-                if (direct)
-                    for (int gsz : groups_direct) cands.push_back({gsz, p, th, split});
-                else
-                    cands.push_back({c->tune.group, p, th, split});
+    for (int streams : {2, 1}) {
+        if (streams == 2 && direct) continue;   // the direct method's passes run in one stream
+        for (int split : {2, 1}) {
+            if (split == 2 && c->n != 128) continue;   // the cluster form of the spectrum's plane pass
+            for (int th : {512, 1024}) {
+                if (th == 1024 && c->n != 128) continue;
+                if (th == 1024 && split == 2 && !direct) continue;   // the CTA size then changes no kernel of the step
+                for (int p : pairs_list) {
+                    if (direct)
+                        for (int gsz : groups_direct) cands.push_back({gsz, p, th, split, streams});
+                    else
+                        cands.push_back({c->tune.group, p, th, split, streams});
+                }
             }
         }
     }
@@ -730,7 +733,7 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
         c->trace_on = traced;
         return fail(c, EOR_ECUDA, "autotune events");
     }
-    const Cand start{c->tune.group, c->tune.pairs, c->tune.plane_threads, c->tune.ps_split};
+    const Cand start{c->tune.group, c->tune.pairs, c->tune.plane_threads, c->tune.ps_split, c->tune.ps_streams};
     Cand best = start;
     double best_ms = INFINITY;
     std::vector<double> chi2_host;
@@ -750,6 +753,7 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     for (const Cand& k : cands) {
         if ((r = eor_set_tuning(c, k.group, k.pairs, k.threads)) != EOR_OK) break;
         c->tune.ps_split = k.split;
+        c->tune.ps_streams = k.streams;
         // warm-up: captures this schedule's graph and checks the arguments
         if ((r = eor_likelihood(c, params, n_walkers, mock_d2, sigma, chi2, nullptr, mem)) != EOR_OK) break;
         cudaEventRecord(e0, c->stream);
@@ -777,10 +781,12 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
         const std::string msg = c->err;
         eor_set_tuning(c, start.group, start.pairs, start.threads);
         c->tune.ps_split = start.split;
+        c->tune.ps_streams = start.streams;
         return fail(c, r, "autotune: " + msg);
     }
     if ((r = eor_set_tuning(c, best.group, best.pairs, best.threads)) != EOR_OK) return r;
     c->tune.ps_split = best.split;
+    c->tune.ps_streams = best.streams;
     if (group) *group = best.group;
     if (pairs) *pairs = best.pairs;
     if (plane_threads) *plane_threads = best.threads;
@@ -802,12 +808,26 @@ int eor_set_ps_split(eor_ctx* c, int split) {
     return EOR_OK;
 }
 
-int eor_get_tuning(const eor_ctx* c, int* group, int* pairs, int* plane_threads, int* ps_split) {
+int eor_set_ps_streams(eor_ctx* c, int streams) {
+    if (!c) return EOR_EINVAL;
+    if (streams != 1 && streams != 2) return fail(c, EOR_EINVAL, "ps_streams must be 1 or 2");
+    CK(cudaStreamSynchronize(c->stream), "ps streams");
+    c->tune.ps_streams = streams;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_walkers = -1;
+    }
+    return EOR_OK;
+}
+
+int eor_get_tuning(const eor_ctx* c, int* group, int* pairs, int* plane_threads, int* ps_split, int* ps_streams) {
     if (!c) return EOR_EINVAL;
     if (group) *group = c->tune.group;
     if (pairs) *pairs = c->tune.pairs;
     if (plane_threads) *plane_threads = c->tune.plane_threads;
     if (ps_split) *ps_split = c->n == 128 ? c->tune.ps_split : 1;
+    if (ps_streams) *ps_streams = c->tune.ps_streams;
     return EOR_OK;
 }
 

@@ -179,9 +179,55 @@ constexpr size_t gt_smem(bool b_exact) {
     return 2 * (size_t)gt_stage_bytes<NT>(b_exact) + 4 * sizeof(uint64_t) + 16;
 }
 
+// One stage's operand values in registers: core row (row, quad) = the 4 values k = 4 quad ..
+// 4 quad + 3 of one row, 16 bytes of the K-major core-matrix layout. Core row index cr maps
+// to row (cr >> 6) * 8 + (cr & 7) and quad (cr >> 3) & 7, so that a warp's 32 lanes write 8
+// rows x 4 quads: 512 contiguous-in-banks bytes, no bank conflict.
+template <int ROWS>
+struct GtStage {
+    static constexpr int PER = ROWS * 8 / kGtThreads;   // core rows per thread
+    float4 v[PER];
+};
+
+__device__ __forceinline__ int gt_row(int cr) { return (cr >> 6) * 8 + (cr & 7); }
+__device__ __forceinline__ int gt_quad(int cr) { return (cr >> 3) & 7; }
+
+// Operand (row, k) = P[row * rs + k * ks] for row < rows and k < K, else 0.
+template <int ROWS>
+__device__ __forceinline__ void gt_load(GtStage<ROWS>& st, const float* P, long long rs, long long ks, int row0,
+                                        int rows, int k0, int K) {
+#pragma unroll
+    for (int i = 0; i < GtStage<ROWS>::PER; i++) {
+        const int cr = threadIdx.x + i * kGtThreads, r = row0 + gt_row(cr), k = k0 + 4 * gt_quad(cr);
+        float x[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) x[c] = (r < rows && k + c < K) ? P[r * rs + (k + c) * ks] : 0.0f;
+        st.v[i] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+}
+
+// hi (and with LO the remainder's TF32 rounding) of the stage into the core-matrix layout.
+template <int ROWS, bool LO>
+__device__ __forceinline__ void gt_store(const GtStage<ROWS>& st, unsigned char* hi, unsigned char* lo) {
+#pragma unroll
+    for (int i = 0; i < GtStage<ROWS>::PER; i++) {
+        const int cr = threadIdx.x + i * kGtThreads;
+        const uint32_t off = tc::core_offset(gt_row(cr), 4 * gt_quad(cr));
+        const float x[4] = {st.v[i].x, st.v[i].y, st.v[i].z, st.v[i].w};
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            h[c] = tc::to_tf32(x[c]);
+            l[c] = tc::to_tf32(x[c] - __uint_as_float(h[c]));
+        }
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if constexpr (LO) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 template <int EPI, bool B_EXACT, int NT>
 __global__ void __launch_bounds__(kGtThreads) k_emu_gemm_tc(GemmArgs g) {
-    static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "MMA N");
+    static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256 && (NT * 8) % kGtThreads == 0, "MMA N");
     constexpr uint32_t kStage = gt_stage_bytes<NT>(B_EXACT);
     constexpr uint32_t kBBytes = (uint32_t)NT * kGtK * 4;
     constexpr uint32_t kCols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
@@ -202,10 +248,15 @@ __global__ void __launch_bounds__(kGtThreads) k_emu_gemm_tc(GemmArgs g) {
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const int nk = (g.K + kGtK - 1) / kGtK;
+    // B(n, k) = B[k bk + n bn]: rows n, stride bn; k stride bk
+    GtStage<kGtM> ra;
+    GtStage<NT> rb;
+    gt_load<kGtM>(ra, A, g.am, g.ak, m0, g.M, 0, g.K);
+    gt_load<NT>(rb, B, g.bn, g.bk, n0, g.N, 0, g.K);
     bool ok = true;
     int last = -1;   // the last stage whose MMAs were issued (every thread tracks it)
     for (int kc = 0; kc < nk; kc++) {
-        const int st = kc & 1, k0 = kc * kGtK;
+        const int st = kc & 1;
         // the MMAs that read this stage two steps ago are done (a timeout stops every thread)
         if (kc >= 2 && !__syncthreads_and(tc::mbar_wait(bar + st, (uint32_t)((kc - 2) >> 1) & 1u, kGtWaitNs))) {
             ok = false;
@@ -215,24 +266,11 @@ __global__ void __launch_bounds__(kGtThreads) k_emu_gemm_tc(GemmArgs g) {
         unsigned char* Al = Ah + kGtABytes;
         unsigned char* Bh = Al + kGtABytes;
         unsigned char* Bl = Bh + kBBytes;   // unused with B_EXACT
-        // consecutive threads walk the operand's unit-stride index (coalesced loads)
-        const bool a_kfast = g.ak == 1, b_nfast = g.bn == 1;
-        for (int idx = t; idx < kGtM * kGtK; idx += kGtThreads) {
-            const int mm = a_kfast ? idx / kGtK : idx % kGtM, kk = a_kfast ? idx % kGtK : idx / kGtM;
-            const int m = m0 + mm, k = k0 + kk;
-            const float v = (m < g.M && k < g.K) ? A[m * g.am + k * g.ak] : 0.0f;
-            const uint32_t hi = tc::to_tf32(v), lo = tc::to_tf32(v - __uint_as_float(hi));
-            *reinterpret_cast<uint32_t*>(Ah + tc::core_offset(mm, kk)) = hi;
-            *reinterpret_cast<uint32_t*>(Al + tc::core_offset(mm, kk)) = lo;
-        }
-        for (int idx = t; idx < NT * kGtK; idx += kGtThreads) {
-            const int nn = b_nfast ? idx % NT : idx / kGtK, kk = b_nfast ? idx / NT : idx % kGtK;
-            const int n = n0 + nn, k = k0 + kk;
-            const float v = (n < g.N && k < g.K) ? B[k * g.bk + n * g.bn] : 0.0f;
-            const uint32_t hi = tc::to_tf32(v);
-            *reinterpret_cast<uint32_t*>(Bh + tc::core_offset(nn, kk)) = hi;
-            if constexpr (!B_EXACT)
-                *reinterpret_cast<uint32_t*>(Bl + tc::core_offset(nn, kk)) = tc::to_tf32(v - __uint_as_float(hi));
+        gt_store<kGtM, true>(ra, Ah, Al);
+        gt_store<NT, !B_EXACT>(rb, Bh, Bl);
+        if (kc + 1 < nk) {   // the next stage's loads are in flight during the barrier and the MMAs
+            gt_load<kGtM>(ra, A, g.am, g.ak, m0, g.M, (kc + 1) * kGtK, g.K);
+            gt_load<NT>(rb, B, g.bn, g.bk, n0, g.N, (kc + 1) * kGtK, g.K);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();

@@ -1167,16 +1167,20 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
     if (flags) cudaMemsetAsync(c->d_xq, 0, sizeof(unsigned long long) * n_pairs, c->stream);
     const float kf = (float)(2.0 * kPi / c->cfg.box_mpc);
     // batches of P pairs: the pencil pass of batch b (c->stream) fills half b % 2 of the
-    // intermediate buffer; the plane pass of batch b (stream2) reads it while the pencil pass of
-    // batch b + 1 fills the other half; batch b + 2 waits for the plane pass of batch b
-    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
-    if (e != cudaSuccess) return e;
+    // intermediate buffer; with two streams the plane pass of batch b (stream2) reads it while
+    // the pencil pass of batch b + 1 fills the other half, and batch b + 2 waits for the plane
+    // pass of batch b; with one stream the passes run in turn
+    const bool two = c->tune.ps_streams == 2;
+    cudaStream_t ps = two ? c->stream2 : c->stream;   // the plane passes' stream
+    cudaError_t e = cudaSuccess;
+    if (two && ((e = cudaEventRecord(c->ev_fork, c->stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0)) != cudaSuccess))
+        return e;
     int b = 0;
     for (int pair0 = 0; pair0 < n_pairs; pair0 += P, b++) {
         const int h = b & 1;
         float2* half = c->d_psinter + (size_t)h * P * c->nspec;
-        if (b >= 2 && (e = cudaStreamWaitEvent(c->stream, c->ev_plane[h], 0)) != cudaSuccess) return e;
+        if (two && b >= 2 && (e = cudaStreamWaitEvent(c->stream, c->ev_plane[h], 0)) != cudaSuccess) return e;
         trace_begin(c, kKForward);
         if (flags) {
             BrightArgs ba{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, half,
@@ -1188,14 +1192,15 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
                 c->d_dtb, half, pair0, n_pairs);
         }
         trace_end(c);
-        if ((e = cudaEventRecord(c->ev_pencil[h], c->stream)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(c->stream2, c->ev_pencil[h], 0)) != cudaSuccess) return e;
+        if (two && ((e = cudaEventRecord(c->ev_pencil[h], c->stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(c->stream2, c->ev_pencil[h], 0)) != cudaSuccess))
+            return e;
         PSArgs ap{half, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins, kf * kf * kf};
-        if ((e = plane_ps<N, T>(c, ap, c->ps_planes, P, c->stream2)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(c->ev_plane[h], c->stream2)) != cudaSuccess) return e;
+        if ((e = plane_ps<N, T>(c, ap, c->ps_planes, P, ps)) != cudaSuccess) return e;
+        if (two && (e = cudaEventRecord(c->ev_plane[h], c->stream2)) != cudaSuccess) return e;
     }
     // join: the last plane pass of each half
-    for (int h = 0; h < 2 && h < b; h++)
+    for (int h = 0; two && h < 2 && h < b; h++)
         if ((e = cudaStreamWaitEvent(c->stream, c->ev_plane[(b - 1 - h) & 1], 0)) != cudaSuccess) return e;
     if (flags) {
         trace_begin(c, kKFinish);

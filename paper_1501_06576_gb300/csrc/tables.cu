@@ -245,58 +245,79 @@ struct WalkerTableArgs {
 
 // One thread per (walker, redshift): M_min (Sec. 2.1.3), ladder (Sec. 2.1), sigma^2 of
 // each radius, the threshold overdensity of Eq. 1 and the partial-ionization constants.
+// One warp per (walker, redshift): lane j takes radii j and j + 32 of the ladder. Every lane
+// forms the ladder by the same sequence of FP64 divisions (so that radius j is bitwise the
+// serial ladder's), the walker's M_min and erfcinv(1/zeta); the lanes then fill their radii's
+// thresholds of Eq. 1 and the last lane to hold a radius sets the R_cell quantities.
 __global__ void k_walker_tables(WalkerTableArgs a) {
-    int pid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (pid >= a.n_walkers * a.n_z) return;
-    int w = pid / a.n_z, zi = pid % a.n_z;
-    double zeta = a.params[3 * w], r_mfp = a.params[3 * w + 1], logt = a.params[3 * w + 2];
+    const int w = pid / a.n_z, zi = pid % a.n_z;
+    const double zeta = a.params[3 * w], r_mfp = a.params[3 * w + 1], logt = a.params[3 * w + 2];
     PairInfo& P = a.pairs[pid];
-    P.w = w; P.zi = zi; P.pad = 0;
-    bool ok = isfinite(zeta) && isfinite(r_mfp) && isfinite(logt) && zeta > 0.0 && r_mfp > 0.0 &&
-              r_mfp <= a.r_mfp_max && logt > 0.0 && logt < 12.0;
+    const bool ok = isfinite(zeta) && isfinite(r_mfp) && isfinite(logt) && zeta > 0.0 && r_mfp > 0.0 &&
+                    r_mfp <= a.r_mfp_max && logt > 0.0 && logt < 12.0;
     if (!ok) {
-        atomicOr(a.err, kErrParam);
-        P.n_r = 0;
-        if (zi == 0) a.walkers[w].n_r = 0;
+        if (lane == 0) {
+            atomicOr(a.err, kErrParam);
+            P.w = w; P.zi = zi; P.pad = 0;
+            P.n_r = 0;
+            if (zi == 0) a.walkers[w].n_r = 0;
+        }
         return;
     }
     // radius ladder: R_mfp, R_mfp / f, ... while above R_cell, then R_cell once
-    double radii[kMaxRadii];
+    double rj[2] = {0.0, 0.0};
     int nr = 0;
-    double r = r_mfp;
-    while (r > a.r_cell) {
-        if (nr >= a.max_radii - 1) { atomicOr(a.err, kErrLadder); break; }
-        radii[nr++] = r;
-        r = r / a.r_factor;
+    bool over = false;
+    {
+        double r = r_mfp;
+        while (r > a.r_cell) {
+            if (nr >= a.max_radii - 1) { over = true; break; }
+            if (nr == lane) rj[0] = r;
+            if (nr == lane + 32) rj[1] = r;
+            nr++;
+            r = r / a.r_factor;
+        }
+        if (nr == lane) rj[0] = a.r_cell;
+        if (nr == lane + 32) rj[1] = a.r_cell;
+        nr++;
     }
-    radii[nr++] = a.r_cell;
-    P.n_r = nr;
-    if (zi == 0) {
-        a.walkers[w].n_r = nr;
-        for (int j = 0; j < nr; j++) a.walkers[w].radii[j] = radii[j];
-    }
+    if (over && lane == 0) atomicOr(a.err, kErrLadder);
     // virial temperature -> minimum halo mass at z
-    double zp = 1.0 + a.z[zi];
-    double m_min = virial_mass(logt, a.z[zi], a.h, a.omega_m, a.omega_l, a.mu);
-    double r_min = cbrt(3.0 * m_min / (4.0 * kPi * a.rho_mean));
-    double g2 = a.growth[zi] * a.growth[zi];
-    double s2_min = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, r_min, a.err);
+    const double zp = 1.0 + a.z[zi];
+    const double m_min = virial_mass(logt, a.z[zi], a.h, a.omega_m, a.omega_l, a.mu);
+    const double r_min = cbrt(3.0 * m_min / (4.0 * kPi * a.rho_mean));
+    const double g2 = a.growth[zi] * a.growth[zi];
+    const double s2_min = g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, r_min, a.err);
     // zeta erfc((delta_c - delta_R) / sqrt(2 s2)) >= 1  <=>  delta_R >= delta_c - sqrt(2 s2) erfcinv(1/zeta)
-    double u_star = zeta >= 1.0 ? erfcinv(1.0 / zeta) : 0.0;
-    double s2 = 0.0;
-    for (int j = 0; j < nr; j++) {
-        s2 = s2_min - g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, radii[j], a.err);
-        double dcrit = (s2 > 0.0 && zeta >= 1.0) ? a.delta_c - sqrt(2.0 * s2) * u_star : INFINITY;
-        P.delta_crit[j] = (float)dcrit;
+    const double u_star = zeta >= 1.0 ? erfcinv(1.0 / zeta) : 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int j = lane + 32 * h;
+        if (j < nr) {
+            const double s2 = s2_min - g2 * interp_lnsig(a.lnsig, a.lnr_lo, a.dlnr, rj[h], a.err);
+            const double dcrit = (s2 > 0.0 && zeta >= 1.0) ? a.delta_c - sqrt(2.0 * s2) * u_star : INFINITY;
+            P.delta_crit[j] = (float)dcrit;
+            if (zi == 0) a.walkers[w].radii[j] = rj[h];
+            if (j == nr - 1) {   // R_cell
+                P.cell_ok = s2 > 0.0 ? 1.0f : 0.0f;
+                P.inv_sqrt2s2_cell = s2 > 0.0 ? (float)(1.0 / sqrt(2.0 * s2)) : 0.0f;
+            }
+        } else if (j < kMaxRadii) {
+            P.delta_crit[j] = INFINITY;
+        }
+        if (j < kMaxRadii) P.delta_hi[j] = INFINITY;
     }
-    for (int j = nr; j < kMaxRadii; j++) P.delta_crit[j] = INFINITY;
-    for (int j = 0; j < kMaxRadii; j++) P.delta_hi[j] = INFINITY;
-    P.f_inv_h = 0.0f;
-    P.zeta = (float)zeta;
-    P.cell_ok = s2 > 0.0 ? 1.0f : 0.0f;
-    P.inv_sqrt2s2_cell = s2 > 0.0 ? (float)(1.0 / sqrt(2.0 * s2)) : 0.0f;
-    double h2 = a.h * a.h;
-    P.t0 = (float)(27.0 * sqrt(zp / 10.0 * 0.15 / (a.omega_m * h2)) * (a.omega_b * h2 / 0.023));
+    if (lane == 0) {
+        P.w = w; P.zi = zi; P.pad = 0;
+        P.n_r = nr;
+        if (zi == 0) a.walkers[w].n_r = nr;
+        P.f_inv_h = 0.0f;
+        P.zeta = (float)zeta;
+        const double h2 = a.h * a.h;
+        P.t0 = (float)(27.0 * sqrt(zp / 10.0 * 0.15 / (a.omega_m * h2)) * (a.omega_b * h2 / 0.023));
+    }
 }
 
 // ------------------------------------------------ mass-dependent efficiency (Sec. 5)
@@ -625,7 +646,7 @@ cudaError_t build_walker_tables(eor_ctx* c, int n_walkers) {
     a.err = c->d_err;
     int np = n_walkers * g.n_z;
     trace_begin(c, kKTables);
-    k_walker_tables<<<(np + 127) / 128, 128, 0, c->stream>>>(a);
+    k_walker_tables<<<(np + 3) / 4, 128, 0, c->stream>>>(a);   // one warp per (walker, redshift)
     trace_end(c);
     if (g.efficiency_model) {
         PopArgs pa{};

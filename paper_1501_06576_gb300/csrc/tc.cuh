@@ -123,10 +123,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // One test of the mbarrier phase `parity`; the thread may be suspended for at most about
-// kSuspendNs while the phase is incomplete (explicit suspend-time hint; 0: the hardware's own
-// time limit).
+// kSuspendNs while the phase is incomplete (explicit suspend-time hint; 0, the default: the
+// hardware's own time limit, measured 2 % faster on the flag contraction's step than 1000 ns).
 #ifndef EOR_MBAR_SUSPEND_NS
-#define EOR_MBAR_SUSPEND_NS 1000
+#define EOR_MBAR_SUSPEND_NS 0
 #endif
 constexpr uint32_t kSuspendNs = EOR_MBAR_SUSPEND_NS;
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {

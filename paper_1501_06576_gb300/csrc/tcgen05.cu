@@ -642,7 +642,8 @@ namespace {
 constexpr int kFM = 128;                        // cells per tile (MMA M)
 constexpr int kFN = 256;                        // coefficient columns per chunk (MMA N)
 constexpr int kFKMax = 96;                      // FP16 K slots at most (six MMA steps of 16)
-constexpr int kFStages = 3;                     // coefficient chunks in flight
+constexpr int kFStagesMax = 4;                  // coefficient chunks in flight (4, or 3 when 4 do not fit)
+constexpr int kFMetaStages = 8;                 // group records (and widths) of chunks in flight
 constexpr int kFGroups = kFN / kGroup;          // walker groups per chunk
 constexpr uint32_t kFRecBytes = kFGroups * 16;  // group records
 constexpr uint32_t kFWidthBytes = kFN * 4;      // per column t (delta_hi - delta_crit) (mass-dependent efficiency)
@@ -805,6 +806,7 @@ struct F16Args {
     int n_z, chunks_per_z, tiles_per_z, ksteps;
     uint32_t a_bytes, b_bytes, sbo;
     uint32_t meta_bytes;        // group records (and with POPS the columns' interval widths)
+    int stages;                 // coefficient stages (3 or 4)
     long long n3;
     int withhold;               // test-only failure injection (see TcArgs), -1 off
     uint64_t free_wait_ns;
@@ -813,31 +815,35 @@ struct F16Args {
 // Persistent CTA (one per SM): tiles of 128 cells t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // (all cells of box 0 first), each against every coefficient chunk of its box. Roles: thread
 // 32 issues the bulk copies (a tile's A operands into one of two stages half-way through the
-// previous tile, once the MMAs of the tile two before are done; chunk g into stage
-// g % kFStages as soon as chunk g - kFStages has left it), thread 0 the MMAs (per chunk ksteps
-// M128 N256 K16 FP16 MMAs into tensor-memory buffer g % 2; it waits only for operands and a
-// free buffer, also across tiles), warps 4-19 the epilogue: warp (q = lane quarter, p) reads
-// its 32 cells' columns 64 p .. 64 p + 63 of the buffer, releases the buffer and, for the
-// walkers of groups 2p, 2p + 1, stores the Eq. 1 flags of its 32 cells as one word (a walker's
-// flag: the AND of the sign bits of its columns is clear). x_HI, delta T_b and the power
-// spectrum follow in the pencil pass. Chunk counters g run over all chunks of the CTA's
-// tiles. POPS (a mass-dependent efficiency): a column flags where 0 <= D <= t (delta_hi -
-// delta_crit), the width staged with the group records. Every wait is bounded in GPU time;
-// on a timeout the CTA records where (err[1]: role, barrier, g), stops, waits for its MMAs
-// and copies in flight and frees its tensor memory.
+// previous tile, once the MMAs of the tile two before are done; chunk g's coefficients into
+// stage g % stages as soon as the MMAs of chunk g - stages are done, and its group records
+// into ring slot g % kFMetaStages once the epilogue has read chunk g - kFMetaStages's), thread
+// 0 the MMAs (per chunk ksteps M128 N256 K16 FP16 MMAs into tensor-memory buffer g % 2; it
+// waits only for operands and a free buffer, also across tiles), warps 4-19 the epilogue in
+// two sets taking alternate chunks (set s, buffer s): a set's warp (q = lane quarter, p)
+// reads 128 columns of its 32 cells in two rounds of 64, releases the buffer after the last
+// read and, for the walkers of the groups it read, stores the Eq. 1 flags of its 32 cells as
+// one word each (a walker's flag: the AND of the sign bits of its columns is clear). x_HI,
+// delta T_b and the power spectrum follow in the pencil pass. Chunk counters g run over all
+// chunks of the CTA's tiles. POPS (a mass-dependent efficiency): a column flags where
+// 0 <= D <= t (delta_hi - delta_crit), the width staged with the group records. Every wait is
+// bounded in GPU time; on a timeout the CTA records where (err[1]: role, barrier, g), stops,
+// waits for its MMAs and copies in flight and frees its tensor memory.
 template <bool POPS>
 __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     extern __shared__ __align__(1024) unsigned char sm[];
+    const int S = a.stages;
     unsigned char* As = sm;                                    // [2][a_bytes]
-    unsigned char* Bs = As + 2 * a.a_bytes;                    // [kFStages][b_bytes]
-    unsigned char* Ms = Bs + kFStages * a.b_bytes;             // [kFStages][meta_bytes]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFStages * a.meta_bytes);
+    unsigned char* Bs = As + 2 * a.a_bytes;                    // [S][b_bytes]
+    unsigned char* Ms = Bs + S * a.b_bytes;                    // [kFMetaStages][meta_bytes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFMetaStages * a.meta_bytes);
     uint64_t* barA = bars;                   // [2] A stage landed
     uint64_t* barAe = barA + 2;              // [2] A stage free (MMAs of its tile done)
-    uint64_t* barB = barAe + 2;              // [kFStages] chunk (coefficients + meta) landed
-    uint64_t* barBe = barB + kFStages;       // [kFStages] its MMAs are done
-    uint64_t* barMe = barBe + kFStages;      // [kFStages] the epilogue has read its meta
-    uint64_t* barD = barMe + kFStages;       // [2] accumulator buffer ready
+    uint64_t* barB = barAe + 2;              // [S] coefficient stage landed
+    uint64_t* barBe = barB + kFStagesMax;    // [S] its MMAs are done
+    uint64_t* barM = barBe + kFStagesMax;    // [kFMetaStages] group records landed
+    uint64_t* barMe = barM + kFMetaStages;   // [kFMetaStages] the epilogue has read them
+    uint64_t* barD = barMe + kFMetaStages;   // [2] accumulator buffer ready
     uint64_t* barE = barD + 2;               // [2] accumulator buffer released by the epilogue
     uint64_t* barF = barE + 2;               // MMAs drained (abort path)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(barF + 1);
@@ -858,9 +864,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             tc::mbar_init(barD + s, 1);
             tc::mbar_init(barE + s, kFSetThreads);
         }
-        for (int s = 0; s < kFStages; s++) {
+        for (int s = 0; s < S; s++) {
             tc::mbar_init(barB + s, 1);
             tc::mbar_init(barBe + s, 1);
+        }
+        for (int s = 0; s < kFMetaStages; s++) {
+            tc::mbar_init(barM + s, 1);
             tc::mbar_init(barMe + s, kFSetThreads);
         }
         tc::mbar_init(barF, 1);
@@ -871,9 +880,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     // copy-thread bookkeeping: parity of the phase each copy barrier still owes, or -1
-    int owedA[2] = {-1, -1}, owedB[kFStages];
+    int owedA[2] = {-1, -1}, owedB[kFStagesMax], owedM[kFMetaStages];
 #pragma unroll
-    for (int s = 0; s < kFStages; s++) owedB[s] = -1;
+    for (int s = 0; s < kFStagesMax; s++) owedB[s] = -1;
+#pragma unroll
+    for (int s = 0; s < kFMetaStages; s++) owedM[s] = -1;
 
     if (t == 32 && work) {
         // ---------------- copy thread
@@ -898,19 +909,23 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             for (int c = 0; c < nch; c++) {
                 // the next tile's A operands half-way through this tile's chunks
                 if (c == nch / 2 && it + 1 < my_tiles && !(ok = issue_a(it + 1))) break;
-                const int g = it * nch + c, st = g % kFStages;
-                const uint32_t use = (uint32_t)(g / kFStages);
-                if (use > 0) {
-                    ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kWaitNs, abort);
-                    if (!ok) { record_timeout(a.err, 1, 3, g); break; }
-                    ok = tc::mbar_wait_or_abort(barMe + st, (use - 1) & 1u, kWaitNs, abort);
-                    if (!ok) { record_timeout(a.err, 1, 5, g); break; }
+                const int g = it * nch + c, st = g % S, ms = g % kFMetaStages;
+                const uint32_t use = (uint32_t)(g / S), muse = (uint32_t)(g / kFMetaStages);
+                if (use > 0 && !(ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kWaitNs, abort))) {
+                    record_timeout(a.err, 1, 3, g);
+                    break;
                 }
                 const unsigned char* src = Bz + (size_t)c * (a.b_bytes + a.meta_bytes);
-                tc::mbar_expect_tx(barB + st, a.b_bytes + a.meta_bytes);
+                tc::mbar_expect_tx(barB + st, a.b_bytes);
                 tc::bulk_g2s(Bs + (size_t)st * a.b_bytes, src, a.b_bytes, barB + st);
-                tc::bulk_g2s(Ms + st * a.meta_bytes, src + a.b_bytes, a.meta_bytes, barB + st);
                 owedB[st] = (int)(use & 1u);
+                if (muse > 0 && !(ok = tc::mbar_wait_or_abort(barMe + ms, (muse - 1) & 1u, kWaitNs, abort))) {
+                    record_timeout(a.err, 1, 5, g);
+                    break;
+                }
+                tc::mbar_expect_tx(barM + ms, a.meta_bytes);
+                tc::bulk_g2s(Ms + (size_t)ms * a.meta_bytes, src + a.b_bytes, a.meta_bytes, barM + ms);
+                owedM[ms] = (int)(muse & 1u);
             }
         }
         if (!ok) *abort = 1;
@@ -926,8 +941,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             }
             const uint32_t abase = tc::smem_addr(As + (size_t)as * a.a_bytes);
             for (int c = 0; c < nch; c++) {
-                const int g = it * nch + c, st = g % kFStages, tb = g & 1;
-                ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / kFStages) & 1u, kWaitNs, abort);
+                const int g = it * nch + c, st = g % S, tb = g & 1;
+                ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / S) & 1u, kWaitNs, abort);
                 if (!ok) { record_timeout(a.err, 2, 2, g); break; }
                 if (g >= 2)   // the epilogue of chunk g - 2 has released buffer tb
                     ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((g - 2) >> 1) & 1u, a.free_wait_ns, abort);
@@ -958,16 +973,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             // the first chunk of this tile that the set takes (chunk counters continue across tiles)
             int c = (set - (it * nch) % kFEpiSets + kFEpiSets) % kFEpiSets;
             for (; c < nch; c += kFEpiSets) {
-                const int g = it * nch + c, st = g % kFStages, tb = g & 1;
+                const int g = it * nch + c, ms = g % kFMetaStages, tb = g & 1;
                 const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(g >> 1) & 1u, kWaitNs, abort);
-                const bool okB = okD && tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / kFStages) & 1u, kWaitNs, abort);
-                if (!okB) {
+                const bool okM =
+                    okD && tc::mbar_wait_or_abort(barM + ms, (uint32_t)(g / kFMetaStages) & 1u, kWaitNs, abort);
+                if (!okM) {
                     if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, g);
                     *abort = 1;
                     ok = false;
                     break;
                 }
                 tc::fence_after_sync();
+                const unsigned char* meta = Ms + (size_t)ms * a.meta_bytes;
 #pragma unroll 1
                 for (int r = 0; r < kFRounds; r++) {
                     const int col = p * 64 * kFRounds + r * 64;   // first column of this round
@@ -977,12 +994,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                         tc::fence_before_sync();
                         if (g != a.withhold) tc::mbar_arrive(barE + tb);   // accumulators read: buffer free
                     }
-                    const int4* gm = reinterpret_cast<const int4*>(Ms + st * a.meta_bytes) + col / kGroup;
+                    const int4* gm = reinterpret_cast<const int4*>(meta) + col / kGroup;
                     const int m0 = gm[0].x, m1 = gm[1].x;
                     if constexpr (POPS) {
                         // a column does not flag iff D < 0 or D > width: the sign bit of D | (width - D)
                         // (+inf for an infinite width), then the same AND of sign bits
-                        const float4* wd = reinterpret_cast<const float4*>(Ms + st * a.meta_bytes + kFRecBytes) + col / 4;
+                        const float4* wd = reinterpret_cast<const float4*>(meta + kFRecBytes) + col / 4;
 #pragma unroll
                         for (int k = 0; k < 8; k++) {
                             const float4 wa = wd[k], wb = wd[8 + k];
@@ -1006,7 +1023,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                         if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
                     }
                 }
-                tc::mbar_arrive(barMe + st);   // the group records (and widths) of this chunk are read
+                tc::mbar_arrive(barMe + ms);   // the group records (and widths) of this chunk are read
             }
         }
     }
@@ -1019,8 +1036,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
         } else if (t == 32) {   // wait for every bulk copy that may still land
             for (int s = 0; s < 2; s++)
                 if (owedA[s] >= 0) tc::mbar_wait(barA + s, (uint32_t)owedA[s], kWaitNs);
-            for (int s = 0; s < kFStages; s++)
+            for (int s = 0; s < S; s++)
                 if (owedB[s] >= 0) tc::mbar_wait(barB + s, (uint32_t)owedB[s], kWaitNs);
+            for (int s = 0; s < kFMetaStages; s++)
+                if (owedM[s] >= 0) tc::mbar_wait(barM + s, (uint32_t)owedM[s], kWaitNs);
         }
     }
     __syncthreads();
@@ -1037,14 +1056,17 @@ int f16_slots(const eor_ctx* c) {
     return (c->cfg.max_walkers * per_walker + kFN - 1) / kFN * kFN;
 }
 
-// Dynamic shared memory of the contraction: at least 120 KB, so that one CTA holds an SM (and
-// all of its tensor memory) at every basis size.
-size_t f16_smem(int kslots, bool pops) {
+// Dynamic shared memory of the contraction with `stages` coefficient stages: at least 120 KB,
+// so that one CTA holds an SM (and all of its tensor memory) at every basis size.
+size_t f16_smem(int kslots, bool pops, int stages) {
     const size_t a = (size_t)kFM * kslots * 2, b = (size_t)kFN * kslots * 2;
-    const size_t need =
-        2 * a + kFStages * (b + f16_meta_bytes(pops)) + (4 + 3 * kFStages + 4 + 1) * sizeof(uint64_t) + 16;
+    const size_t need = 2 * a + stages * b + kFMetaStages * (size_t)f16_meta_bytes(pops) +
+                        (4 + 2 * kFStagesMax + 2 * kFMetaStages + 4 + 1) * sizeof(uint64_t) + 16;
     return need > (120u << 10) ? need : (120u << 10);
 }
+
+// Four coefficient stages where they fit in 227 KB, else three.
+int f16_stages(int kslots, bool pops) { return f16_smem(kslots, pops, 4) <= (227u << 10) ? 4 : 3; }
 
 }  // namespace
 
@@ -1060,10 +1082,10 @@ size_t basis_f16_column_slots(const eor_ctx* c) { return (size_t)f16_slots(c); }
 cudaError_t prepare_basis_f16(eor_ctx* c) {
     if (!c->f16) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_basis_ionize_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)f16_smem(c->k16, false));
+                                         (int)f16_smem(c->k16, false, f16_stages(c->k16, false)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_basis_ionize_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)f16_smem(c->k16, true));
+                                 (int)f16_smem(c->k16, true, f16_stages(c->k16, true)));
     return e;
 }
 
@@ -1117,15 +1139,17 @@ cudaError_t launch_basis_ionize_f16(eor_ctx* c) {
     const int tiles_per_z = (int)(c->n3 / kFM);
     const int total = tiles_per_z * c->cfg.n_z;
     const bool pops = c->cfg.efficiency_model != 0;
+    const int stages = f16_stages(c->k16, pops);
     F16Args a{c->d_a16, c->d_b16, c->d_ncols, c->d_fwords, c->d_err, c->cfg.n_z, f16_slots(c) / kFN, tiles_per_z,
               c->k16 / 16, (uint32_t)(kFM * c->k16 * 2), (uint32_t)(kFN * c->k16 * 2), f16_sbo(c->k16),
-              f16_meta_bytes(pops), (long long)c->n3, c->dbg_withhold, c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
+              f16_meta_bytes(pops), stages, (long long)c->n3, c->dbg_withhold,
+              c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
     const int grid = total < c->num_sms ? total : c->num_sms;
     trace_begin(c, kKBasis);
     if (pops)
-        k_basis_ionize_f16<true><<<grid, kFThreads, f16_smem(c->k16, true), c->stream>>>(a);
+        k_basis_ionize_f16<true><<<grid, kFThreads, f16_smem(c->k16, true, stages), c->stream>>>(a);
     else
-        k_basis_ionize_f16<false><<<grid, kFThreads, f16_smem(c->k16, false), c->stream>>>(a);
+        k_basis_ionize_f16<false><<<grid, kFThreads, f16_smem(c->k16, false, stages), c->stream>>>(a);
     trace_end(c);
     return cudaGetLastError();
 }

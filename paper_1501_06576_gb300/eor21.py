@@ -22,7 +22,7 @@ MAX_Z, MAX_BINS, MAX_RADII = 8, 64, 64
 EXPORTS = ("eor_default_config", "eor_create", "eor_init_boxes", "eor_set_efficiency", "eor_set_params",
            "eor_run_ionization",
            "eor_power_spectrum", "eor_chi2", "eor_likelihood", "eor_filtered_density",
-           "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_ps_split", "eor_get_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_basis_window", "eor_contraction_info", "eor_debug_withhold", "eor_trace",
+           "eor_density_spectrum", "eor_density_box", "eor_walker_ladder", "eor_box_power_spectrum", "eor_set_tuning", "eor_set_ps_split", "eor_set_ps_streams", "eor_get_tuning", "eor_autotune", "eor_noise_sigma", "eor_set_method", "eor_basis_info", "eor_basis_window", "eor_contraction_info", "eor_debug_withhold", "eor_trace",
            "eor_trace_read", "eor_kernel_class_name", "eor_launch_count", "eor_box_power_spectrum_noalloc",
            "eor_tensor_core_check", "eor_last_error", "eor_version", "eor_destroy",
            "eor_emu_default_config", "eor_emu_create", "eor_emu_n_params", "eor_emu_set_data", "eor_emu_train",
@@ -112,7 +112,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "eor_box_power_spectrum": (I, [P, P, P, P, P, I]),
         "eor_set_tuning": (I, [P, I, I, I]),
         "eor_set_ps_split": (I, [P, I]),
-        "eor_get_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "eor_set_ps_streams": (I, [P, I]),
+        "eor_get_tuning": (I, [P] + [ctypes.POINTER(I)] * 5),
         "eor_set_method": (I, [P, I]),
         "eor_autotune": (I, [P, P, I, P, P, I, P, P, P, P, I]),
         "eor_noise_sigma": (I, [P, P, P, D, P, I]),
@@ -355,11 +356,13 @@ class Context:
     def eor_set_ps_split(self, split: int):
         self._check(self.lib.eor_set_ps_split(self.handle, int(split)))
 
+    def eor_set_ps_streams(self, streams: int):
+        self._check(self.lib.eor_set_ps_streams(self.handle, int(streams)))
+
     def eor_get_tuning(self) -> dict:
-        g, p, t, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.eor_get_tuning(self.handle, ctypes.byref(g), ctypes.byref(p), ctypes.byref(t),
-                                            ctypes.byref(sp)))
-        return {"group": g.value, "pairs": p.value, "plane_threads": t.value, "ps_split": sp.value}
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(self.lib.eor_get_tuning(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("group", "pairs", "plane_threads", "ps_split", "ps_streams"), (x.value for x in v)))
 
     def eor_autotune(self, params, mock_d2, sigma, reps: int = 3):
         """Pick the fastest launch schedule for these walkers; returns (group, pairs,
@@ -440,6 +443,7 @@ class Context:
     set_method = eor_set_method
     autotune = eor_autotune
     set_ps_split = eor_set_ps_split
+    set_ps_streams = eor_set_ps_streams
     get_tuning = eor_get_tuning
     noise_sigma = eor_noise_sigma
     basis_info = eor_basis_info

@@ -71,8 +71,15 @@ def test_power_spectrum_plane_tiling_does_not_change_results():
         out[split] = ctx.likelihood(params, mock, sigma, want_d2=True)
     np.testing.assert_allclose(out[2][1], out[1][1], rtol=2e-6, equal_nan=True)
     np.testing.assert_allclose(out[2][0], out[1][0], rtol=1e-5)
+    # the spectrum's passes on one stream in turn, or overlapped on two: the same kernels and
+    # sums (up to the order of the FP64 additions across planes)
+    for streams in (1, 2):
+        ctx.set_ps_streams(streams)
+        assert ctx.get_tuning()["ps_streams"] == streams
+        d2 = ctx.likelihood(params, mock, sigma, want_d2=True)[1]
+        np.testing.assert_allclose(d2, out[2][1], rtol=1e-12, equal_nan=True)
     ctx.autotune(params, mock, sigma, reps=1)
-    assert ctx.get_tuning()["ps_split"] in (1, 2)
+    assert ctx.get_tuning()["ps_split"] in (1, 2) and ctx.get_tuning()["ps_streams"] in (1, 2)
     ctx.close()
     small = eor21.Context(n=64, box_mpc=100.0, z=zs, max_walkers=1)
     with pytest.raises(eor21.EorError) as ei:
