@@ -801,9 +801,9 @@ def main():
                 if contract_kind == eor21.EOR_CONTRACT_FP16:
                     peak, peak_kind = fp16_peak_tflops()
                     executed = 2 * k_slots * N ** 3 * f16_column_chunks(ladders) * 256 * len(ZS)
-                    tf32, _ = tf32_peak_tflops()
+                    tf32_peak, _ = tf32_peak_tflops()
                     extra = {"executed_fp16_tflops": executed * args.steps / launches_c / (avg_ms / 1e3) / 1e12,
-                             "frac_of_tf32_peak": achieved / tf32, "k_slots": k_slots}
+                             "frac_of_tf32_peak": achieved / tf32_peak, "k_slots": k_slots}
                     bound = "tensor"
                 elif contract_kind == eor21.EOR_CONTRACT_TF32:
                     peak, peak_kind = tf32_peak_tflops()

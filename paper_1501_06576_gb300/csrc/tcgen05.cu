@@ -644,6 +644,7 @@ constexpr int kFN = 256;                        // coefficient columns per chunk
 constexpr int kFKMax = 96;                      // FP16 K slots at most (six MMA steps of 16)
 constexpr int kFStagesMax = 4;                  // coefficient chunks in flight (4, or 3 when 4 do not fit)
 constexpr int kFMetaStages = 8;                 // group records (and widths) of chunks in flight
+constexpr int kFMetaLead = 4;                   // records issued this many chunks ahead of the coefficients
 constexpr int kFGroups = kFN / kGroup;          // walker groups per chunk
 constexpr uint32_t kFRecBytes = kFGroups * 16;  // group records
 constexpr uint32_t kFWidthBytes = kFN * 4;      // per column t (delta_hi - delta_crit) (mass-dependent efficiency)
@@ -829,10 +830,10 @@ struct F16Args {
 // 0 <= D <= t (delta_hi - delta_crit), the width staged with the group records. Every wait is
 // bounded in GPU time; on a timeout the CTA records where (err[1]: role, barrier, g), stops,
 // waits for its MMAs and copies in flight and frees its tensor memory.
-template <bool POPS>
+template <bool POPS, int S>
 __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
+    static_assert(S == 3 || S == 4, "coefficient stages");
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int S = a.stages;
     unsigned char* As = sm;                                    // [2][a_bytes]
     unsigned char* Bs = As + 2 * a.a_bytes;                    // [S][b_bytes]
     unsigned char* Ms = Bs + S * a.b_bytes;                    // [kFMetaStages][meta_bytes]
@@ -879,15 +880,17 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    // copy-thread bookkeeping: parity of the phase each copy barrier still owes, or -1
-    int owedA[2] = {-1, -1}, owedB[kFStagesMax], owedM[kFMetaStages];
-#pragma unroll
-    for (int s = 0; s < kFStagesMax; s++) owedB[s] = -1;
-#pragma unroll
-    for (int s = 0; s < kFMetaStages; s++) owedM[s] = -1;
+    // copy-thread bookkeeping (registers): bit 2s of a mask = stage s has a copy that may still
+    // land, bit 2s + 1 = the parity of the phase it completes
+    uint32_t owedA = 0, owedB = 0, owedM = 0;
 
     if (t == 32 && work) {
-        // ---------------- copy thread
+        // ---------------- copy thread (incremental counters: no division in the loop)
+        const size_t chunk_bytes = (size_t)a.b_bytes + a.meta_bytes;
+        auto tile_base = [&](int it) {
+            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+            return a.B + (size_t)(tile / a.tiles_per_z) * a.chunks_per_z * chunk_bytes;
+        };
         // A operands of tile j into stage j % 2 once the MMAs of tile j - 2 are done
         auto issue_a = [&](int j) -> bool {
             const int as = j & 1;
@@ -898,34 +901,52 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             const int tile = (int)blockIdx.x + j * (int)gridDim.x;
             tc::mbar_expect_tx(barA + as, a.a_bytes);
             tc::bulk_g2s(As + (size_t)as * a.a_bytes, a.A + (size_t)tile * a.a_bytes, a.a_bytes, barA + as);
-            owedA[as] = (j >> 1) & 1;
+            owedA = (owedA & ~(3u << (2 * as))) | ((1u | ((uint32_t)(j >> 1) & 1u) << 1) << (2 * as));
+            return true;
+        };
+        // group records: a cursor (tile mit, chunk mc, counter mg) kFMetaLead chunks ahead
+        const int total_g = my_tiles * nch;
+        int mit = 0, mc = 0, mg = 0;
+        const unsigned char* mbase = tile_base(0);
+        auto issue_m = [&]() -> bool {
+            const int ms = mg & (kFMetaStages - 1);
+            const uint32_t muse = (uint32_t)mg / kFMetaStages;
+            if (muse > 0 && !tc::mbar_wait_or_abort(barMe + ms, (muse - 1) & 1u, kWaitNs, abort)) {
+                record_timeout(a.err, 1, 5, mg);
+                return false;
+            }
+            tc::mbar_expect_tx(barM + ms, a.meta_bytes);
+            tc::bulk_g2s(Ms + (size_t)ms * a.meta_bytes, mbase + (size_t)mc * chunk_bytes + a.b_bytes, a.meta_bytes,
+                         barM + ms);
+            owedM = (owedM & ~(3u << (2 * ms))) | ((1u | (muse & 1u) << 1) << (2 * ms));
+            mg++;
+            if (++mc == nch) {
+                mc = 0;
+                if (++mit < my_tiles) mbase = tile_base(mit);
+            }
             return true;
         };
         bool ok = issue_a(0);
+        while (ok && mg < kFMetaLead && mg < total_g) ok = issue_m();
+        int st = 0;
+        uint32_t use = 0;   // chunk g = it nch + c goes to stage st, the use-th time that stage is filled
         for (int it = 0; it < my_tiles && ok; it++) {
-            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-            const int zi = tile / a.tiles_per_z;
-            const unsigned char* Bz = a.B + (size_t)zi * a.chunks_per_z * (a.b_bytes + a.meta_bytes);
+            const unsigned char* Bz = tile_base(it);
             for (int c = 0; c < nch; c++) {
                 // the next tile's A operands half-way through this tile's chunks
                 if (c == nch / 2 && it + 1 < my_tiles && !(ok = issue_a(it + 1))) break;
-                const int g = it * nch + c, st = g % S, ms = g % kFMetaStages;
-                const uint32_t use = (uint32_t)(g / S), muse = (uint32_t)(g / kFMetaStages);
+                if (mg < total_g && !(ok = issue_m())) break;
                 if (use > 0 && !(ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kWaitNs, abort))) {
-                    record_timeout(a.err, 1, 3, g);
+                    record_timeout(a.err, 1, 3, it * nch + c);
                     break;
                 }
-                const unsigned char* src = Bz + (size_t)c * (a.b_bytes + a.meta_bytes);
                 tc::mbar_expect_tx(barB + st, a.b_bytes);
-                tc::bulk_g2s(Bs + (size_t)st * a.b_bytes, src, a.b_bytes, barB + st);
-                owedB[st] = (int)(use & 1u);
-                if (muse > 0 && !(ok = tc::mbar_wait_or_abort(barMe + ms, (muse - 1) & 1u, kWaitNs, abort))) {
-                    record_timeout(a.err, 1, 5, g);
-                    break;
+                tc::bulk_g2s(Bs + (size_t)st * a.b_bytes, Bz + (size_t)c * chunk_bytes, a.b_bytes, barB + st);
+                owedB = (owedB & ~(3u << (2 * st))) | ((1u | (use & 1u) << 1) << (2 * st));
+                if (++st == S) {
+                    st = 0;
+                    use++;
                 }
-                tc::mbar_expect_tx(barM + ms, a.meta_bytes);
-                tc::bulk_g2s(Ms + (size_t)ms * a.meta_bytes, src + a.b_bytes, a.meta_bytes, barM + ms);
-                owedM[ms] = (int)(muse & 1u);
             }
         }
         if (!ok) *abort = 1;
@@ -933,16 +954,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
         // ---------------- MMA thread
         const uint32_t idesc = tc::idesc_f16(kFM, kFN);
         bool ok = true;
+        int st = 0, g = 0;
+        uint32_t use = 0;   // phase parity of stage st is use & 1
         for (int it = 0; it < my_tiles && ok; it++) {
             const int as = it & 1;
             if (!(ok = tc::mbar_wait_or_abort(barA + as, (uint32_t)(it >> 1) & 1u, kWaitNs, abort))) {
-                record_timeout(a.err, 2, 1, it * nch);
+                record_timeout(a.err, 2, 1, g);
                 break;
             }
             const uint32_t abase = tc::smem_addr(As + (size_t)as * a.a_bytes);
-            for (int c = 0; c < nch; c++) {
-                const int g = it * nch + c, st = g % S, tb = g & 1;
-                ok = tc::mbar_wait_or_abort(barB + st, (uint32_t)(g / S) & 1u, kWaitNs, abort);
+            for (int c = 0; c < nch; c++, g++) {
+                const int tb = g & 1;
+                ok = tc::mbar_wait_or_abort(barB + st, use & 1u, kWaitNs, abort);
                 if (!ok) { record_timeout(a.err, 2, 2, g); break; }
                 if (g >= 2)   // the epilogue of chunk g - 2 has released buffer tb
                     ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((g - 2) >> 1) & 1u, a.free_wait_ns, abort);
@@ -956,6 +979,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                 }
                 tc::mma_commit(barD + tb);    // accumulators ready for the epilogue
                 tc::mma_commit(barBe + st);   // coefficient stage free for the copy thread
+                if (++st == S) {
+                    st = 0;
+                    use++;
+                }
             }
             if (ok) tc::mma_commit(barAe + as);   // the tile's A stage may be refilled
         }
@@ -1035,11 +1062,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             tc::mbar_wait(barF, 0, kWaitNs);
         } else if (t == 32) {   // wait for every bulk copy that may still land
             for (int s = 0; s < 2; s++)
-                if (owedA[s] >= 0) tc::mbar_wait(barA + s, (uint32_t)owedA[s], kWaitNs);
+                if ((owedA >> (2 * s)) & 1u) tc::mbar_wait(barA + s, (owedA >> (2 * s + 1)) & 1u, kWaitNs);
             for (int s = 0; s < S; s++)
-                if (owedB[s] >= 0) tc::mbar_wait(barB + s, (uint32_t)owedB[s], kWaitNs);
+                if ((owedB >> (2 * s)) & 1u) tc::mbar_wait(barB + s, (owedB >> (2 * s + 1)) & 1u, kWaitNs);
             for (int s = 0; s < kFMetaStages; s++)
-                if (owedM[s] >= 0) tc::mbar_wait(barM + s, (uint32_t)owedM[s], kWaitNs);
+                if ((owedM >> (2 * s)) & 1u) tc::mbar_wait(barM + s, (owedM >> (2 * s + 1)) & 1u, kWaitNs);
         }
     }
     __syncthreads();
@@ -1081,11 +1108,14 @@ size_t basis_f16_column_slots(const eor_ctx* c) { return (size_t)f16_slots(c); }
 
 cudaError_t prepare_basis_f16(eor_ctx* c) {
     if (!c->f16) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_basis_ionize_f16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)f16_smem(c->k16, false, f16_stages(c->k16, false)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_basis_ionize_f16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)f16_smem(c->k16, true, f16_stages(c->k16, true)));
+    cudaError_t e = cudaSuccess;
+    for (int pops = 0; pops < 2 && e == cudaSuccess; pops++) {
+        const int st = f16_stages(c->k16, pops != 0);
+        const int bytes = (int)f16_smem(c->k16, pops != 0, st);
+        auto k = pops ? (st == 4 ? k_basis_ionize_f16<true, 4> : k_basis_ionize_f16<true, 3>)
+                      : (st == 4 ? k_basis_ionize_f16<false, 4> : k_basis_ionize_f16<false, 3>);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
     return e;
 }
 
@@ -1146,10 +1176,9 @@ cudaError_t launch_basis_ionize_f16(eor_ctx* c) {
               c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
     const int grid = total < c->num_sms ? total : c->num_sms;
     trace_begin(c, kKBasis);
-    if (pops)
-        k_basis_ionize_f16<true><<<grid, kFThreads, f16_smem(c->k16, true, stages), c->stream>>>(a);
-    else
-        k_basis_ionize_f16<false><<<grid, kFThreads, f16_smem(c->k16, false, stages), c->stream>>>(a);
+    auto k = pops ? (stages == 4 ? k_basis_ionize_f16<true, 4> : k_basis_ionize_f16<true, 3>)
+                  : (stages == 4 ? k_basis_ionize_f16<false, 4> : k_basis_ionize_f16<false, 3>);
+    k<<<grid, kFThreads, f16_smem(c->k16, pops, stages), c->stream>>>(a);
     trace_end(c);
     return cudaGetLastError();
 }
