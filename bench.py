@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--no-direct", action="store_true", help="skip timing the per-radius FFT method")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule (profiling runs)")
-    ap.add_argument("--ps-split", type=int, default=0, choices=[0, 1, 2],
-                    help="force the power spectrum's plane tiling after the autotuner (0: keep its choice)")
+    ap.add_argument("--ps-split", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="force the power spectrum's tiling after the autotuner (0 slab passes, 1 planes, "
+                         "2 plane clusters; -1: keep its choice)")
     ap.add_argument("--no-emulator", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-mcmc", action="store_true", help="skip the device-side sampler leg")
     ap.add_argument("--mcmc-steps", type=int, default=10)
@@ -652,10 +653,10 @@ def main():
         # launch schedule picked by the library's autotuner on these walkers (untimed set-up)
         if not args.no_autotune:
             ctx.autotune(d_params, d_mock, d_sigma, reps=3)
-        if args.ps_split:
+        if args.ps_split >= 0:
             ctx.set_ps_split(args.ps_split)
         schedule = ctx.get_tuning()
-        if args.ps_split:
+        if args.ps_split >= 0:
             schedule["forced"] = "ps_split"
         ctx.trace(not args.no_trace)
         for _ in range(args.warmup):
@@ -817,12 +818,16 @@ def main():
                                      "unit_def": "one (walker, redshift, radius) over all cells",
                                      "units_per_launch": units, "avg_launch_ms": avg_ms, **extra}
             elif cls in ("forward_fft", "ps_plane"):
-                # per (walker, redshift): the pencil pass writes the half spectrum and reads the flag
-                # words and its share of delta and delta at R_cell; the plane pass reads the planes
-                # that hold a binned mode
+                # per (walker, redshift): the first pass (slab or pencil) reads the flag words and its
+                # share of delta and delta at R_cell and writes the kz planes (the slab pass only those
+                # with a binned mode, the pencil pass all n/2 + 1); the second pass (x lines or planes)
+                # reads the planes that hold a binned mode
+                slab = schedule.get("ps_split") == 0
                 if cls == "forward_fft":
-                    per_unit = nspec_b + N ** 3 // 8 + 2 * N ** 3 * 4 // W
-                    udef = "one (walker, redshift): half spectrum write + flag words + delta, delta_Rcell share"
+                    per_unit = (planes * N * N * 8 if slab else nspec_b) + N ** 3 // 8 + 2 * N ** 3 * 4 // W
+                    udef = ("one (walker, redshift): " + (f"write of the {planes} binned kz planes" if slab else
+                                                          "half spectrum write") +
+                            " + flag words + delta, delta_Rcell share")
                 else:
                     per_unit = planes * N * N * 8
                     udef = f"one (walker, redshift): read of the {planes} kz planes with a binned mode"

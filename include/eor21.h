@@ -209,11 +209,17 @@ int eor_noise_sigma(eor_ctx* ctx, const double* mock_d2, const float* thermal, d
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
 
-/* The plane tiling of the power spectrum's 2D transform at n = 128: split 1 = one CTA per
- * 128 x 128 plane (132 KB of shared memory), split 2 = a cluster of two CTAs per plane (each
- * holds 64 rows, transforms them, then 64 columns reading the other half through distributed
- * shared memory; two such CTAs share an SM). Default 2; EOR_ENOTSUP for 2 at other n. Drops
- * the captured graph. eor_get_tuning reads the current schedule (each pointer optional). */
+/* The tiling of the power spectrum's 3D transform. split 0 (default; n <= 128, the basis
+ * methods) = slab passes: one CTA per x slab forms the real input (delta T_b from the flag
+ * contraction's flags, or the stored boxes), transforms it along z and y in shared memory
+ * (about 68 KB at n = 128, three CTAs per SM), then one CTA per (kz plane, 32 y slots)
+ * transforms along x and adds the shell sums. split 1 = a pencil pass along z, then one CTA
+ * per n x n kz plane (132 KB at n = 128); split 2 (n = 128) = the same with a cluster of two
+ * CTAs per plane (each holds 64 rows, transforms them, then 64 columns reading the other half
+ * through distributed shared memory). The direct method always runs split 1 or 2 (0 reads as
+ * 1 there); n = 256 runs its own row and column passes. EOR_ENOTSUP for 2 at n != 128 and for
+ * 0 at n > 128; EOR_EINVAL outside 0..2. Drops the captured graph. eor_get_tuning reads the
+ * current schedule (each pointer optional; ps_split reads 1 where the choice does not apply). */
 int eor_set_ps_split(eor_ctx* ctx, int split);
 /* Streams of the basis methods' power spectrum: 2 (default) = the plane pass of a batch of
  * (walker, redshift) pairs runs on a second stream of the context while the pencil pass of the
@@ -223,13 +229,15 @@ int eor_set_ps_split(eor_ctx* ctx, int split);
 int eor_set_ps_streams(eor_ctx* ctx, int streams);
 int eor_get_tuning(const eor_ctx* ctx, int* group, int* pairs, int* plane_threads, int* ps_split, int* ps_streams);
 
-/* Autotuner of the launch schedule (results do not depend on it): times eor_likelihood on
+/* Autotuner of the launch schedule (results depend on it only through the FP32 rounding of
+ * the spectrum's transforms and partial sums): times eor_likelihood on
  * these walkers (arguments as there, n_walkers <= max_walkers) with CUDA events on the
  * context's stream, `reps` graph replays per candidate after one warm-up, over the
- * candidates of the current method -- pairs in {4, 8, 16, 32} x the spectrum's plane tiling
- * (128^3 grids: split 2, or split 1 with plane_threads 512 or 1024; split 1 and 512
- * otherwise) x ps_streams in {2, 1}, and for EOR_METHOD_DIRECT (one stream) also group in
- * {4, 8, 16} and plane_threads with both splits -- and keeps the fastest (eor_set_tuning,
+ * candidates of the current method -- pairs in {4, 8, 16, 32} x the spectrum's tiling
+ * (split 0 at n <= 128; 128^3 grids also split 2, and split 1 with plane_threads 512 or
+ * 1024; split 1 and 512 otherwise) x ps_streams in {2, 1}, and for EOR_METHOD_DIRECT (one
+ * stream, splits 1 and 2) also group in {4, 8, 16} and plane_threads -- and keeps the
+ * fastest (eor_set_tuning,
  * eor_set_ps_split, eor_set_ps_streams). group, pairs, plane_threads and ms (mean
  * milliseconds of one call) receive the choice, each optional; eor_get_tuning gives the
  * rest. Tracing is off while it runs and is restored afterwards. */

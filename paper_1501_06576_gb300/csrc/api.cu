@@ -711,11 +711,12 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     const bool direct = c->tune.method == eor::kMethodDirect;
     for (int streams : {2, 1}) {
         if (streams == 2 && direct) continue;   // the direct method's passes run in one stream
-        for (int split : {2, 1}) {
+        for (int split : {0, 2, 1}) {
+            if (split == 0 && (direct || c->n > 128)) continue;   // slab passes: the basis methods' spectrum
             if (split == 2 && c->n != 128) continue;   // the cluster form of the spectrum's plane pass
             for (int th : {512, 1024}) {
                 if (th == 1024 && c->n != 128) continue;
-                if (th == 1024 && split == 2 && !direct) continue;   // the CTA size then changes no kernel of the step
+                if (th == 1024 && split != 1 && !direct) continue;   // the CTA size then changes no kernel of the step
                 for (int p : pairs_list) {
                     if (direct)
                         for (int gsz : groups_direct) cands.push_back({gsz, p, th, split, streams});
@@ -796,8 +797,9 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
 
 int eor_set_ps_split(eor_ctx* c, int split) {
     if (!c) return EOR_EINVAL;
-    if (split != 1 && split != 2) return fail(c, EOR_EINVAL, "ps_split must be 1 or 2");
+    if (split < 0 || split > 2) return fail(c, EOR_EINVAL, "ps_split must be 0, 1 or 2");
     if (split == 2 && c->n != 128) return fail(c, EOR_ENOTSUP, "the two-CTA plane pass serves n = 128 only");
+    if (split == 0 && c->n > 128) return fail(c, EOR_ENOTSUP, "the slab passes serve n <= 128 only");
     CK(cudaStreamSynchronize(c->stream), "ps split");
     c->tune.ps_split = split;
     if (c->graph_exec) {
@@ -826,7 +828,7 @@ int eor_get_tuning(const eor_ctx* c, int* group, int* pairs, int* plane_threads,
     if (group) *group = c->tune.group;
     if (pairs) *pairs = c->tune.pairs;
     if (plane_threads) *plane_threads = c->tune.plane_threads;
-    if (ps_split) *ps_split = c->n == 128 ? c->tune.ps_split : 1;
+    if (ps_split) *ps_split = c->n > 128 || (c->n < 128 && c->tune.ps_split == 2) ? 1 : c->tune.ps_split;
     if (ps_streams) *ps_streams = c->tune.ps_streams;
     return EOR_OK;
 }

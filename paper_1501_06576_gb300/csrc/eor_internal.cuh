@@ -114,7 +114,7 @@ struct Tuning {
     int pairs;          // (walker, redshift) pairs in flight (P)
     int plane_threads;  // CTA size of the 128^3 plane kernels (512 or 1024)
     int method;         // kMethodBasis, kMethodDirect, kMethodBasisSimt or kMethodBasisTf32
-    int ps_split;       // CTAs per 128 x 128 plane of the power spectrum: 1, or 2 (a cluster)
+    int ps_split;       // spectrum tiling: 0 slab + x-line passes (n <= 128), 1 one CTA per plane, 2 a cluster (n = 128)
     int ps_streams;     // 2: the spectrum's plane passes overlap the next batch's pencil pass; 1: in turn
 };
 
@@ -131,7 +131,7 @@ struct eor_ctx {
     int n = 0, nh = 0, n_m2 = 0, max_radii = 0;
     size_t n3 = 0, nspec = 0;
     eor::CosmoParams cosmo{};
-    eor::Tuning tune{8, 16, 512, eor::kMethodBasis, 2, 2};
+    eor::Tuning tune{8, 16, 512, eor::kMethodBasis, 0, 2};
 
     // device buffers
     float* d_delta = nullptr;        // [n_z][n^3]

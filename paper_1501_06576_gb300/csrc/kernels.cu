@@ -206,11 +206,28 @@ struct PSArgs {
 
 constexpr int kPrivBins = 16;   // bins kept in per-thread shared-memory slots
 
+// The CTA's shell sums from the per-thread slots priv[b][T]: warp w takes bins w, w + T/32,
+// ...; each lane adds its slots, then a shuffle tree, in FP32 (this GPU issues FP64 at a few
+// operations per clock per SM: a per-slot FP64 sum cost as much as the transforms), and the
+// CTA's sum per bin goes to s_bins in FP64 for the global accumulation. The order is fixed, so
+// the sums are reproducible; their rounding stays below 1e-5 relative per bin.
+template <int T>
+__device__ __forceinline__ void bin_sums(const float* priv, int n_bins, double* s_bins) {
+    constexpr int WARPS = T / 32 > 0 ? T / 32 : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x / 32;
+    for (int b = warp; b < n_bins; b += WARPS) {
+        float sum = 0.0f;
+        for (int k = lane; k < T; k += 32) sum += priv[b * T + k];
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) s_bins[b] = (double)sum;
+    }
+}
+
 // Forward 2D FFT of one kz plane of delta T_b's z-transformed box, then the shell sums
 // S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2: the conjugate half). Each thread
 // first sums its own modes per bin in FP32 (at most 32 modes each) in private shared-memory
-// slots; the slots of all threads are then added in FP64 in a fixed order, and the plane's
-// FP64 sums go to the global shell sums.
+// slots; bin_sums adds the slots of all threads in a fixed order, and the plane's sums go to
+// the global FP64 shell sums.
 template <int N, int T>
 __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) {
     using P = Plane<N, T>;
@@ -255,15 +272,7 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
     }
     __syncthreads();
     if (priv_ok) {
-        // warp w adds the slots of bins w, w + warps, ... in FP64, lanes then tree
-        constexpr int WARPS = P::THREADS / 32 > 0 ? P::THREADS / 32 : 1;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x / 32;
-        for (int b = warp; b < a.n_bins; b += WARPS) {
-            double sum = 0.0;
-            for (int i = lane; i < P::THREADS; i += 32) sum += (double)priv[b * P::THREADS + i];
-            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-            if (lane == 0) s_bins[b] = sum;
-        }
+        bin_sums<P::THREADS>(priv, a.n_bins, s_bins);
         __syncthreads();
     }
     for (int b = threadIdx.x; b < a.n_bins; b += P::THREADS)
@@ -389,16 +398,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPs2Threads, 2) k_pl
         }
     }
     __syncthreads();
-    // bin sums: warp w adds the slots of bins w, w + 16, ... in FP64, lanes then a tree
-    const int lane = t & 31, warp = t >> 5;
-    if (valid) {
-        for (int b = warp; b < a.n_bins; b += kPs2Threads / 32) {
-            double sum = 0.0;
-            for (int k = lane; k < kPs2Threads; k += 32) sum += (double)priv[b * kPs2Threads + k];
-            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-            if (lane == 0) s_bins[b] = sum;
-        }
-    }
+    if (valid) bin_sums<kPs2Threads>(priv, a.n_bins, s_bins);
     __syncthreads();
     if (valid)
         for (int b = t; b < a.n_bins; b += kPs2Threads)
@@ -555,14 +555,7 @@ __global__ void __launch_bounds__(kLThreads) k_lines_cols(LineArgs a) {
         }
         __syncthreads();
         if (priv_ok) {
-            constexpr int WARPS = kLThreads / 32;
-            const int lane = threadIdx.x & 31, warp = threadIdx.x / 32;
-            for (int b = warp; b < a.n_bins; b += WARPS) {
-                double sum = 0.0;
-                for (int k = lane; k < kLThreads; k += 32) sum += (double)priv[b * kLThreads + k];
-                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                if (lane == 0) s_bins[b] = sum;
-            }
+            bin_sums<kLThreads>(priv, a.n_bins, s_bins);
             __syncthreads();
         }
         const int pair = a.pair0 + slot;
@@ -1004,6 +997,322 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_density(const flo
     pencil_store_real<N>(s, out + ((size_t)x * N + y0) * N);
 }
 
+// ------------------------------------------------------------------ slab passes of the spectrum
+//
+// The power spectrum's 3D transform at n <= 128 as two passes, each CTA small enough that
+// several share an SM (and the two passes of consecutive batches share SMs on two streams):
+//   slab pass  — one CTA per (x slab, pair): the slab's n x n real values (rows y, columns z)
+//                sit in shared memory as n rows of M + 1 complex values (M = n / 2; the odd
+//                row stride keeps every column and row walk conflict-free). The CTA forms the
+//                real input (delta T_b from the Eq. 1 flags, or a stored box), transforms
+//                along z (an M-point complex FFT of the packed (even, odd) pairs, then the
+//                real-to-half-complex split), then along y, all in place, and writes planes
+//                kz < planes of [kz][x][y slot];
+//   x-line pass — one CTA per (kz plane, 32 y slots, pair): the transform along x, then the
+//                shell sums as in k_plane_ps.
+// In-place two-step transforms leave their outputs in a permuted order, which only relabels
+// the modes: after the z transform kz = k1 + P1 k2 sits in column P2 k1 + k2 (kz = M in the
+// extra column M), after the y transform ky = k1 + R1 k2 in row slot R2 k1 + k2.
+
+template <int N>
+struct Slab {
+    static constexpr int M = N / 2, ZS = M + 1;                   // row stride (float2), odd
+    static constexpr int P1 = Split<M>::R1, P2 = Split<M>::R2;   // the z transform (M points)
+    static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;   // the y transform (N points)
+    static constexpr int THREADS = N * N / 4 < 256 ? N * N / 4 : 256;
+    static constexpr size_t SMEM = (size_t)N * ZS * sizeof(float2) + N * sizeof(float2);
+};
+
+template <int N>
+__device__ __forceinline__ int slab_col(int kz) {
+    using S = Slab<N>;
+    return kz == S::M ? S::M : S::P2 * (kz % S::P1) + kz / S::P1;
+}
+
+// ky (or kx) held by row slot r after an in-place two-step N-point transform
+template <int N>
+__device__ __forceinline__ int slot_k(int r) {
+    return r / Split<N>::R2 + Split<N>::R1 * (r % Split<N>::R2);
+}
+
+struct SlabArgs {
+    const uint32_t* fwords;     // flag contraction: [pair][n3 / 32] Eq. 1 flags above R_cell
+    const PairInfo* pairs;
+    const float* delta;         // brightness base [n_z][n3]
+    const float* dcell;         // [n_z][n3] delta at R_cell
+    float* xhi_out;             // optional [pair][n3]
+    unsigned long long* xq;     // [pair] fixed-point (2^23) sums of x_HI
+    const float* ftab;          // [pair][kFTab] with a mass-dependent efficiency, else nullptr
+    const float* box;           // stored boxes [pair][n3] (the other methods' delta T_b)
+    float2* dst;                // [slot][nh][n][n]: planes kz < planes, [kz][x][y slot]
+    int pair0, n_pairs, planes;
+    float delta_c;
+};
+
+// One radix step of an in-place two-step transform over the R elements e[s * stride]
+// (s = first + step * j, j < R): DFT over j, then the twiddles w_N^(tw_mul * i * k1), the
+// outputs back into the same slots (slot first + step * k1).
+template <int N, int R, int DIR>
+__device__ __forceinline__ void ip_stage1(float2* e, int stride, int step, const float2* tw, int i, int tw_mul) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; j++) v[j] = e[(step * j) * stride];
+    dft_reg<R, DIR>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R; k1++) v[k1] = cmul(v[k1], tw_get<N, DIR>(tw, tw_mul * i * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < R; k1++) e[(step * k1) * stride] = v[k1];
+}
+
+// The second step: DFT over the R consecutive slots e[j * stride], outputs back in place.
+template <int R, int DIR>
+__device__ __forceinline__ void ip_stage2(float2* e, int stride) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; j++) v[j] = e[j * stride];
+    dft_reg<R, DIR>(v);
+#pragma unroll
+    for (int k = 0; k < R; k++) e[k * stride] = v[k];
+}
+
+// The slab pass for pairs pair0 .. pair0 + gridDim.y - 1, slab x = blockIdx.x. BRIGHT: per
+// cell x_HI = 0 where a radius above R_cell flagged it (Eq. 1), else 1 - min(1, zeta f_coll(R_cell))
+// with f_coll = erfc((delta_c - delta_Rcell) / sqrt(2 s^2)) (1 where delta_Rcell >= delta_c;
+// x_HI = 1 where s^2 <= 0) (Sec. 2.1), or with a mass-dependent efficiency 1 - min(1, F) from
+// the pair's table of the efficiency-weighted collapsed fraction at nu = delta_c - delta_Rcell;
+// delta T_b = T0 x_HI (1 + delta) (Sec. 2.2), never stored; the pair's x_HI sum is exact (fixed
+// point 2^-23, integer warp sums and 64-bit atomics). Otherwise the input is the pair's stored box.
+template <int N, bool BRIGHT>
+__global__ void __launch_bounds__(Slab<N>::THREADS, 3) k_slab_ps(SlabArgs a) {
+    using S = Slab<N>;
+    constexpr int T = S::THREADS, NH = S::M + 1, ZS = S::ZS;
+    constexpr int V = N * N / 4;                     // float4 per slab
+    constexpr int PER = V / T;                       // float4 per thread
+    constexpr int BATCH = PER < 4 ? PER : 4;         // loads in flight per thread
+    static_assert(PER * T == V && PER % BATCH == 0, "slab tiling");
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;                              // [N][ZS]
+    float2* tw = smem + N * ZS;                      // [N]
+    float* ftab = reinterpret_cast<float*>(tw + N);  // [kFTab]
+    float* re = reinterpret_cast<float*>(buf);       // real view: row y at re + 2 ZS y
+    const int x = blockIdx.x, slot = blockIdx.y, pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    const int t = threadIdx.x;
+    const size_t n3 = (size_t)N * N * N, cell0 = (size_t)x * N * N;
+    fill_twiddles<N>(tw);
+    if constexpr (BRIGHT) {
+        const PairInfo& pi = a.pairs[pair];
+        if (a.ftab) {
+            for (int e = t; e < kFTab; e += T) ftab[e] = __ldg(a.ftab + (size_t)pair * kFTab + e);
+            __syncthreads();
+        }
+        const float4* d4 = reinterpret_cast<const float4*>(a.delta + (size_t)pi.zi * n3 + cell0);
+        const float4* c4 = reinterpret_cast<const float4*>(a.dcell + (size_t)pi.zi * n3 + cell0);
+        const uint32_t* fw = a.fwords + (size_t)pair * (n3 / 32) + cell0 / 32;
+        const float zeta = pi.zeta, t0 = pi.t0, inv = pi.cell_ok > 0.5f ? pi.inv_sqrt2s2_cell : 0.0f;
+        int xq = 0;   // at most 64 cells x 2^23 per thread
+#pragma unroll 1
+        for (int k0 = 0; k0 < PER; k0 += BATCH) {
+            float4 dv[BATCH], cv[BATCH];
+            uint32_t bits[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; k++) {   // every load of the batch before the first use
+                const int e = t + (k0 + k) * T;
+                dv[k] = __ldg(d4 + e);
+                cv[k] = __ldg(c4 + e);
+                bits[k] = __ldg(fw + (4 * e) / 32) >> ((4 * e) % 32);
+            }
+#pragma unroll
+            for (int k = 0; k < BATCH; k++) {
+                const int e = t + (k0 + k) * T;
+                const float dd[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w}, dc[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+                float xh[4], tb[4];
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const bool flagged = (bits[k] >> h) & 1u;
+                    const float nu = a.delta_c - dc[h];
+                    float v = 0.0f;
+                    if (!flagged) {
+                        if (a.ftab) {
+                            v = 1.0f - fminf(1.0f, pop_table_f(ftab, nu, pi.f_inv_h));
+                        } else {
+                            const float f = nu <= 0.0f ? 1.0f : erfc_cheb(nu * inv);
+                            v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
+                        }
+                    }
+                    xh[h] = v;
+                    tb[h] = t0 * v * (1.0f + dd[h]);
+                    xq += __float2int_rn(v * 8388608.0f);
+                }
+                const int y = (4 * e) / N, z = (4 * e) % N;
+                float2* d = reinterpret_cast<float2*>(re + 2 * ZS * y + z);
+                d[0] = make_float2(tb[0], tb[1]);
+                d[1] = make_float2(tb[2], tb[3]);
+                if (a.xhi_out)
+                    reinterpret_cast<float4*>(a.xhi_out + (size_t)pair * n3 + cell0)[e] =
+                        make_float4(xh[0], xh[1], xh[2], xh[3]);
+            }
+        }
+        unsigned long long wsum = (unsigned long long)xq;
+        for (int off = 16; off > 0; off >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        if ((t & 31) == 0) atomicAdd(a.xq + pair, wsum);
+    } else {
+        const float4* b4 = reinterpret_cast<const float4*>(a.box + (size_t)pair * n3 + cell0);
+#pragma unroll 1
+        for (int k0 = 0; k0 < PER; k0 += BATCH) {
+            float4 v[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; k++) v[k] = __ldg(b4 + t + (k0 + k) * T);
+#pragma unroll
+            for (int k = 0; k < BATCH; k++) {
+                const int e = t + (k0 + k) * T, y = (4 * e) / N, z = (4 * e) % N;
+                float2* d = reinterpret_cast<float2*>(re + 2 * ZS * y + z);
+                d[0] = make_float2(v[k].x, v[k].y);
+                d[1] = make_float2(v[k].z, v[k].w);
+            }
+        }
+    }
+    __syncthreads();
+    // along z: the M-point FFT of c[m] = x[2m] + i x[2m+1] per row y (lanes walk y)
+#pragma unroll 1
+    for (int u = t; u < N * S::P2; u += T) {
+        const int y = u % N, i = u / N;
+        ip_stage1<N, S::P1, -1>(buf + y * ZS + i, 1, S::P2, tw, i, 2);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int u = t; u < N * S::P1; u += T) {
+        const int y = u % N, k1 = u / N;
+        ip_stage2<S::P2, -1>(buf + y * ZS + S::P2 * k1, 1);
+    }
+    __syncthreads();
+    // the real-to-half-complex split, pair (k, M - k) in the two columns it read:
+    // X[k] = E - (i/2) w_N^k D, X[M-k] = conj(E) - (i/2) conj(w_N^k D), E = (Z[k] + conj Z[M-k]) / 2,
+    // D = Z[k] - conj Z[M-k]; X[0] = Re + Im of Z[0], X[M] = Re - Im of Z[0], X[M/2] = conj Z[M/2]
+#pragma unroll 1
+    for (int u = t; u < N * (S::M / 2 + 1); u += T) {
+        const int y = u % N, k = u / N;
+        float2* row = buf + y * ZS;
+        if (k == 0) {
+            const float2 z0 = row[0];
+            row[0] = make_float2(z0.x + z0.y, 0.0f);
+            row[S::M] = make_float2(z0.x - z0.y, 0.0f);
+        } else if (2 * k == S::M) {
+            const int ca = slab_col<N>(k);
+            row[ca] = cconj(row[ca]);
+        } else {
+            const int ca = slab_col<N>(k), cb = slab_col<N>(S::M - k);
+            const float2 zk = row[ca], zm = cconj(row[cb]);
+            const float2 e = cscale(cadd(zk, zm), 0.5f);
+            const float2 d = cmul(csub(zk, zm), tw_get<N, -1>(tw, k));
+            row[ca] = make_float2(e.x + 0.5f * d.y, e.y - 0.5f * d.x);
+            row[cb] = make_float2(e.x - 0.5f * d.y, -e.y - 0.5f * d.x);
+        }
+    }
+    __syncthreads();
+    // along y for each column (lanes walk the columns); column M (kz = M) only when binned
+    const bool col_m = a.planes > S::M;
+#pragma unroll 1
+    for (int u = t; u < S::M * S::R2; u += T) {
+        const int c = u % S::M, i = u / S::M;
+        ip_stage1<N, S::R1, -1>(buf + i * ZS + c, ZS, S::R2, tw, i, 1);
+    }
+    if (col_m)
+        for (int i = t; i < S::R2; i += T) ip_stage1<N, S::R1, -1>(buf + i * ZS + S::M, ZS, S::R2, tw, i, 1);
+    __syncthreads();
+#pragma unroll 1
+    for (int u = t; u < S::M * S::R1; u += T) {
+        const int c = u % S::M, k1 = u / S::M;
+        ip_stage2<S::R2, -1>(buf + (S::R2 * k1) * ZS + c, ZS);
+    }
+    if (col_m)
+        for (int k1 = t; k1 < S::R1; k1 += T) ip_stage2<S::R2, -1>(buf + (S::R2 * k1) * ZS + S::M, ZS);
+    __syncthreads();
+    // planes kz < planes: row x of plane kz, y slots in order (two per thread and store)
+    float4* out = reinterpret_cast<float4*>(a.dst + (size_t)slot * NH * N * N);
+    for (int u = t; u < a.planes * (N / 2); u += T) {
+        const int kz = u / (N / 2), r = 2 * (u % (N / 2)), c = slab_col<N>(kz);
+        const float2 v0 = buf[r * ZS + c], v1 = buf[(r + 1) * ZS + c];
+        out[(((size_t)kz * N + x) * N + r) / 2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+}
+
+template <int N>
+struct XLine {
+    static constexpr int TG = N < 32 ? N : 32;                    // y slots per CTA
+    static constexpr int GS = TG + 1;                             // row stride (float2)
+    static constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
+    static constexpr int THREADS = TG * R2;
+    static constexpr size_t SMEM =
+        (size_t)N * GS * sizeof(float2) + N * sizeof(float2) + (size_t)kPrivBins * THREADS * sizeof(float);
+};
+
+// The x-line pass: plane kz = blockIdx.x / (N / TG), y slots g0 .. g0 + TG - 1, of the slab
+// pass's output; the transform along x (first step straight from global memory), then the
+// shell sums S_b += weight * k^3 |X|^2 (weight 2 for 0 < kz < n/2) in per-thread FP32 slots
+// (at most R1 modes each), added by bin_sums in a fixed order.
+template <int N>
+__global__ void __launch_bounds__(XLine<N>::THREADS) k_xline_ps(PSArgs a) {
+    using L = XLine<N>;
+    constexpr int T = L::THREADS, TG = L::TG, GS = L::GS, NH = N / 2 + 1, NT = N / TG;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;                                  // [N][GS]
+    float2* tw = smem + N * GS;                          // [N]
+    float* priv = reinterpret_cast<float*>(tw + N);      // [kPrivBins][T]
+    __shared__ double s_bins[EOR21_MAX_BINS];
+    const int kz = blockIdx.x / NT, g0 = (blockIdx.x % NT) * TG, slot = blockIdx.y;
+    const int pair = a.pair0 + slot;
+    if (pair >= a.n_pairs) return;
+    const int t = threadIdx.x;
+    const bool priv_ok = a.n_bins <= kPrivBins;
+    // first step along x, loads first: task (column cc, i), rows x = i + R2 j
+    const int cc = t % TG, i = t / TG;
+    const float2* src = a.ps_inter + ((size_t)slot * NH + kz) * N * N + g0 + cc;
+    float2 v[L::R1];
+#pragma unroll
+    for (int j = 0; j < L::R1; j++) v[j] = __ldg(src + (size_t)(i + L::R2 * j) * N);
+    fill_twiddles<N>(tw);
+    for (int e = t; e < kPrivBins * T; e += T) priv[e] = 0.0f;
+    for (int e = t; e < EOR21_MAX_BINS; e += T) s_bins[e] = 0.0;
+    __syncthreads();
+    dft_reg<L::R1, -1>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < L::R1; k1++) v[k1] = cmul(v[k1], tw_get<N, -1>(tw, i * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < L::R1; k1++) buf[(i + L::R2 * k1) * GS + cc] = v[k1];
+    __syncthreads();
+    const float weight = (kz == 0 || 2 * kz == N) ? 1.0f : 2.0f;
+    const int mz2 = kz * kz;
+#pragma unroll
+    for (int u = t; u < TG * L::R1; u += T) {
+        const int c = u % TG, k1 = u / TG;
+        float2 w[L::R2];
+#pragma unroll
+        for (int i2 = 0; i2 < L::R2; i2++) w[i2] = buf[(L::R2 * k1 + i2) * GS + c];
+        dft_reg<L::R2, -1>(w);
+        const int my = signed_index(slot_k<N>(g0 + c), N);
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; k2++) {   // mode (kx = k1 + R1 k2, ky, kz)
+            const int mx = signed_index(k1 + L::R1 * k2, N);
+            const int m2 = mx * mx + my * my + mz2;
+            const int b = a.bin_of_m2[m2];
+            if (b >= 0) {
+                const float fm2 = (float)m2;
+                const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (w[k2].x * w[k2].x + w[k2].y * w[k2].y);
+                if (priv_ok) priv[b * T + t] += val;
+                else atomicAdd(&s_bins[b], (double)val);
+            }
+        }
+    }
+    __syncthreads();
+    if (priv_ok) {
+        bin_sums<T>(priv, a.n_bins, s_bins);
+        __syncthreads();
+    }
+    for (int b = t; b < a.n_bins; b += T)
+        if (s_bins[b] != 0.0) atomicAdd(&a.ps_sum[(size_t)pair * a.n_bins + b], s_bins[b]);
+}
+
 // ------------------------------------------------------------------ spectra and chi^2
 
 // Delta^2 = S_b dx^6 / (2 pi^2 V) / n_b and mean |k| per (pair, bin).
@@ -1148,6 +1457,9 @@ cudaError_t prepare_n() {
         if ((e = set_smem(k_plane_ps<N, T>, Plane<N, T>::SMEM_PS)) != cudaSuccess) return e;
         if constexpr (N == 128)
             if ((e = set_smem(k_plane_ps2, kPs2Smem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_slab_ps<N, true>, Slab<N>::SMEM + kFTab * sizeof(float))) != cudaSuccess) return e;
+        if ((e = set_smem(k_slab_ps<N, false>, Slab<N>::SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_xline_ps<N>, XLine<N>::SMEM)) != cudaSuccess) return e;
     }
     if ((e = set_smem(k_pencil_ionize<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
     if ((e = set_smem(k_pencil_density<N>, Pencil<N>::SMEM)) != cudaSuccess) return e;
@@ -1171,6 +1483,7 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
     // the pencil pass of batch b + 1 fills the other half, and batch b + 2 waits for the plane
     // pass of batch b; with one stream the passes run in turn
     const bool two = c->tune.ps_streams == 2;
+    const bool slab = N != kL && c->tune.ps_split == 0;   // slab and x-line passes
     cudaStream_t ps = two ? c->stream2 : c->stream;   // the plane passes' stream
     cudaError_t e = cudaSuccess;
     if (two && ((e = cudaEventRecord(c->ev_fork, c->stream)) != cudaSuccess ||
@@ -1182,7 +1495,17 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
         float2* half = c->d_psinter + (size_t)h * P * c->nspec;
         if (two && b >= 2 && (e = cudaStreamWaitEvent(c->stream, c->ev_plane[h], 0)) != cudaSuccess) return e;
         trace_begin(c, kKForward);
-        if (flags) {
+        if (slab) {
+            if constexpr (N != kL) {
+                SlabArgs sa{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, pop_tables(c),
+                            c->d_dtb, half, pair0, n_pairs, c->ps_planes, (float)c->cfg.delta_c};
+                if (flags)
+                    k_slab_ps<N, true><<<dim3(N, P), Slab<N>::THREADS,
+                                         Slab<N>::SMEM + (sa.ftab ? kFTab * sizeof(float) : 0), c->stream>>>(sa);
+                else
+                    k_slab_ps<N, false><<<dim3(N, P), Slab<N>::THREADS, Slab<N>::SMEM, c->stream>>>(sa);
+            }
+        } else if (flags) {
             BrightArgs ba{c->d_fwords, c->d_pairs, brightness_base(c), c->d_dcell, xhi_out, c->d_xq, half,
                           pop_tables(c), pair0, n_pairs, (float)c->cfg.delta_c};
             k_pencil_brightness<N><<<dim3(Pencil<N>::TILES, P), Pencil<N>::THREADS,
@@ -1196,7 +1519,16 @@ cudaError_t ps_from_boxes_n(eor_ctx* c, float* xhi_out) {
                     (e = cudaStreamWaitEvent(c->stream2, c->ev_pencil[h], 0)) != cudaSuccess))
             return e;
         PSArgs ap{half, c->d_pairs, c->d_bin_of_m2, c->d_ps_sum, pair0, n_pairs, c->cfg.n_bins, kf * kf * kf};
-        if ((e = plane_ps<N, T>(c, ap, c->ps_planes, P, ps)) != cudaSuccess) return e;
+        if (slab) {
+            if constexpr (N != kL) {
+                trace_begin_on(c, kKPsPlane, ps);
+                k_xline_ps<N><<<dim3(c->ps_planes * (N / XLine<N>::TG), P), XLine<N>::THREADS, XLine<N>::SMEM, ps>>>(ap);
+                trace_end_on(c, ps);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+        } else if ((e = plane_ps<N, T>(c, ap, c->ps_planes, P, ps)) != cudaSuccess) {
+            return e;
+        }
         if (two && (e = cudaEventRecord(c->ev_plane[h], c->stream2)) != cudaSuccess) return e;
     }
     // join: the last plane pass of each half

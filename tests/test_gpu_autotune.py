@@ -1,5 +1,6 @@
 """GPU test of the launch-schedule autotuner (eor_autotune): it picks one of its candidates,
-leaves the context usable, and the likelihood does not depend on the schedule."""
+leaves the context usable, and the likelihood depends on the schedule only through the FP32
+rounding of the spectrum's transforms."""
 import numpy as np
 import pytest
 
@@ -30,8 +31,9 @@ def test_autotune_picks_a_candidate_and_keeps_results(method):
     assert p in (4, 8, 16, 32) and t == 512 and ms > 0
     assert g in ((4, 8, 16) if method == eor21.EOR_METHOD_DIRECT else (8,))
     after, d2_after = ctx.likelihood(params, mock, sigma, want_d2=True)
-    assert np.allclose(after, before, rtol=1e-9, atol=0)
-    assert np.allclose(d2_after, d2_before, rtol=1e-9, atol=0, equal_nan=True)
+    # the spectrum's tiling may change with the schedule: the same sums up to FP32 rounding
+    assert np.allclose(after, before, rtol=1e-5, atol=0)
+    assert np.allclose(d2_after, d2_before, rtol=1e-5, atol=0, equal_nan=True)
     ctx.close()
 
 
@@ -55,9 +57,9 @@ def test_autotune_device_buffers_and_errors():
 
 
 def test_power_spectrum_plane_tiling_does_not_change_results():
-    """At 128^3 the spectrum's plane pass runs as one CTA per plane or as a two-CTA cluster
-    (eor_set_ps_split); the spectra agree to the FP32 rounding of the per-thread partial
-    sums, and the autotuner reports the tiling it kept."""
+    """At 128^3 the spectrum runs as slab and x-line passes, or as a pencil pass and one CTA
+    per plane or a two-CTA cluster per plane (eor_set_ps_split); the spectra agree to the
+    FP32 rounding of the transforms, and the autotuner reports the tiling it kept."""
     n, box, zs = 128, 250.0, (9.0,)
     ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=4)
     ctx.init_boxes(synth.density_boxes(n, box, zs, seed=12))
@@ -65,12 +67,13 @@ def test_power_spectrum_plane_tiling_does_not_change_results():
     mock = np.full((1, 14), 20.0)
     sigma = 0.2 * mock
     out = {}
-    for split in (1, 2):
+    for split in (0, 1, 2):
         ctx.set_ps_split(split)
         assert ctx.get_tuning()["ps_split"] == split
         out[split] = ctx.likelihood(params, mock, sigma, want_d2=True)
-    np.testing.assert_allclose(out[2][1], out[1][1], rtol=2e-6, equal_nan=True)
-    np.testing.assert_allclose(out[2][0], out[1][0], rtol=1e-5)
+    for split in (0, 2):
+        np.testing.assert_allclose(out[split][1], out[1][1], rtol=1e-5, equal_nan=True)
+        np.testing.assert_allclose(out[split][0], out[1][0], rtol=1e-4)
     # the spectrum's passes on one stream in turn, or overlapped on two: the same kernels and
     # sums (up to the order of the FP64 additions across planes)
     for streams in (1, 2):
@@ -79,7 +82,7 @@ def test_power_spectrum_plane_tiling_does_not_change_results():
         d2 = ctx.likelihood(params, mock, sigma, want_d2=True)[1]
         np.testing.assert_allclose(d2, out[2][1], rtol=1e-12, equal_nan=True)
     ctx.autotune(params, mock, sigma, reps=1)
-    assert ctx.get_tuning()["ps_split"] in (1, 2) and ctx.get_tuning()["ps_streams"] in (1, 2)
+    assert ctx.get_tuning()["ps_split"] in (0, 1, 2) and ctx.get_tuning()["ps_streams"] in (1, 2)
     ctx.close()
     small = eor21.Context(n=64, box_mpc=100.0, z=zs, max_walkers=1)
     with pytest.raises(eor21.EorError) as ei:
