@@ -273,7 +273,9 @@ int eor_contraction_info(const eor_ctx* ctx, int* kind, int* k_slots);
  * every CTA of the tensor-core contraction withholds the epilogue's release of the
  * accumulator buffer that holds the chunk-th coefficient chunk it processes (its chunk
  * counter runs over every cell tile it takes), and the MMA thread's wait for that release
- * (before chunk + 2) gives up after wait_ms milliseconds of GPU time instead of 2 s. The wait that gives up records role 2 (MMA), barrier 7
+ * (before chunk + 2) gives up after about wait_ms milliseconds (counted in SM clock cycles at
+ * the highest SM clock; longer in wall time at a lower clock) instead of 2 s. The wait that
+ * gives up records role 2 (MMA), barrier 7
  * (accumulator free) and the chunk; the CTA then stops issuing, waits for its MMAs and
  * copies already in flight, frees its tensor memory and exits, and the next call that reads
  * the context's error word (eor_set_params, or eor_likelihood with host buffers) returns

@@ -115,13 +115,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// Nanosecond clock of the GPU (%globaltimer).
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // One test of the mbarrier phase `parity`; the thread may be suspended for at most about
 // kSuspendNs while the phase is incomplete (explicit suspend-time hint; 0, the default: the
 // hardware's own time limit, measured 2 % faster on the flag contraction's step than 1000 ns).
@@ -147,13 +140,23 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for the mbarrier phase `parity` for at most limit_ns nanoseconds of GPU time;
-// false if the limit ran out.
+// Deadlines of the bounded waits are kept on the SM's cycle counter (clock64: a few cycles
+// to read; a %globaltimer read costs hundreds of cycles, and one per wait on the contraction's
+// MMA and copy threads cost about as much time as the MMAs), at 2.125 cycles per nanosecond:
+// above this GPU's highest SM clock, so that a lower clock only lengthens a wait in wall
+// time. The first test of the barrier comes before the clock is read.
+__device__ __forceinline__ long long wait_cycles(uint64_t limit_ns) {
+    return (long long)(2 * limit_ns + (limit_ns >> 3));
+}
+
+// Wait for the mbarrier phase `parity` for at most about limit_ns nanoseconds; false if the
+// limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    const uint64_t t0 = global_ns();
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64(), limit = wait_cycles(limit_ns);
     while (true) {
         if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -284,11 +287,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // Time-bounded wait (as mbar_wait) that also gives up when *abort becomes non-zero.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
                                                    volatile int* abort) {
-    const uint64_t t0 = global_ns();
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64(), limit = wait_cycles(limit_ns);
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > limit_ns) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
