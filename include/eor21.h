@@ -269,19 +269,20 @@ int eor_basis_info(const eor_ctx* ctx, int* rank, double* max_residual);
  * (0 for the first two). */
 enum { EOR_CONTRACT_NONE = 0, EOR_CONTRACT_FP32 = 1, EOR_CONTRACT_TF32 = 2, EOR_CONTRACT_FP16 = 3 };
 int eor_contraction_info(const eor_ctx* ctx, int* kind, int* k_slots);
-/* Test-only failure injection (off by default; not part of the method). With chunk >= 0,
+/* Test-only failure injection (off by default; not part of the method). With step >= 0,
  * every CTA of the tensor-core contraction withholds the epilogue's release of the
- * accumulator buffer that holds the chunk-th coefficient chunk it processes (its chunk
- * counter runs over every cell tile it takes), and the MMA thread's wait for that release
- * (before chunk + 2) gives up after about wait_ms milliseconds (counted in SM clock cycles at
- * the highest SM clock; longer in wall time at a lower clock) instead of 2 s. The wait that
- * gives up records role 2 (MMA), barrier 7
- * (accumulator free) and the chunk; the CTA then stops issuing, waits for its MMAs and
- * copies already in flight, frees its tensor memory and exits, and the next call that reads
- * the context's error word (eor_set_params, or eor_likelihood with host buffers) returns
- * EOR_ETIMEOUT. No asynchronous copy or MMA is made to time out. chunk < 0 switches the
- * injection off. The captured likelihood graph is rebuilt at the next call. */
-int eor_debug_withhold(eor_ctx* ctx, int chunk, double wait_ms);
+ * accumulator buffer of its step-th accumulator tile (a step is one coefficient chunk against
+ * one tile of cells; each CTA counts its steps over all the cells it takes), and the MMA
+ * thread's wait for that release (before step + 2, the same buffer) gives up after about
+ * wait_ms milliseconds (counted in SM clock cycles at the highest SM clock; longer in wall
+ * time at a lower clock) instead of 2 s. The wait that gives up records role 2 (MMA),
+ * barrier 7 (accumulator free) and the step; the CTA then stops issuing, waits for its MMAs
+ * and copies already in flight, frees its tensor memory and exits, and the next call that
+ * reads the context's error word (eor_set_params, or eor_likelihood with host buffers)
+ * returns EOR_ETIMEOUT, its message naming the first role, barrier and step that gave up. No
+ * asynchronous copy or MMA is made to time out. step < 0 switches the injection off. The
+ * captured likelihood graph is rebuilt at the next call. */
+int eor_debug_withhold(eor_ctx* ctx, int step, double wait_ms);
 
 /* Diagnostic of the basis reformulation: w[m2] = sum_b c_b(R) phi_b(k) for R = r_mpc and
  * k = (2 pi / box_mpc) sqrt(m2), m2 = 0 .. 3 (n/2)^2 (double [3 (n/2)^2 + 1]; NaN where no

@@ -110,7 +110,7 @@ int check_device_error(eor_ctx* c) {
                                     "(Eq. 1 is then not one interval; not supported)");
     if (err & eor::kErrTimeout) {
         char where[96];
-        snprintf(where, sizeof(where), " (first: role %d, barrier %d, chunk %d)", (words[1] >> 28) & 15,
+        snprintf(where, sizeof(where), " (first: role %d, barrier %d, step %d)", (words[1] >> 28) & 15,
                  (words[1] >> 20) & 255, words[1] & 0xFFFFF);
         return fail(c, EOR_ETIMEOUT, std::string("a bounded tensor-core wait ran out") + where);
     }
@@ -915,13 +915,13 @@ int eor_basis_window(eor_ctx* c, double r_mpc, double* w, int mem) {
     return finish(c, mem);
 }
 
-int eor_debug_withhold(eor_ctx* c, int chunk, double wait_ms) {
+int eor_debug_withhold(eor_ctx* c, int step, double wait_ms) {
     if (!c) return EOR_EINVAL;
-    if (chunk >= 0 && !(wait_ms > 0.0 && wait_ms <= 2000.0))
+    if (step >= 0 && !(wait_ms > 0.0 && wait_ms <= 2000.0))
         return fail(c, EOR_EINVAL, "wait_ms must be in (0, 2000]");
     CK(cudaStreamSynchronize(c->stream), "debug withhold");
-    c->dbg_withhold = chunk >= 0 ? chunk : -1;
-    c->dbg_wait_ns = chunk >= 0 ? (unsigned long long)(wait_ms * 1e6) : 0ull;
+    c->dbg_withhold = step >= 0 ? step : -1;
+    c->dbg_wait_ns = step >= 0 ? (unsigned long long)(wait_ms * 1e6) : 0ull;
     if (c->graph_exec) {   // the captured graph holds the kernel's arguments
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;

@@ -1228,12 +1228,12 @@ __global__ void __launch_bounds__(Slab<N>::THREADS, 3) k_slab_ps(SlabArgs a) {
     if (col_m)
         for (int k1 = t; k1 < S::R1; k1 += T) ip_stage2<S::R2, -1>(buf + (S::R2 * k1) * ZS + S::M, ZS);
     __syncthreads();
-    // planes kz < planes: row x of plane kz, y slots in order (two per thread and store)
-    float4* out = reinterpret_cast<float4*>(a.dst + (size_t)slot * NH * N * N);
-    for (int u = t; u < a.planes * (N / 2); u += T) {
-        const int kz = u / (N / 2), r = 2 * (u % (N / 2)), c = slab_col<N>(kz);
-        const float2 v0 = buf[r * ZS + c], v1 = buf[(r + 1) * ZS + c];
-        out[(((size_t)kz * N + x) * N + r) / 2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    // planes kz < planes: row x of plane kz, y slots in order (lanes walk the slots: the
+    // column reads of stride ZS are conflict-free, the row stores coalesced)
+    float2* out = a.dst + (size_t)slot * NH * N * N;
+    for (int u = t; u < a.planes * N; u += T) {
+        const int kz = u / N, r = u % N;
+        out[((size_t)kz * N + x) * N + r] = buf[r * ZS + slab_col<N>(kz)];
     }
 }
 

@@ -140,6 +140,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+// One non-blocking test of the mbarrier phase `parity`.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Deadlines of the bounded waits are kept on the SM's cycle counter (clock64: a few cycles
 // to read; a %globaltimer read costs hundreds of cycles, and one per wait on the contraction's
 // MMA and copy threads cost about as much time as the MMAs), at 2.125 cycles per nanosecond:

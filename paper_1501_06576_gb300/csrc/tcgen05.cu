@@ -642,26 +642,22 @@ namespace {
 constexpr int kFM = 128;                        // cells per tile (MMA M)
 constexpr int kFN = 256;                        // coefficient columns per chunk (MMA N)
 constexpr int kFKMax = 96;                      // FP16 K slots at most (six MMA steps of 16)
-constexpr int kFStagesMax = 4;                  // coefficient chunks in flight (4, or 3 when 4 do not fit)
+constexpr int kFStagesMax = 3;                  // coefficient chunks in flight (3, or 2 when 3 do not fit)
+constexpr int kFGT = 4;                         // cell tiles per group: a coefficient chunk serves kFGT tiles
 constexpr int kFMetaStages = 8;                 // group records (and widths) of chunks in flight
-constexpr int kFMetaLead = 4;                   // records issued this many chunks ahead of the coefficients
 constexpr int kFGroups = kFN / kGroup;          // walker groups per chunk
 constexpr uint32_t kFRecBytes = kFGroups * 16;  // group records
 constexpr uint32_t kFWidthBytes = kFN * 4;      // per column t (delta_hi - delta_crit) (mass-dependent efficiency)
 constexpr uint32_t f16_meta_bytes(bool pops) { return kFRecBytes + (pops ? kFWidthBytes : 0u); }
 constexpr int kFEpiWarps = 16;                  // four per tensor-memory lane quarter
-#ifndef EOR_F16_EPI_SETS
-#define EOR_F16_EPI_SETS 2
-#endif
-constexpr int kFEpiSets = EOR_F16_EPI_SETS;     // epilogue warp sets, alternating chunks (1 or 2)
-constexpr int kFSetThreads = 32 * kFEpiWarps / kFEpiSets;   // threads of one set
-constexpr int kFRounds = 2 * kFEpiSets / 2;     // 64-column rounds of a warp per chunk
+constexpr int kFEpiSets = 2;                    // epilogue warp sets, alternating units (each on its own buffer)
+constexpr int kFSetWarps = kFEpiWarps / kFEpiSets;   // warps of one set: one arrival each on the set's barriers
+constexpr int kFRounds = 2;                     // 64-column rounds of an epilogue warp per unit
 constexpr int kFThreads = 128 + 32 * kFEpiWarps;
 constexpr uint32_t kFTmemCols = 2 * kFN;        // two accumulator buffers
 constexpr float kFScale = 16384.0f;             // 2^14
 static_assert(kFTmemCols <= 512, "tensor memory");
-static_assert(kFEpiSets == 1 || kFEpiSets == 2, "one set, or two sets each on its own accumulator buffer");
-static_assert(kFN == 8 * kGroup && kFEpiWarps == 16,
+static_assert(kFN == 8 * kGroup && kFEpiWarps == 16 && kFEpiSets == 2,
               "epilogue: a set's warp (q, p) reads 64 kFRounds columns of lane quarter q, 64 per round");
 
 __host__ __device__ constexpr int f16_kslots(int rank) { return (3 * (rank + 1) + 15) / 16 * 16; }
@@ -807,43 +803,46 @@ struct F16Args {
     int n_z, chunks_per_z, tiles_per_z, ksteps;
     uint32_t a_bytes, b_bytes, sbo;
     uint32_t meta_bytes;        // group records (and with POPS the columns' interval widths)
-    int stages;                 // coefficient stages (3 or 4)
     long long n3;
     int withhold;               // test-only failure injection (see TcArgs), -1 off
     uint64_t free_wait_ns;
 };
 
-// Persistent CTA (one per SM): tiles of 128 cells t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (all cells of box 0 first), each against every coefficient chunk of its box. Roles: thread
-// 32 issues the bulk copies (a tile's A operands into one of two stages half-way through the
-// previous tile, once the MMAs of the tile two before are done; chunk g's coefficients into
-// stage g % stages as soon as the MMAs of chunk g - stages are done, and its group records
-// into ring slot g % kFMetaStages once the epilogue has read chunk g - kFMetaStages's), thread
-// 0 the MMAs (per chunk ksteps M128 N256 K16 FP16 MMAs into tensor-memory buffer g % 2; it
-// waits only for operands and a free buffer, also across tiles), warps 4-19 the epilogue in
-// two sets taking alternate chunks (set s, buffer s): a set's warp (q = lane quarter, p)
-// reads 128 columns of its 32 cells in two rounds of 64, releases the buffer after the last
-// read and, for the walkers of the groups it read, stores the Eq. 1 flags of its 32 cells as
-// one word each (a walker's flag: the AND of the sign bits of its columns is clear). x_HI,
-// delta T_b and the power spectrum follow in the pencil pass. Chunk counters g run over all
-// chunks of the CTA's tiles. POPS (a mass-dependent efficiency): a column flags where
-// 0 <= D <= t (delta_hi - delta_crit), the width staged with the group records. Every wait is
-// bounded in GPU time; on a timeout the CTA records where (err[1]: role, barrier, g), stops,
-// waits for its MMAs and copies in flight and frees its tensor memory.
+// Persistent CTA (one per SM): groups of kFGT consecutive 128-cell tiles of one box, grp =
+// blockIdx.x, blockIdx.x + gridDim.x, ... (all groups of box 0 first). Work unit u = (group,
+// chunk, tile of the group) in that order: a coefficient chunk is copied once per group and
+// serves its kFGT tiles, whose A operands stay in kFGT slots for the group (each chunk copy
+// costs its copy thread a few hundred cycles whatever its size, and the chunks of all SMs
+// share L2 bandwidth, so one chunk per tile fell behind the MMAs). Roles: thread 32 copies
+// chunk k's group records into ring slot k % kFMetaStages and its coefficients into stage
+// k % S (k counts the CTA's chunks over its groups) once the slot / stage is free, and the
+// next group's A operands into slot i as soon as this group's last MMAs on slot i are done
+// (tested between and during its other waits, so that no A copy holds up a coefficient
+// copy); thread 0 issues the MMAs (per unit ksteps M128 N256 K16 FP16 MMAs into
+// tensor-memory buffer u % 2; it waits only for operands and a free buffer); warps 4-19 run
+// the epilogue in two sets taking alternate units (set s, buffer s): a set's warp (q = lane
+// quarter, p) reads 128 columns of its 32 cells in two rounds of 64, releases the buffer
+// after the last read and, for the walkers of the groups it read, stores the Eq. 1 flags of
+// its 32 cells as one word each (a walker's flag: the AND of the sign bits of its columns is
+// clear). x_HI, delta T_b and the power spectrum follow in the pencil pass. POPS (a
+// mass-dependent efficiency): a column flags where 0 <= D <= t (delta_hi - delta_crit), the
+// width staged with the group records. Every wait is bounded; on a timeout the CTA records
+// where (err[1]: role, barrier, unit or chunk), stops, waits for its MMAs and copies in
+// flight and frees its tensor memory.
 template <bool POPS, int S>
 __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
-    static_assert(S == 3 || S == 4, "coefficient stages");
+    static_assert(S == 2 || S == 3, "coefficient stages");
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* As = sm;                                    // [2][a_bytes]
-    unsigned char* Bs = As + 2 * a.a_bytes;                    // [S][b_bytes]
+    unsigned char* As = sm;                                    // [kFGT][a_bytes]
+    unsigned char* Bs = As + kFGT * a.a_bytes;                 // [S][b_bytes]
     unsigned char* Ms = Bs + S * a.b_bytes;                    // [kFMetaStages][meta_bytes]
     uint64_t* bars = reinterpret_cast<uint64_t*>(Ms + kFMetaStages * a.meta_bytes);
-    uint64_t* barA = bars;                   // [2] A stage landed
-    uint64_t* barAe = barA + 2;              // [2] A stage free (MMAs of its tile done)
-    uint64_t* barB = barAe + 2;              // [S] coefficient stage landed
+    uint64_t* barA = bars;                   // [kFGT] A slot landed
+    uint64_t* barAe = barA + kFGT;           // [kFGT] A slot free (the group's last MMAs on it are done)
+    uint64_t* barB = barAe + kFGT;           // [S] coefficient stage landed
     uint64_t* barBe = barB + kFStagesMax;    // [S] its MMAs are done
     uint64_t* barM = barBe + kFStagesMax;    // [kFMetaStages] group records landed
-    uint64_t* barMe = barM + kFMetaStages;   // [kFMetaStages] the epilogue has read them
+    uint64_t* barMe = barM + kFMetaStages;   // [kFMetaStages] the epilogue has read them (kFGT units)
     uint64_t* barD = barMe + kFMetaStages;   // [2] accumulator buffer ready
     uint64_t* barE = barD + 2;               // [2] accumulator buffer released by the epilogue
     uint64_t* barF = barE + 2;               // MMAs drained (abort path)
@@ -853,17 +852,21 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int ncols = *a.ncols;
     const int nch = (ncols + kFN - 1) / kFN;
-    const int total = a.n_z * a.tiles_per_z;
-    const int my_tiles = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const bool work = nch > 0 && my_tiles > 0;
+    const int groups_per_z = a.tiles_per_z / kFGT;
+    const int total = a.n_z * groups_per_z;
+    const int my_groups = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const bool work = nch > 0 && my_groups > 0;
+    auto group_of = [&](int gi) { return (int)blockIdx.x + gi * (int)gridDim.x; };
 
     if (warp == 0) tc::tmem_alloc(tslot, kFTmemCols);
     if (t == 0) {
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < kFGT; s++) {
             tc::mbar_init(barA + s, 1);
             tc::mbar_init(barAe + s, 1);
+        }
+        for (int s = 0; s < 2; s++) {
             tc::mbar_init(barD + s, 1);
-            tc::mbar_init(barE + s, kFSetThreads);
+            tc::mbar_init(barE + s, kFSetWarps);
         }
         for (int s = 0; s < S; s++) {
             tc::mbar_init(barB + s, 1);
@@ -871,7 +874,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
         }
         for (int s = 0; s < kFMetaStages; s++) {
             tc::mbar_init(barM + s, 1);
-            tc::mbar_init(barMe + s, kFSetThreads);
+            tc::mbar_init(barMe + s, kFGT * kFSetWarps);
         }
         tc::mbar_init(barF, 1);
         *abort = 0;
@@ -880,64 +883,62 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    // copy-thread bookkeeping (registers): bit 2s of a mask = stage s has a copy that may still
-    // land, bit 2s + 1 = the parity of the phase it completes
+    // copy-thread bookkeeping (registers): bit 2s of a mask = slot / stage s has a copy that
+    // may still land, bit 2s + 1 = the parity of the phase it completes
     uint32_t owedA = 0, owedB = 0, owedM = 0;
 
     if (t == 32 && work) {
-        // ---------------- copy thread (incremental counters: no division in the loop)
+        // ---------------- copy thread (counters, no division in the loop)
         const size_t chunk_bytes = (size_t)a.b_bytes + a.meta_bytes;
-        auto tile_base = [&](int it) {
-            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-            return a.B + (size_t)(tile / a.tiles_per_z) * a.chunks_per_z * chunk_bytes;
+        auto copy_a = [&](int gi, int i) {   // A operands of group gi's tile i into slot i
+            const size_t tile = (size_t)group_of(gi) * kFGT + i;
+            tc::mbar_expect_tx(barA + i, a.a_bytes);
+            tc::bulk_g2s(As + (size_t)i * a.a_bytes, a.A + tile * a.a_bytes, a.a_bytes, barA + i);
+            owedA = (owedA & ~(3u << (2 * i))) | ((1u | ((uint32_t)gi & 1u) << 1) << (2 * i));
         };
-        // A operands of tile j into stage j % 2 once the MMAs of tile j - 2 are done
-        auto issue_a = [&](int j) -> bool {
-            const int as = j & 1;
-            if (j >= 2 && !tc::mbar_wait_or_abort(barAe + as, (uint32_t)((j - 2) >> 1) & 1u, kWaitNs, abort)) {
-                record_timeout(a.err, 1, 9, j * nch);
-                return false;
+        int na_g = 1, na_i = 0;   // the next A copy: group na_g, slot na_i (after group na_g - 1 freed it)
+        auto poll_a = [&]() {
+            while (na_g < my_groups && tc::mbar_test(barAe + na_i, (uint32_t)(na_g - 1) & 1u)) {
+                copy_a(na_g, na_i);
+                if (++na_i == kFGT) {
+                    na_i = 0;
+                    na_g++;
+                }
             }
-            const int tile = (int)blockIdx.x + j * (int)gridDim.x;
-            tc::mbar_expect_tx(barA + as, a.a_bytes);
-            tc::bulk_g2s(As + (size_t)as * a.a_bytes, a.A + (size_t)tile * a.a_bytes, a.a_bytes, barA + as);
-            owedA = (owedA & ~(3u << (2 * as))) | ((1u | ((uint32_t)(j >> 1) & 1u) << 1) << (2 * as));
-            return true;
         };
-        // group records: a cursor (tile mit, chunk mc, counter mg) kFMetaLead chunks ahead
-        const int total_g = my_tiles * nch;
-        int mit = 0, mc = 0, mg = 0;
-        const unsigned char* mbase = tile_base(0);
-        auto issue_m = [&]() -> bool {
-            const int ms = mg & (kFMetaStages - 1);
-            const uint32_t muse = (uint32_t)mg / kFMetaStages;
-            if (muse > 0 && !tc::mbar_wait_or_abort(barMe + ms, (muse - 1) & 1u, kWaitNs, abort)) {
-                record_timeout(a.err, 1, 5, mg);
-                return false;
+        // wait for a phase, issuing the A copies that become possible meanwhile; false on a
+        // timeout or an abort
+        auto wait_poll = [&](uint64_t* bar, uint32_t parity) -> bool {
+            if (tc::mbar_test(bar, parity)) return true;
+            const long long t0 = clock64(), limit = tc::wait_cycles(kWaitNs);
+            while (true) {
+                poll_a();
+                if (tc::mbar_try(bar, parity)) return true;
+                if (*abort) return false;
+                if (clock64() - t0 > limit) return false;
             }
-            tc::mbar_expect_tx(barM + ms, a.meta_bytes);
-            tc::bulk_g2s(Ms + (size_t)ms * a.meta_bytes, mbase + (size_t)mc * chunk_bytes + a.b_bytes, a.meta_bytes,
-                         barM + ms);
-            owedM = (owedM & ~(3u << (2 * ms))) | ((1u | (muse & 1u) << 1) << (2 * ms));
-            mg++;
-            if (++mc == nch) {
-                mc = 0;
-                if (++mit < my_tiles) mbase = tile_base(mit);
-            }
-            return true;
         };
-        bool ok = issue_a(0);
-        while (ok && mg < kFMetaLead && mg < total_g) ok = issue_m();
-        int st = 0;
-        uint32_t use = 0;   // chunk g = it nch + c goes to stage st, the use-th time that stage is filled
-        for (int it = 0; it < my_tiles && ok; it++) {
-            const unsigned char* Bz = tile_base(it);
-            for (int c = 0; c < nch; c++) {
-                // the next tile's A operands half-way through this tile's chunks
-                if (c == nch / 2 && it + 1 < my_tiles && !(ok = issue_a(it + 1))) break;
-                if (mg < total_g && !(ok = issue_m())) break;
-                if (use > 0 && !(ok = tc::mbar_wait_or_abort(barBe + st, (use - 1) & 1u, kWaitNs, abort))) {
-                    record_timeout(a.err, 1, 3, it * nch + c);
+        for (int i = 0; i < kFGT; i++) copy_a(0, i);
+        bool ok = true;
+        int st = 0, ms = 0, k = 0;
+        uint32_t use = 0, muse = 0;   // the use-th filling of stage st, the muse-th of ring slot ms
+        for (int gi = 0; gi < my_groups && ok; gi++) {
+            const unsigned char* Bz = a.B + (size_t)(group_of(gi) / groups_per_z) * a.chunks_per_z * chunk_bytes;
+            for (int c = 0; c < nch; c++, k++) {
+                if (muse > 0 && !(ok = wait_poll(barMe + ms, (muse - 1) & 1u))) {
+                    record_timeout(a.err, 1, 5, k);
+                    break;
+                }
+                tc::mbar_expect_tx(barM + ms, a.meta_bytes);
+                tc::bulk_g2s(Ms + (size_t)ms * a.meta_bytes, Bz + (size_t)c * chunk_bytes + a.b_bytes, a.meta_bytes,
+                             barM + ms);
+                owedM = (owedM & ~(3u << (2 * ms))) | ((1u | (muse & 1u) << 1) << (2 * ms));
+                if (++ms == kFMetaStages) {
+                    ms = 0;
+                    muse++;
+                }
+                if (use > 0 && !(ok = wait_poll(barBe + st, (use - 1) & 1u))) {
+                    record_timeout(a.err, 1, 3, k);
                     break;
                 }
                 tc::mbar_expect_tx(barB + st, a.b_bytes);
@@ -947,110 +948,158 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                     st = 0;
                     use++;
                 }
+                poll_a();
             }
+        }
+        while (ok && na_g < my_groups) {   // A copies still pending
+            if (!(ok = wait_poll(barAe + na_i, (uint32_t)(na_g - 1) & 1u))) {
+                record_timeout(a.err, 1, 9, na_g);
+                break;
+            }
+            poll_a();
         }
         if (!ok) *abort = 1;
     } else if (t == 0 && work) {
-        // ---------------- MMA thread
+        // ---------------- MMA thread. Its own instructions are kept few (descriptors built once
+        // and advanced by constants): it shares its scheduler with four epilogue warps, and
+        // while it runs them the tensor pipe's short queue of MMAs drains.
         const uint32_t idesc = tc::idesc_f16(kFM, kFN);
+        // descriptors of K step 0 of A slot i and of B stage 0; a K step lies 256 bytes further
+        // (16 in the descriptor's address field, which holds address / 16), a stage b_bytes
+        uint64_t adesc[kFGT];
+#pragma unroll
+        for (int i = 0; i < kFGT; i++) adesc[i] = tc::smem_desc(tc::smem_addr(As + (size_t)i * a.a_bytes), tc::kLBO, a.sbo);
+        const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(Bs), tc::kLBO, a.sbo);
+        const uint64_t bstep = a.b_bytes >> 4;
+        const int ksteps = a.ksteps;
         bool ok = true;
-        int st = 0, g = 0;
+        int st = 0, u = 0;
         uint32_t use = 0;   // phase parity of stage st is use & 1
-        for (int it = 0; it < my_tiles && ok; it++) {
-            const int as = it & 1;
-            if (!(ok = tc::mbar_wait_or_abort(barA + as, (uint32_t)(it >> 1) & 1u, kWaitNs, abort))) {
-                record_timeout(a.err, 2, 1, g);
-                break;
-            }
-            const uint32_t abase = tc::smem_addr(As + (size_t)as * a.a_bytes);
-            for (int c = 0; c < nch; c++, g++) {
-                const int tb = g & 1;
-                ok = tc::mbar_wait_or_abort(barB + st, use & 1u, kWaitNs, abort);
-                if (!ok) { record_timeout(a.err, 2, 2, g); break; }
-                if (g >= 2)   // the epilogue of chunk g - 2 has released buffer tb
-                    ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((g - 2) >> 1) & 1u, a.free_wait_ns, abort);
-                if (!ok) { record_timeout(a.err, 2, 7, g); break; }
-                tc::fence_after_sync();
-                const uint32_t bbase = tc::smem_addr(Bs + (size_t)st * a.b_bytes);
-                for (int ks = 0; ks < a.ksteps; ks++) {
-                    const uint64_t ad = tc::smem_desc(abase + ks * 256, tc::kLBO, a.sbo);
-                    const uint64_t bd = tc::smem_desc(bbase + ks * 256, tc::kLBO, a.sbo);
-                    tc::mma_f16(tmem + (uint32_t)(tb * kFN), ad, bd, idesc, ks > 0 ? 1u : 0u);
+        uint64_t bdesc = bdesc0;
+        for (int gi = 0; gi < my_groups && ok; gi++) {
+            for (int c = 0; c < nch && ok; c++) {
+                if (!(ok = tc::mbar_wait_or_abort(barB + st, use & 1u, kWaitNs, abort))) {
+                    record_timeout(a.err, 2, 2, u);
+                    break;
                 }
-                tc::mma_commit(barD + tb);    // accumulators ready for the epilogue
+#pragma unroll
+                for (int i = 0; i < kFGT; i++, u++) {
+                    if (c == 0 && !(ok = tc::mbar_wait_or_abort(barA + i, (uint32_t)gi & 1u, kWaitNs, abort))) {
+                        record_timeout(a.err, 2, 1, u);
+                        break;
+                    }
+                    const int tb = u & 1;
+                    if (u >= 2 &&   // the epilogue of unit u - 2 has released buffer tb
+                        !(ok = tc::mbar_wait_or_abort(barE + tb, (uint32_t)((u - 2) >> 1) & 1u, a.free_wait_ns, abort))) {
+                        record_timeout(a.err, 2, 7, u);
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(tb * kFN);
+                    tc::mma_f16(d, adesc[i], bdesc, idesc, 0u);
+                    for (int ks = 1; ks < ksteps; ks++)
+                        tc::mma_f16(d, adesc[i] + 16u * (uint32_t)ks, bdesc + 16u * (uint32_t)ks, idesc, 1u);
+                    tc::mma_commit(barD + tb);                     // accumulators ready for the epilogue
+                    if (c == nch - 1) tc::mma_commit(barAe + i);   // the group's last MMAs on slot i
+                }
+                if (!ok) break;
                 tc::mma_commit(barBe + st);   // coefficient stage free for the copy thread
                 if (++st == S) {
                     st = 0;
                     use++;
+                    bdesc = bdesc0;
+                } else {
+                    bdesc += bstep;
                 }
             }
-            if (ok) tc::mma_commit(barAe + as);   // the tile's A stage may be refilled
         }
         if (!ok) *abort = 1;
     } else if (warp >= 4 && work) {
-        // ---------------- epilogue warps: set `set` takes the chunks g = set (mod kFEpiSets);
-        // its warp (q = lane quarter, p) reads columns (64 p + 64 r) (r < kFRounds) of the buffer
+        // ---------------- epilogue warps: set `set` takes the units u with u % kFEpiSets == set;
+        // its warp (q = lane quarter, p) reads columns (64 p kFRounds + 64 r) (r < kFRounds)
         const int e = warp - 4, q = warp & 3, set = e / (kFEpiWarps / kFEpiSets), p = (e % (kFEpiWarps / kFEpiSets)) >> 2;
         const long long words = a.n3 / 32;
         bool ok = true;
-        for (int it = 0; it < my_tiles && ok; it++) {
-            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-            const int zi = tile / a.tiles_per_z;
-            const long long word = (long long)(tile % a.tiles_per_z) * (kFM / 32) + q;   // cells 32 word .. + 31
-            // the first chunk of this tile that the set takes (chunk counters continue across tiles)
-            int c = (set - (it * nch) % kFEpiSets + kFEpiSets) % kFEpiSets;
-            for (; c < nch; c += kFEpiSets) {
-                const int g = it * nch + c, ms = g % kFMetaStages, tb = g & 1;
-                const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(g >> 1) & 1u, kWaitNs, abort);
-                const bool okM =
-                    okD && tc::mbar_wait_or_abort(barM + ms, (uint32_t)(g / kFMetaStages) & 1u, kWaitNs, abort);
-                if (!okM) {
-                    if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, g);
-                    *abort = 1;
-                    ok = false;
-                    break;
-                }
-                tc::fence_after_sync();
-                const unsigned char* meta = Ms + (size_t)ms * a.meta_bytes;
-#pragma unroll 1
-                for (int r = 0; r < kFRounds; r++) {
-                    const int col = p * 64 * kFRounds + r * 64;   // first column of this round
-                    float v0[32], v1[32];
-                    tc::tmem_ld32x2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kFN + col), v0, v1);
-                    if (r == kFRounds - 1) {
-                        tc::fence_before_sync();
-                        if (g != a.withhold) tc::mbar_arrive(barE + tb);   // accumulators read: buffer free
+        int k = 0;
+        for (int gi = 0; gi < my_groups && ok; gi++) {
+            const int grp = group_of(gi), zi = grp / groups_per_z;
+            for (int c = 0; c < nch && ok; c++, k++) {
+                const int ms = k % kFMetaStages;
+                for (int i = set; i < kFGT; i += kFEpiSets) {   // u % kFEpiSets == i % kFEpiSets (kFGT even)
+                    const int u = kFGT * k + i, tb = u & 1;
+                    const long long word = (long long)((grp * kFGT + i) % a.tiles_per_z) * (kFM / 32) + q;
+                    const bool okD = tc::mbar_wait_or_abort(barD + tb, (uint32_t)(u >> 1) & 1u, kWaitNs, abort);
+                    const bool okM =
+                        okD && tc::mbar_wait_or_abort(barM + ms, (uint32_t)(k / kFMetaStages) & 1u, kWaitNs, abort);
+                    if (!okM) {
+                        if (lane == 0) record_timeout(a.err, 3, okD ? 4 : 6, u);
+                        *abort = 1;
+                        ok = false;
+                        break;
                     }
-                    const int4* gm = reinterpret_cast<const int4*>(meta) + col / kGroup;
-                    const int m0 = gm[0].x, m1 = gm[1].x;
-                    if constexpr (POPS) {
-                        // a column does not flag iff D < 0 or D > width: the sign bit of D | (width - D)
-                        // (+inf for an infinite width), then the same AND of sign bits
-                        const float4* wd = reinterpret_cast<const float4*>(meta + kFRecBytes) + col / 4;
+                    tc::fence_after_sync();
+                    const unsigned char* meta = Ms + (size_t)ms * a.meta_bytes;
+                    // both rounds' reads first, with only the sign-bit ANDs between them, so that the
+                    // buffer is released as early as possible (the MMAs two units on wait for it);
+                    // the ballots and stores follow the release
+                    static_assert(kFRounds == 2, "two rounds per unit");
+                    uint32_t b00 = 0u, b01 = 0u, b10 = 0u, b11 = 0u;   // (round, 32-column group) ANDs
+#pragma unroll 1
+                    for (int r = 0; r < kFRounds; r++) {
+                        const int col = p * 64 * kFRounds + r * 64;   // first column of this round
+                        float v0[32], v1[32];
+                        tc::tmem_ld32x2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kFN + col), v0, v1);
+                        if (r == kFRounds - 1) {
+                            tc::fence_before_sync();
+                            // accumulators read: buffer free (one arrival per warp, not per thread: the
+                            // barrier takes 8 updates instead of 256)
+                            __syncwarp();
+                            if (lane == 0 && u != a.withhold) tc::mbar_arrive(barE + tb);
+                        }
+                        if constexpr (POPS) {
+                            // a column does not flag iff D < 0 or D > width: the sign bit of D | (width - D)
+                            // (+inf for an infinite width), then the same AND of sign bits
+                            const float4* wd = reinterpret_cast<const float4*>(meta + kFRecBytes) + col / 4;
 #pragma unroll
-                        for (int k = 0; k < 8; k++) {
-                            const float4 wa = wd[k], wb = wd[8 + k];
-                            const float xa[4] = {wa.x, wa.y, wa.z, wa.w}, xb[4] = {wb.x, wb.y, wb.z, wb.w};
+                            for (int kk = 0; kk < 8; kk++) {
+                                const float4 wa = wd[kk], wb = wd[8 + kk];
+                                const float xa[4] = {wa.x, wa.y, wa.z, wa.w}, xb[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
-                            for (int h = 0; h < 4; h++) {
-                                const int i = 4 * k + h;
-                                v0[i] = __uint_as_float(__float_as_uint(v0[i]) | __float_as_uint(xa[h] - v0[i]));
-                                v1[i] = __uint_as_float(__float_as_uint(v1[i]) | __float_as_uint(xb[h] - v1[i]));
+                                for (int hh = 0; hh < 4; hh++) {
+                                    const int ii = 4 * kk + hh;
+                                    v0[ii] = __uint_as_float(__float_as_uint(v0[ii]) | __float_as_uint(xa[hh] - v0[ii]));
+                                    v1[ii] = __uint_as_float(__float_as_uint(v1[ii]) | __float_as_uint(xb[hh] - v1[ii]));
+                                }
                             }
                         }
+                        const uint32_t x0 = and32(v0), x1 = and32(v1);
+                        if (r == 0) {
+                            b00 = x0;
+                            b01 = x1;
+                        } else {
+                            b10 = x0;
+                            b11 = x1;
+                        }
                     }
-                    // Eq. 1 flags: AND of the sign bits over the walker's radii above R_cell; the
-                    // second group of the pair continues the walker of the first when it is not a
-                    // first group (a two-group walker starts on an even group)
-                    const uint32_t a0 = and32(v0), a1 = and32(v1);
-                    const uint32_t w0 = __ballot_sync(0xffffffffu, (a0 >> 31) == 0u);
-                    const uint32_t w1 = __ballot_sync(0xffffffffu, (((m1 & 2) == 0 ? (a0 & a1) : a1) >> 31) == 0u);
-                    if (lane == 0) {
-                        if (m0 >= 0 && (m0 & 1)) a.flags[((size_t)(m0 >> 2) * a.n_z + zi) * words + word] = w0;
-                        if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
+#pragma unroll
+                    for (int r = 0; r < kFRounds; r++) {
+                        // Eq. 1 flags: AND of the sign bits over the walker's radii above R_cell; the
+                        // second group of the pair continues the walker of the first when it is not a
+                        // first group (a two-group walker starts on an even group)
+                        const int col = p * 64 * kFRounds + r * 64;
+                        const int4* gm = reinterpret_cast<const int4*>(meta) + col / kGroup;
+                        const int m0 = gm[0].x, m1 = gm[1].x;
+                        const uint32_t a0 = r == 0 ? b00 : b10, a1 = r == 0 ? b01 : b11;
+                        const uint32_t w0 = __ballot_sync(0xffffffffu, (a0 >> 31) == 0u);
+                        const uint32_t w1 = __ballot_sync(0xffffffffu, (((m1 & 2) == 0 ? (a0 & a1) : a1) >> 31) == 0u);
+                        if (lane == 0) {
+                            if (m0 >= 0 && (m0 & 1)) a.flags[((size_t)(m0 >> 2) * a.n_z + zi) * words + word] = w0;
+                            if (m1 >= 0 && (m1 & 1)) a.flags[((size_t)(m1 >> 2) * a.n_z + zi) * words + word] = w1;
+                        }
                     }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(barMe + ms);   // this unit has read the chunk's records (and widths)
                 }
-                tc::mbar_arrive(barMe + ms);   // the group records (and widths) of this chunk are read
             }
         }
     }
@@ -1061,7 +1110,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
             tc::mma_commit(barF);
             tc::mbar_wait(barF, 0, kWaitNs);
         } else if (t == 32) {   // wait for every bulk copy that may still land
-            for (int s = 0; s < 2; s++)
+            for (int s = 0; s < kFGT; s++)
                 if ((owedA >> (2 * s)) & 1u) tc::mbar_wait(barA + s, (owedA >> (2 * s + 1)) & 1u, kWaitNs);
             for (int s = 0; s < S; s++)
                 if ((owedB >> (2 * s)) & 1u) tc::mbar_wait(barB + s, (owedB >> (2 * s + 1)) & 1u, kWaitNs);
@@ -1087,13 +1136,13 @@ int f16_slots(const eor_ctx* c) {
 // so that one CTA holds an SM (and all of its tensor memory) at every basis size.
 size_t f16_smem(int kslots, bool pops, int stages) {
     const size_t a = (size_t)kFM * kslots * 2, b = (size_t)kFN * kslots * 2;
-    const size_t need = 2 * a + stages * b + kFMetaStages * (size_t)f16_meta_bytes(pops) +
-                        (4 + 2 * kFStagesMax + 2 * kFMetaStages + 4 + 1) * sizeof(uint64_t) + 16;
+    const size_t need = kFGT * a + stages * b + kFMetaStages * (size_t)f16_meta_bytes(pops) +
+                        (2 * kFGT + 2 * kFStagesMax + 2 * kFMetaStages + 4 + 1) * sizeof(uint64_t) + 16;
     return need > (120u << 10) ? need : (120u << 10);
 }
 
-// Four coefficient stages where they fit in 227 KB, else three.
-int f16_stages(int kslots, bool pops) { return f16_smem(kslots, pops, 4) <= (227u << 10) ? 4 : 3; }
+// Three coefficient stages where they fit in 227 KB, else two.
+int f16_stages(int kslots, bool pops) { return f16_smem(kslots, pops, 3) <= (227u << 10) ? 3 : 2; }
 
 }  // namespace
 
@@ -1112,8 +1161,8 @@ cudaError_t prepare_basis_f16(eor_ctx* c) {
     for (int pops = 0; pops < 2 && e == cudaSuccess; pops++) {
         const int st = f16_stages(c->k16, pops != 0);
         const int bytes = (int)f16_smem(c->k16, pops != 0, st);
-        auto k = pops ? (st == 4 ? k_basis_ionize_f16<true, 4> : k_basis_ionize_f16<true, 3>)
-                      : (st == 4 ? k_basis_ionize_f16<false, 4> : k_basis_ionize_f16<false, 3>);
+        auto k = pops ? (st == 3 ? k_basis_ionize_f16<true, 3> : k_basis_ionize_f16<true, 2>)
+                      : (st == 3 ? k_basis_ionize_f16<false, 3> : k_basis_ionize_f16<false, 2>);
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     }
     return e;
@@ -1172,12 +1221,13 @@ cudaError_t launch_basis_ionize_f16(eor_ctx* c) {
     const int stages = f16_stages(c->k16, pops);
     F16Args a{c->d_a16, c->d_b16, c->d_ncols, c->d_fwords, c->d_err, c->cfg.n_z, f16_slots(c) / kFN, tiles_per_z,
               c->k16 / 16, (uint32_t)(kFM * c->k16 * 2), (uint32_t)(kFN * c->k16 * 2), f16_sbo(c->k16),
-              f16_meta_bytes(pops), stages, (long long)c->n3, c->dbg_withhold,
+              f16_meta_bytes(pops), (long long)c->n3, c->dbg_withhold,
               c->dbg_withhold >= 0 ? c->dbg_wait_ns : kWaitNs};
-    const int grid = total < c->num_sms ? total : c->num_sms;
+    const int groups = total / kFGT;   // tiles per box are a multiple of kFGT (n >= 16)
+    const int grid = groups < c->num_sms ? groups : c->num_sms;
     trace_begin(c, kKBasis);
-    auto k = pops ? (stages == 4 ? k_basis_ionize_f16<true, 4> : k_basis_ionize_f16<true, 3>)
-                  : (stages == 4 ? k_basis_ionize_f16<false, 4> : k_basis_ionize_f16<false, 3>);
+    auto k = pops ? (stages == 3 ? k_basis_ionize_f16<true, 3> : k_basis_ionize_f16<true, 2>)
+                  : (stages == 3 ? k_basis_ionize_f16<false, 3> : k_basis_ionize_f16<false, 2>);
     k<<<grid, kFThreads, f16_smem(c->k16, pops, stages), c->stream>>>(a);
     trace_end(c);
     return cudaGetLastError();

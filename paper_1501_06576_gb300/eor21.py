@@ -406,9 +406,9 @@ class Context:
         self._check(self.lib.eor_contraction_info(self.handle, ctypes.byref(k), ctypes.byref(ks)))
         return k.value, ks.value
 
-    def eor_debug_withhold(self, chunk: int, wait_ms: float = 1.0):
-        """Test-only: make the contraction withhold one accumulator release (chunk < 0: off)."""
-        self._check(self.lib.eor_debug_withhold(self.handle, int(chunk), float(wait_ms)))
+    def eor_debug_withhold(self, step: int, wait_ms: float = 1.0):
+        """Test-only: make the contraction withhold one accumulator release (step < 0: off)."""
+        self._check(self.lib.eor_debug_withhold(self.handle, int(step), float(wait_ms)))
 
     def eor_trace(self, enable: bool = True):
         self._check(self.lib.eor_trace(self.handle, 1 if enable else 0))

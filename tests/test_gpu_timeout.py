@@ -1,11 +1,12 @@
 """A bounded device wait that runs out is reported, and leaves the GPU usable.
 
 Every wait of the tensor-core contraction is bounded in GPU time; when one gives up, the CTA
-records where (role, barrier, chunk), stops issuing, waits for its MMAs and bulk copies in
+records where (role, barrier, step), stops issuing, waits for its MMAs and bulk copies in
 flight, frees its tensor memory and exits, and the host sees EOR_ETIMEOUT. The test makes
 that happen without a GPU fault: the test-only switch eor_debug_withhold makes the
-epilogue keep back its release of the accumulator buffer of chunk 0, so the MMA thread's
-wait before chunk 2 (the same buffer) runs out after 1 ms. Nothing asynchronous is made to
+epilogue keep back its release of the accumulator buffer of step 0 (the first coefficient
+chunk against the first cell tile), so the MMA thread's wait before step 2 (the same
+buffer) runs out after 1 ms. Nothing asynchronous is made to
 time out. Then the context is destroyed, and a fresh context gives the same chi^2 as one
 that never saw the fault.
 """
@@ -17,7 +18,7 @@ from paper_1501_06576_gb300 import eor21, synth
 pytestmark = pytest.mark.gpu
 
 N, BOX, ZS = 32, 60.0, (9.0,)
-WALKERS = 12          # 12 walkers x one 32-column group each = 384 columns = 3 chunks of 128
+WALKERS = 12          # 12 walkers x one 32-column group each = 384 columns = 2 chunks of 256
 
 
 def _inputs():
@@ -47,7 +48,7 @@ def test_withheld_release_times_out_and_context_recovers():
     with pytest.raises(eor21.EorError) as e:
         ctx.likelihood(params, mock, 0.2 * mock)
     assert e.value.code == eor21.EOR_ETIMEOUT
-    assert "role 2, barrier 7, chunk 2" in str(e.value), str(e.value)
+    assert "role 2, barrier 7, step 2" in str(e.value), str(e.value)
     ctx.close()                                   # eor_destroy after the timeout
 
     with eor21.Context(n=N, box_mpc=BOX, z=ZS, max_walkers=WALKERS) as fresh:
