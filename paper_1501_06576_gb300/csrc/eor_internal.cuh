@@ -48,9 +48,11 @@ struct PairInfo {
 // "erfcc"; fractional error below 1.2e-7 everywhere): t = 1 / (1 + x/2) and
 // erfc(x) = t exp(-x^2 + P(t)) with P a degree-9 polynomial. Branch-free. The exponential is
 // CUDA's fast __expf (a few ulp, and |-x^2 + P| of at most ~30 for the arguments that matter:
-// below 2e-6 relative in erfc, 2e-6 of x_HI at most).
+// below 2e-6 relative in erfc, 2e-6 of x_HI at most) and the reciprocal CUDA's fast
+// __fdividef (about 2 ulp in t: a few 1e-7 relative in erfc). The correctly rounded
+// reciprocal made this function about a third of the pencil pass's instructions.
 __device__ __forceinline__ float erfc_cheb(float x) {
-    const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+    const float t = __fdividef(1.0f, fmaf(0.5f, x, 1.0f));
     float p = 0.17087277f;
     p = fmaf(p, t, -0.82215223f);
     p = fmaf(p, t, 1.48851587f);

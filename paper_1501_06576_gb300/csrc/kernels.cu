@@ -206,6 +206,11 @@ struct PSArgs {
 
 constexpr int kPrivBins = 16;   // bins kept in per-thread shared-memory slots
 
+// |m|^3 of a mode from m2 = |m|^2 >= 1 (every binned mode): m2^2 / sqrt(m2) with the fast
+// reciprocal square root (a few 1e-7 relative; the correctly rounded sqrtf takes a longer
+// instruction sequence, once per mode of every plane)
+__device__ __forceinline__ float k3_of(float fm2) { return fm2 * fm2 * rsqrtf(fm2); }
+
 // The CTA's shell sums from the per-thread slots priv[b][T]: warp w takes bins w, w + T/32,
 // ...; each lane adds its slots, then a shuffle tree, in FP32 (this GPU issues FP64 at a few
 // operations per clock per SM: a per-slot FP64 sum cost as much as the transforms), and the
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(Plane<N, T>::THREADS, 1) k_plane_ps(PSArgs a) 
                 if (b >= 0) {
                     const float2 v = hold[l][q][k2];
                     const float fm2 = (float)m2;
-                    const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (v.x * v.x + v.y * v.y);
+                    const float val = weight * a.kf3 * k3_of(fm2) * (v.x * v.x + v.y * v.y);
                     if (priv_ok) priv[b * P::THREADS + threadIdx.x] += val;
                     else atomicAdd(&s_bins[b], (double)val);
                 }
@@ -392,7 +397,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPs2Threads, 2) k_pl
                 if (b >= 0) {
                     const float2 u = hold[q][k2];
                     const float fm2 = (float)m2;
-                    priv[b * kPs2Threads + t] += weight * a.kf3 * fm2 * sqrtf(fm2) * (u.x * u.x + u.y * u.y);
+                    priv[b * kPs2Threads + t] += weight * a.kf3 * k3_of(fm2) * (u.x * u.x + u.y * u.y);
                 }
             }
         }
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(kLThreads) k_lines_cols(LineArgs a) {
             if (b >= 0) {
                 const float2 v = hold[k2];
                 const float fm2 = (float)m2;
-                const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (v.x * v.x + v.y * v.y);
+                const float val = weight * a.kf3 * k3_of(fm2) * (v.x * v.x + v.y * v.y);
                 if (priv_ok) priv[b * kLThreads + threadIdx.x] += val;
                 else atomicAdd(&s_bins[b], (double)val);
             }
@@ -664,12 +669,19 @@ __device__ __forceinline__ void pencil_r2c(const PencilSmem<N>& s, int p, int i,
         for (int k2 = 0; k2 < P::P2; k2++) s.xs[(k1 + P::P1 * k2) * P::TY + p] = b[k2];   // Z natural
     }
     __syncthreads();
-    for (int k = i; k <= P::M; k += P::P2) {
-        const float2 zk = s.xs[(k % P::M) * P::TY + p];
-        const float2 zm = cconj(s.xs[((P::M - k) % P::M) * P::TY + p]);
+    // the split in pairs (k, M - k), one pair per two loads and one twiddle:
+    // X[k] = E - (i/2) D, X[M - k] = conj(E) - (i/2) conj(D), E = (Z[k] + conj Z[M-k]) / 2,
+    // D = (Z[k] - conj Z[M-k]) w_N^k (Z[M] = Z[0]; X[M] = E + (i/2) D at k = 0)
+    for (int k = i; 2 * k <= P::M; k += P::P2) {
+        const float2 zk = s.xs[k * P::TY + p];
+        const float2 zm = cconj(s.xs[((P::M - k) & (P::M - 1)) * P::TY + p]);
         const float2 e = cscale(cadd(zk, zm), 0.5f);
         const float2 d = cmul(csub(zk, zm), tw_get<N, -1>(s.tw, k));
-        dst[(size_t)k * kstride + p] = make_float2(e.x + 0.5f * d.y, e.y - 0.5f * d.x);   // e - (i/2) d
+        dst[(size_t)k * kstride + p] = make_float2(e.x + 0.5f * d.y, e.y - 0.5f * d.x);
+        if (k == 0)
+            dst[(size_t)P::M * kstride + p] = make_float2(e.x - 0.5f * d.y, e.y + 0.5f * d.x);
+        else if (2 * k != P::M)
+            dst[(size_t)(P::M - k) * kstride + p] = make_float2(e.x - 0.5f * d.y, -e.y - 0.5f * d.x);
     }
 }
 
@@ -868,6 +880,40 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_forward_batch(con
     pencil_r2c<N>(s, p, i, z, dst + (size_t)slot * NH * N * N + (size_t)x * N + y0, (size_t)N * N);
 }
 
+// round(v 2^23) for v in [0, 1], as __float2int_rn(v * 2^23) gives it, without the
+// conversion unit: v 2^23 + 2^23 lies in [2^23, 2^24], where the float spacing is 1, so the
+// fused multiply-add rounds to the nearest integer (ties to even) and its bits minus those of
+// 2^23 are that integer.
+__device__ __forceinline__ int fixed23(float v) {
+    return __float_as_int(fmaf(v, 8388608.0f, 8388608.0f)) - 0x4B000000;
+}
+
+// x_HI of four cells (Sec. 2.1): 0 where a radius above R_cell flagged the cell (bit h of
+// `bits`), else 1 - min(1, zeta f_coll(R_cell)) with f_coll = erfc((delta_c - delta_Rcell) inv),
+// inv = 1 / sqrt(2 s^2) (f_coll = 1 where delta_Rcell >= delta_c; x_HI = 1 where s^2 <= 0, inv
+// = 0), or with a mass-dependent efficiency 1 - min(1, F) from the pair's table `ftab` of the
+// efficiency-weighted collapsed fraction at nu = delta_c - delta_Rcell. The step-function form
+// is branch-free, its four erfc evaluations independent: a per-cell branch around them cost
+// more than the evaluations it skipped.
+__device__ __forceinline__ void xhi4(uint32_t bits, const float (&dc)[4], float delta_c, float zeta, float inv,
+                                     const float* ftab, float f_inv_h, float (&xh)[4]) {
+    if (ftab) {
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const float nu = delta_c - dc[h];
+            xh[h] = ((bits >> h) & 1u) ? 0.0f : 1.0f - fminf(1.0f, pop_table_f(ftab, nu, f_inv_h));
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const float nu = delta_c - dc[h];
+            const float fe = erfc_cheb(fmaxf(nu, 0.0f) * inv);
+            const float v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * (nu <= 0.0f ? 1.0f : fe)) : 1.0f;
+            xh[h] = ((bits >> h) & 1u) ? 0.0f : v;
+        }
+    }
+}
+
 struct BrightArgs {
     const uint32_t* fwords;     // [pair][n3 / 32] Eq. 1 flags above R_cell (bit = cell % 32)
     const PairInfo* pairs;
@@ -931,22 +977,11 @@ __global__ void __launch_bounds__(Pencil<N>::THREADS) k_pencil_brightness(Bright
         if (e >= V) continue;
         const float dd[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w}, dc[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
         float xh[4], tb[4];
+        xhi4(bits[k], dc, a.delta_c, zeta, inv, a.ftab ? ftab : nullptr, pi.f_inv_h, xh);
 #pragma unroll
         for (int h = 0; h < 4; h++) {
-            const bool flagged = (bits[k] >> h) & 1u;
-            const float nu = a.delta_c - dc[h];
-            float v = 0.0f;
-            if (!flagged) {   // (ionized regions are coherent: a warp's 128 cells are one z-pencil)
-                if (a.ftab) {
-                    v = 1.0f - fminf(1.0f, pop_table_f(ftab, nu, pi.f_inv_h));
-                } else {
-                    const float f = nu <= 0.0f ? 1.0f : erfc_cheb(nu * inv);
-                    v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
-                }
-            }
-            xh[h] = v;
-            tb[h] = t0 * v * (1.0f + dd[h]);
-            xq += __float2int_rn(v * 8388608.0f);
+            tb[h] = t0 * xh[h] * (1.0f + dd[h]);
+            xq += fixed23(xh[h]);
         }
         const int pp = (4 * e) / N, zz = (4 * e) % N;
         float2* d = reinterpret_cast<float2*>(s.ds + pp * P::DS + zz);
@@ -1127,22 +1162,11 @@ __global__ void __launch_bounds__(Slab<N>::THREADS, 3) k_slab_ps(SlabArgs a) {
                 const int e = t + (k0 + k) * T;
                 const float dd[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w}, dc[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
                 float xh[4], tb[4];
+                xhi4(bits[k], dc, a.delta_c, zeta, inv, a.ftab ? ftab : nullptr, pi.f_inv_h, xh);
 #pragma unroll
                 for (int h = 0; h < 4; h++) {
-                    const bool flagged = (bits[k] >> h) & 1u;
-                    const float nu = a.delta_c - dc[h];
-                    float v = 0.0f;
-                    if (!flagged) {
-                        if (a.ftab) {
-                            v = 1.0f - fminf(1.0f, pop_table_f(ftab, nu, pi.f_inv_h));
-                        } else {
-                            const float f = nu <= 0.0f ? 1.0f : erfc_cheb(nu * inv);
-                            v = inv > 0.0f ? 1.0f - fminf(1.0f, zeta * f) : 1.0f;
-                        }
-                    }
-                    xh[h] = v;
-                    tb[h] = t0 * v * (1.0f + dd[h]);
-                    xq += __float2int_rn(v * 8388608.0f);
+                    tb[h] = t0 * xh[h] * (1.0f + dd[h]);
+                    xq += fixed23(xh[h]);
                 }
                 const int y = (4 * e) / N, z = (4 * e) % N;
                 float2* d = reinterpret_cast<float2*>(re + 2 * ZS * y + z);
@@ -1298,7 +1322,7 @@ __global__ void __launch_bounds__(XLine<N>::THREADS) k_xline_ps(PSArgs a) {
             const int b = a.bin_of_m2[m2];
             if (b >= 0) {
                 const float fm2 = (float)m2;
-                const float val = weight * a.kf3 * fm2 * sqrtf(fm2) * (w[k2].x * w[k2].x + w[k2].y * w[k2].y);
+                const float val = weight * a.kf3 * k3_of(fm2) * (w[k2].x * w[k2].x + w[k2].y * w[k2].y);
                 if (priv_ok) priv[b * T + t] += val;
                 else atomicAdd(&s_bins[b], (double)val);
             }

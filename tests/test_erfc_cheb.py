@@ -17,9 +17,10 @@ def coefficients():
     body = text[text.index("float erfc_cheb(float x)"):]
     body = body[:body.index("\n}\n")]
     lits = [float(v) for v in re.findall(r"(-?\d+\.\d+)f", body)]
-    # t = 1 / (1 + 0.5 x) first, then the ten polynomial coefficients from the top
-    assert lits[:2] == [0.5, 1.0]
-    return lits[2:]
+    # t = 1 / (1 + 0.5 x) first (the numerator, then the fmaf's 0.5 and 1), then the ten
+    # polynomial coefficients from the top
+    assert lits[:3] == [1.0, 0.5, 1.0]
+    return lits[3:]
 
 
 def erfc_cheb64(x, c):
