@@ -260,26 +260,39 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def basis_source_hash() -> str:
-    """Hash of the sources of the contraction kernels (a stale traffic record is not used)."""
+# the sources of each traced kernel class: a traffic record taken before a change to them is
+# not used
+CLASS_SOURCES = {
+    "basis_ionize": ("basis.cu", "tcgen05.cu", "tc.cuh"),
+    "forward_fft": ("kernels.cu", "fft_core.cuh", "eor_internal.cuh"),
+    "ps_plane": ("kernels.cu", "fft_core.cuh", "eor_internal.cuh"),
+}
+
+
+def class_source_hash(kernel_class: str) -> str:
+    """Hash of the sources of a kernel class's kernels."""
     h = hashlib.sha256()
-    for name in ("basis.cu", "tcgen05.cu", "tc.cuh"):
+    for name in CLASS_SOURCES[kernel_class]:
         with open(os.path.join(ROOT, "paper_1501_06576_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_launch_traffic(kernel_class: str, walkers: int):
-    """DRAM bytes of one full launch from the committed ncu capture, or None if the kernel
-    source or the workload differs from the capture's."""
+def ncu_launch_traffic(kernel_class: str, units: float, ps_split=None):
+    """DRAM bytes (read + write) of one launch that processes `units` units of its class, from
+    the committed ncu capture (bytes per unit, as measured on a launch of the same grid size
+    n and spectrum tiling), or None if the class's sources, the grid or the tiling (the
+    spectrum's classes run different kernels per tiling) differ from the capture's."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d["per_launch"][kernel_class]
-        if d.get("basis_source_hash") != basis_source_hash() or e["walkers"] != walkers or e["n"] != N:
+        e = d["per_class"][kernel_class]
+        if e["source_hash"] != class_source_hash(kernel_class) or e["n"] != N:
             return None
-        return e["bytes"]
+        if "ps_split" in e and e["ps_split"] != ps_split:
+            return None
+        return e["bytes_per_unit"] * units
     except Exception:
         return None
 
@@ -813,7 +826,7 @@ def main():
                     peak, peak_kind = fp32_peak_tflops(), "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
                     extra, bound = {}, "alu"
                 kernel_rates[cls] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                     "frac": achieved / peak, "traffic": ncu_launch_traffic(cls, W), "kernel": cls,
+                                     "frac": achieved / peak, "traffic": ncu_launch_traffic(cls, units), "kernel": cls,
                                      "peak_kind": peak_kind, "flops_per_unit": flops_per_unit,
                                      "unit_def": "one (walker, redshift, radius) over all cells",
                                      "units_per_launch": units, "avg_launch_ms": avg_ms, **extra}
@@ -834,7 +847,8 @@ def main():
                 units = pairs_per_step * args.steps / launches_c
                 achieved = per_unit * units / (avg_ms / 1e3) / 1e9
                 kernel_rates[cls] = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak_v, "unit": "GB/s",
-                                     "frac": achieved / hbm_peak_v, "traffic": None, "kernel": cls,
+                                     "frac": achieved / hbm_peak_v,
+                                     "traffic": ncu_launch_traffic(cls, units, schedule.get("ps_split")), "kernel": cls,
                                      "peak_kind": hbm_kind_v, "bytes_per_unit": per_unit, "unit_def": udef,
                                      "units_per_launch": units, "avg_launch_ms": avg_ms}
         dom = max((k for k in class_ms if k in kernel_rates), key=lambda k: class_ms[k])

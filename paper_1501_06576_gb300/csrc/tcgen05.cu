@@ -650,14 +650,17 @@ constexpr uint32_t kFRecBytes = kFGroups * 16;  // group records
 constexpr uint32_t kFWidthBytes = kFN * 4;      // per column t (delta_hi - delta_crit) (mass-dependent efficiency)
 constexpr uint32_t f16_meta_bytes(bool pops) { return kFRecBytes + (pops ? kFWidthBytes : 0u); }
 constexpr int kFEpiWarps = 16;                  // four per tensor-memory lane quarter
-constexpr int kFEpiSets = 2;                    // epilogue warp sets, alternating units (each on its own buffer)
+#ifndef EOR_F16_EPI_SETS
+#define EOR_F16_EPI_SETS 2
+#endif
+constexpr int kFEpiSets = EOR_F16_EPI_SETS;     // epilogue warp sets, alternating units (1 or 2)
 constexpr int kFSetWarps = kFEpiWarps / kFEpiSets;   // warps of one set: one arrival each on the set's barriers
-constexpr int kFRounds = 2;                     // 64-column rounds of an epilogue warp per unit
+constexpr int kFRounds = kFEpiSets;             // 64-column rounds of an epilogue warp per unit
 constexpr int kFThreads = 128 + 32 * kFEpiWarps;
 constexpr uint32_t kFTmemCols = 2 * kFN;        // two accumulator buffers
 constexpr float kFScale = 16384.0f;             // 2^14
 static_assert(kFTmemCols <= 512, "tensor memory");
-static_assert(kFN == 8 * kGroup && kFEpiWarps == 16 && kFEpiSets == 2,
+static_assert(kFN == 8 * kGroup && kFEpiWarps == 16 && (kFEpiSets == 1 || kFEpiSets == 2),
               "epilogue: a set's warp (q, p) reads 64 kFRounds columns of lane quarter q, 64 per round");
 
 __host__ __device__ constexpr int f16_kslots(int rank) { return (3 * (rank + 1) + 15) / 16 * 16; }
@@ -1042,7 +1045,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_basis_ionize_f16(F16Args a) {
                     // both rounds' reads first, with only the sign-bit ANDs between them, so that the
                     // buffer is released as early as possible (the MMAs two units on wait for it);
                     // the ballots and stores follow the release
-                    static_assert(kFRounds == 2, "two rounds per unit");
+                    static_assert(kFRounds <= 2, "at most two rounds per unit");
                     uint32_t b00 = 0u, b01 = 0u, b10 = 0u, b11 = 0u;   // (round, 32-column group) ANDs
 #pragma unroll 1
                     for (int r = 0; r < kFRounds; r++) {

@@ -37,15 +37,16 @@ def test_two_pop_rates_without_classes(bench):
 
 
 def test_traffic_record_used_only_for_its_sources(bench):
-    # the committed ncu record feeds roofline.traffic only while the contraction sources
-    # hash to the recorded value and the workload is the recorded one; otherwise None
+    # the committed ncu record feeds roofline.traffic (bytes per unit x the launch's units) only
+    # while the class's sources hash to the recorded value and the grid is the recorded one
     with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
         rec = json.load(f)
-    e = rec["per_launch"]["basis_ionize"]
-    assert e["bytes"] == e["read"] + e["write"]
-    got = bench.ncu_launch_traffic("basis_ionize", e["walkers"])
-    if rec["basis_source_hash"] == bench.basis_source_hash() and e["n"] == bench.N:
-        assert got == e["bytes"]
-    else:
-        assert got is None
-    assert bench.ncu_launch_traffic("basis_ionize", e["walkers"] + 1) is None
+    for cls, e in rec["per_class"].items():
+        assert e["bytes_per_unit"] == pytest.approx((e["read"] + e["write"]) / e["units"])
+        got = bench.ncu_launch_traffic(cls, 10.0, e.get("ps_split"))
+        if e["source_hash"] == bench.class_source_hash(cls) and e["n"] == bench.N:
+            assert got == pytest.approx(10.0 * e["bytes_per_unit"])
+        else:
+            assert got is None
+    assert bench.ncu_launch_traffic("no_such_class", 1.0) is None
+    assert bench.ncu_launch_traffic("ps_plane", 1.0, 2) is None   # another tiling's kernels
