@@ -248,11 +248,12 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
  * EOR_METHOD_BASIS (default): every walker's filtered fields are assembled from a small
  *   set of basis fields F_b = IDFT(phi_b delta_hat), built once per density box, with the
  *   top-hat W(kR) = sum_b c_b(R) phi_b(k) to 1e-6 on the grid's |k| for every R in
- *   [R_cell, r_mfp_max]; the threshold, OR over radii, x_HI and delta T_b are fused into
- *   that contraction, which runs on the tensor cores (tcgen05, FP32 accumulation) on
+ *   [R_cell, r_mfp_max]; the threshold and the OR over radii are fused into that
+ *   contraction, which runs on the tensor cores (tcgen05, FP32 accumulation) on
  *   power-of-two-scaled FP16 operands split into hi + lo parts (three products side by side
  *   along K) when the basis has at most 31 functions, else on the FP32 units; it yields the
- *   Eq. 1 flags, and x_HI, delta T_b and the spectrum follow in the pencil and plane passes.
+ *   Eq. 1 flags, and x_HI, delta T_b and the spectrum follow in the spectrum's passes
+ *   (eor_set_ps_split), delta T_b never stored.
  * EOR_METHOD_BASIS_TF32: the same contraction on TF32 hi + lo operands (three products per
  *   K step of 8, x_HI and delta T_b in its epilogue): the previous form, kept for comparison
  *   (its operands are allocated when it is chosen).
