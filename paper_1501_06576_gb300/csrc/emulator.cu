@@ -32,7 +32,6 @@ constexpr int kIn = 4;                                 // zeta, R_mfp, log10 T_v
 constexpr int kMaxLayers = EOR21_EMU_MAX_HIDDEN + 1;
 constexpr int kLossHist = 64;                          // ring of per-step minibatch losses
 constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
-constexpr int kGemmTile = 64, kGemmK = 16, kGemmThreads = 256;
 
 // Parameter layout of one member.
 struct Layout {
@@ -82,75 +81,6 @@ __device__ __forceinline__ float gelu_grad_f(float u) {
 }
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_emu_gemm(GemmArgs g) {
-    // rows padded to 68 floats: 16-byte aligned for the float4 reads below
-    __shared__ __align__(16) float As[kGemmK][kGemmTile + 4];   // [k][m]
-    __shared__ __align__(16) float Bs[kGemmK][kGemmTile + 4];   // [k][n]
-    const int e = blockIdx.z, m0 = blockIdx.y * kGemmTile, n0 = blockIdx.x * kGemmTile;
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const float* A = g.A + e * g.ae;
-    const float* B = g.B + e * g.be;
-    const bool a_kfast = g.ak == 1, b_nfast = g.bn == 1;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
-    for (int k0 = 0; k0 < g.K; k0 += kGemmK) {
-#pragma unroll
-        for (int i = 0; i < (kGemmTile * kGemmK) / kGemmThreads; i++) {
-            const int idx = t + i * kGemmThreads;
-            // consecutive threads walk the operand's unit-stride index (coalesced loads)
-            int mm, kk;
-            if (a_kfast) { kk = idx & (kGemmK - 1); mm = idx / kGemmK; }
-            else { mm = idx & (kGemmTile - 1); kk = idx / kGemmTile; }
-            int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.am + k * g.ak] : 0.0f;
-            int nn;
-            if (b_nfast) { nn = idx & (kGemmTile - 1); kk = idx / kGemmTile; }
-            else { kk = idx & (kGemmK - 1); nn = idx / kGemmK; }
-            const int n = n0 + nn;
-            k = k0 + kk;
-            Bs[kk][nn] = (n < g.N && k < g.K) ? B[k * g.bk + n * g.bn] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGemmK; kk++) {
-            const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-            const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-            const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= g.M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= g.N) continue;
-            float v = acc[i][j];
-            const long long ci = e * g.ce + m * g.cm + n;
-            if (EPI == kEpiLinear) {
-                v += g.bias[e * g.bias_e + n];
-            } else if (EPI == kEpiGelu) {
-                v += g.bias[e * g.bias_e + n];
-                g.pre_out[e * g.pre_e + m * g.pre_m + n] = v;
-                v = gelu_f(v);
-            } else if (EPI == kEpiGeluGrad) {
-                v *= gelu_grad_f(g.pre[e * g.pre_e + m * g.pre_m + n]);
-            }
-            g.C[ci] = v;
-        }
-    }
-}
 
 // The same GEMM on the 5th-generation tensor cores: one CTA computes a 128 x NT tile of C
 // (MMA M = 128, N = NT) for member blockIdx.z with tcgen05 kind::tf32 MMAs accumulating in
