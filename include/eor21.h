@@ -233,7 +233,8 @@ int eor_get_tuning(const eor_ctx* ctx, int* group, int* pairs, int* plane_thread
  * the spectrum's transforms and partial sums): times eor_likelihood on
  * these walkers (arguments as there, n_walkers <= max_walkers) with CUDA events on the
  * context's stream, `reps` graph replays per candidate after one warm-up, over the
- * candidates of the current method -- pairs in {4, 8, 16, 32} x the spectrum's tiling
+ * candidates of the current method -- pairs in {4, 8, 16, 32} (and 64 for the basis methods
+ * with more than 32 (walker, redshift) pairs) x the spectrum's tiling
  * (split 0 at n <= 128; 128^3 grids also split 2, and split 1 with plane_threads 512 or
  * 1024; split 1 and 512 otherwise) x ps_streams in {2, 1}, and for EOR_METHOD_DIRECT (one
  * stream, splits 1 and 2) also group in {4, 8, 16} and plane_threads -- and keeps the

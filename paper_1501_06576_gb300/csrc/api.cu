@@ -707,8 +707,9 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
     struct Cand { int group, pairs, threads, split, streams; };
     std::vector<Cand> cands;
     const int groups_direct[] = {4, 8, 16};
-    const int pairs_list[] = {4, 8, 16, 32};
+    const int pairs_list[] = {4, 8, 16, 32, 64};
     const bool direct = c->tune.method == eor::kMethodDirect;
+    const int n_pairs = n_walkers * c->cfg.n_z;
     for (int streams : {2, 1}) {
         if (streams == 2 && direct) continue;   // the direct method's passes run in one stream
         for (int split : {0, 2, 1}) {
@@ -718,6 +719,8 @@ int eor_autotune(eor_ctx* c, const double* params, int n_walkers, const double* 
                 if (th == 1024 && c->n != 128) continue;
                 if (th == 1024 && split != 1 && !direct) continue;   // the CTA size then changes no kernel of the step
                 for (int p : pairs_list) {
+                    // 64 pairs in flight: the basis methods, and only with more than 32 pairs to run
+                    if (p == 64 && (direct || n_pairs <= 32)) continue;
                     if (direct)
                         for (int gsz : groups_direct) cands.push_back({gsz, p, th, split, streams});
                     else

@@ -28,7 +28,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(method):
     sigma = 0.2 * mock
     before, d2_before = ctx.likelihood(params, mock, sigma, want_d2=True)
     g, p, t, ms = ctx.autotune(params, mock, sigma, reps=2)
-    assert p in (4, 8, 16, 32) and t == 512 and ms > 0
+    assert p in (4, 8, 16, 32) and t == 512 and ms > 0   # 64 only with more than 32 pairs to run
     assert g in ((4, 8, 16) if method == eor21.EOR_METHOD_DIRECT else (8,))
     after, d2_after = ctx.likelihood(params, mock, sigma, want_d2=True)
     # the spectrum's tiling may change with the schedule: the same sums up to FP32 rounding

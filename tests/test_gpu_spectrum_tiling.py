@@ -62,6 +62,28 @@ def test_slab_passes_match_plane_passes(n, box, form):
         assert 0.0 < float(np.mean(ref[1])) < 1.0
 
 
+@pytest.mark.parametrize("pairs", [1, 4, 5])
+@pytest.mark.parametrize("n,box", [(32, 64.0), (128, 250.0)])
+def test_slab_pipeline_batches(n, box, pairs):
+    """The slab passes over several batches of pairs (the x-line pass of one batch on the
+    second stream while the slab pass of the next fills the other half of the intermediate
+    buffer), a ragged last batch (7 pairs in batches of 4 or 5) and one pair per batch give the
+    same x_HI and spectra as the plane passes."""
+    zs = (8.0, 9.0, 10.0, 11.0, 12.0, 13.0, 14.0)[: 7 if n == 32 else 1]
+    walkers = 1 if n == 32 else 7
+    params = synth.walker_params(walkers, seed=pairs + n)
+    with eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=walkers) as ctx:
+        ctx.init_boxes(synth.density_boxes(n, box, zs, seed=n + pairs))
+        ctx.set_params(params)
+        ref = run(ctx, 1)
+        ctx.set_tuning(8, pairs, 512)
+        got = run(ctx, 0)
+    np.testing.assert_allclose(got[0], ref[0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(got[1], ref[1], rtol=0, atol=1e-7)
+    np.testing.assert_array_equal(got[3], ref[3])
+    close_spectra(got[2], ref[2])
+
+
 def test_slab_passes_many_bins_and_one_walker():
     """40 bins (more than the per-thread slots of the x-line pass: its shell sums then go
     through shared-memory atomics) and a ragged batch (one pair in flight of 16)."""
