@@ -882,7 +882,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": N, "box_mpc": BOX, "z": list(ZS), "walkers_per_gpu": W,
                        "radius_tasks_per_step": tasks_per_step, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"walkers sharded over {world} GPU(s)", "traced": not args.no_trace,
-                       "schedule": {**schedule, "picked_by": "eor_autotune"}},
+                       "schedule": {**schedule,
+                                    "picked_by": "library default (--no-autotune)" if args.no_autotune else "eor_autotune"}},
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "kernel_rates": kernel_rates,
             "method": {"name": "basis", "rank": basis_rank, "max_residual": basis_resid,
