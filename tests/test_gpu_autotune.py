@@ -89,3 +89,27 @@ def test_power_spectrum_plane_tiling_does_not_change_results():
         small.set_ps_split(2)
     assert ei.value.code == eor21.EOR_ENOTSUP
     small.close()
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_pairs_in_flight_do_not_change_results(split):
+    """36 (walker, redshift) pairs at 32^3 with 1, 4, 16 and 64 pairs per spectrum launch (64:
+    the autotuner's largest candidate, one ragged batch): chi^2 and every Delta^2 bin agree up
+    to the order of the FP64 additions across CTAs."""
+    n, box, zs = 32, 64.0, (8.0, 9.0, 10.0)
+    ctx = eor21.Context(n=n, box_mpc=box, z=zs, max_walkers=12)
+    ctx.init_boxes(synth.density_boxes(n, box, zs, seed=21))
+    params = synth.walker_params(12, seed=22)
+    mock = np.full((3, 14), 20.0)
+    sigma = 0.2 * mock
+    ctx.set_ps_split(split)
+    out = {}
+    for pairs in (1, 4, 16, 64):
+        ctx.set_tuning(8, pairs, 512)
+        assert ctx.get_tuning()["pairs"] == pairs and ctx.get_tuning()["ps_split"] == split
+        out[pairs] = ctx.likelihood(params, mock, sigma, want_d2=True)
+    for pairs in (1, 4, 64):
+        np.testing.assert_allclose(out[pairs][0], out[16][0], rtol=1e-12)
+        np.testing.assert_allclose(out[pairs][1], out[16][1], rtol=1e-12, equal_nan=True)
+    assert np.all(np.isfinite(out[64][0]))
+    ctx.close()
