@@ -204,7 +204,8 @@ int eor_noise_sigma(eor_ctx* ctx, const double* mock_d2, const float* thermal, d
 
 /* Launch schedule of eor_run_ionization / eor_likelihood (results do not depend on it):
  * group = radii per pencil launch (1..16), pairs = (walker, redshift) pairs in flight
- * (1..64; scratch memory grows with group * pairs), plane_threads = CTA size of the
+ * (1..64; scratch memory grows with pairs, and with group * pairs while EOR_METHOD_DIRECT
+ * is chosen), plane_threads = CTA size of the
  * 128^3 plane kernels (512 or 1024; ignored for smaller grids). Defaults 8, 16, 512.
  * Reallocates the scratch buffers and drops the captured graph. */
 int eor_set_tuning(eor_ctx* ctx, int group, int pairs, int plane_threads);
@@ -259,7 +260,9 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
  *   K step of 8, x_HI and delta T_b in its epilogue): the previous form, kept for comparison
  *   (its operands are allocated when it is chosen).
  * EOR_METHOD_BASIS_SIMT: the same contraction on the FP32 units only.
- * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius.
+ * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius
+ *   (its group x pairs half spectra of scratch are allocated when it is chosen and released
+ *   when another method is; EOR_ENOMEM leaves the method unchanged).
  * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. A bounded
  * tensor-core wait that runs out makes the call return EOR_ETIMEOUT. */
 enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2, EOR_METHOD_BASIS_TF32 = 3 };

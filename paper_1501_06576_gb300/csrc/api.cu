@@ -56,6 +56,12 @@ bool alloc_n(eor_ctx* c, T** out, size_t count) {
     return *out != nullptr;
 }
 
+// Half spectra held by d_inter: the direct method filters group x pairs of them per launch;
+// the other methods use one (the filtered-density and box diagnostics).
+size_t inter_slots(int method, int pairs, int group) {
+    return method == eor::kMethodDirect ? (size_t)pairs * group : 1;
+}
+
 // Number of radii of the ladder that starts at r_mfp: used only to size tables and the
 // launch schedule (the ladders themselves are built on the device).
 int ladder_bound(const eor_config& g, double r_mfp) {
@@ -306,7 +312,7 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_nmodes, B) && alloc_n(c, &c->d_ksum, B) && alloc_n(c, &c->d_params, 3 * W) &&
               alloc_n(c, &c->d_walkers, W) && alloc_n(c, &c->d_pairs, pairs) &&
               alloc_n(c, &c->d_wtab, (size_t)W * c->max_radii * c->n_m2) &&
-              alloc_n(c, &c->d_inter, (size_t)P * G * c->nspec) &&
+              alloc_n(c, &c->d_inter, inter_slots(c->tune.method, P, G) * c->nspec) &&
               alloc_n(c, &c->d_flags, (size_t)P * c->flag_words) && alloc_n(c, &c->d_psinter, 2 * (size_t)P * c->nspec) &&
               alloc_n(c, &c->d_ps_sum, pairs * B) && alloc_n(c, &c->d_xhi_sum, pairs) &&
               alloc_n(c, &c->d_xhi_mean, pairs) && alloc_n(c, &c->d_chi2, W) && alloc_n(c, &c->d_mock, 2 * Z * B) &&
@@ -677,7 +683,8 @@ int eor_set_tuning(eor_ctx* c, int group, int pairs, int plane_threads) {
     float2* inter = nullptr;
     uint32_t* flags = nullptr;
     float2* psinter = nullptr;
-    if (!alloc_n(c, &inter, (size_t)pairs * group * c->nspec) || !alloc_n(c, &flags, (size_t)pairs * c->flag_words) ||
+    if (!alloc_n(c, &inter, inter_slots(c->tune.method, pairs, group) * c->nspec) ||
+        !alloc_n(c, &flags, (size_t)pairs * c->flag_words) ||
         !alloc_n(c, &psinter, 2 * (size_t)pairs * c->nspec)) {
         dev_free(c, inter);
         dev_free(c, flags);
@@ -842,6 +849,17 @@ int eor_set_method(eor_ctx* c, int method) {
         method != EOR_METHOD_BASIS_TF32)
         return fail(c, EOR_EINVAL, "unknown method");
     CK(cudaStreamSynchronize(c->stream), "method");
+    const int internal = method == EOR_METHOD_BASIS        ? eor::kMethodBasis
+                         : method == EOR_METHOD_DIRECT     ? eor::kMethodDirect
+                         : method == EOR_METHOD_BASIS_SIMT ? eor::kMethodBasisSimt
+                                                           : eor::kMethodBasisTf32;
+    const size_t slots = inter_slots(internal, c->tune.pairs, c->tune.group);
+    if (slots != inter_slots(c->tune.method, c->tune.pairs, c->tune.group)) {
+        float2* inter = nullptr;
+        if (!alloc_n(c, &inter, slots * c->nspec)) return fail(c, EOR_ENOMEM, "direct-method scratch");
+        dev_free(c, c->d_inter);
+        c->d_inter = inter;
+    }
     if (method == EOR_METHOD_BASIS_TF32 && !c->d_tcA && eor::basis_tc_fits(c->basis_rank)) {
         // the TF32 contraction's operands, formatted now if the boxes are already in place
         if (!alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, c->cfg.n_z)) ||
@@ -859,10 +877,7 @@ int eor_set_method(eor_ctx* c, int method) {
             return fail(c, EOR_ENOMEM, "TF32 contraction columns");
         if (c->stage >= 1) CK(eor::format_basis_tc(c), "TF32 contraction operands");
     }
-    c->tune.method = method == EOR_METHOD_BASIS        ? eor::kMethodBasis
-                     : method == EOR_METHOD_DIRECT     ? eor::kMethodDirect
-                     : method == EOR_METHOD_BASIS_SIMT ? eor::kMethodBasisSimt
-                                                       : eor::kMethodBasisTf32;
+    c->tune.method = internal;
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
