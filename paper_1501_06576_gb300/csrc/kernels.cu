@@ -1372,19 +1372,21 @@ struct Chi2Args {
 };
 
 // chi^2 per walker, summed linearly over redshifts (Sec. 3.4) over the bins the table
-// marks (geometric centre in [chi2_k_lo, chi2_k_hi], Sec. 2.5). FP64.
+// marks (geometric centre in [chi2_k_lo, chi2_k_hi], Sec. 2.5). FP64; one warp per walker,
+// its lanes over the (redshift, bin) terms, then a shuffle tree (one thread per walker spent
+// its time in a chain of dependent FP64 divisions).
 __global__ void k_chi2(Chi2Args a) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= a.n_walkers) return;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= a.n_walkers) return;   // uniform over the warp
     double acc = 0.0;
-    for (int zi = 0; zi < a.n_z; zi++)
-        for (int b = 0; b < a.n_bins; b++) {
-            if (!a.use[b] || a.nmodes[b] == 0) continue;
-            double r = (a.d2[((size_t)w * a.n_z + zi) * a.n_bins + b] - a.mock[zi * a.n_bins + b]) /
-                       a.sigma[zi * a.n_bins + b];
-            acc += r * r;
-        }
-    a.chi2[w] = acc;
+    for (int e = lane; e < a.n_z * a.n_bins; e += 32) {
+        const int zi = e / a.n_bins, b = e % a.n_bins;
+        if (!a.use[b] || a.nmodes[b] == 0) continue;
+        const double r = (a.d2[((size_t)w * a.n_z + zi) * a.n_bins + b] - a.mock[e]) / a.sigma[e];
+        acc += r * r;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) a.chi2[w] = acc;
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -1994,7 +1996,7 @@ cudaError_t launch_chi2(eor_ctx* c) {
     Chi2Args a{c->d_d2, c->d_chi2_use, c->d_nmodes, c->d_mock, c->d_mock + g.n_z * g.n_bins, c->d_chi2, c->n_walkers,
                g.n_z, g.n_bins};
     trace_begin(c, kKFinish);
-    k_chi2<<<(c->n_walkers + 127) / 128, 128, 0, c->stream>>>(a);
+    k_chi2<<<(c->n_walkers + 3) / 4, 128, 0, c->stream>>>(a);   // one warp per walker
     trace_end(c);
     return cudaGetLastError();
 }

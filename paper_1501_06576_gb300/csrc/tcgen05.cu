@@ -516,22 +516,33 @@ __global__ void k_xq_finish(const unsigned long long* xq, int pairs, double* xhi
 // its R_cell radius first, then its radii from R_mfp down, then padding (-1) to the end of
 // its last group. cols[] holds walker << 8 | radius index; gmeta[] per group walker << 2 |
 // first << 1 | last, or -1 for a group left empty; *ncols the number of columns including
-// padding. Thread 0 places the walkers, then the block fills the columns.
+// padding. Thread 0 places the walkers (from their group counts, gathered by the block into
+// shared memory 256 at a time: one dependent global load per walker made the serial loop
+// take tens of microseconds), then the block fills the columns.
 __global__ void k_build_columns(const WalkerInfo* walkers, int n_walkers, int* goff, int* cols, int* gmeta,
                                 int* ncols, int rcell_first) {
     static_assert(kMaxRadii <= 2 * kGroup, "a walker spans at most two groups");
+    constexpr int kChunk = 256;
+    __shared__ unsigned char s_ng[kChunk];
     // columns of a walker: all its radii (R_cell first) or only those above R_cell (at least
     // one group, which carries the walker's x_HI even when it has no radius above R_cell)
     auto width = [&](int nr) { return rcell_first ? nr : nr - 1; };
     auto groups = [&](int nr) { const int ng = (width(nr) + kGroup - 1) / kGroup; return ng > 0 ? ng : 1; };
+    int g = 0;   // thread 0's running group count
+    for (int w0 = 0; w0 < n_walkers; w0 += kChunk) {
+        for (int i = threadIdx.x; i < kChunk && w0 + i < n_walkers; i += blockDim.x)
+            s_ng[i] = (unsigned char)groups(walkers[w0 + i].n_r);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 0; i < kChunk && w0 + i < n_walkers; i++) {
+                const int ng = s_ng[i];
+                if (ng == 2 && (g & 1)) g++;
+                goff[w0 + i] = g;
+                g += ng;
+            }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        int g = 0;
-        for (int w = 0; w < n_walkers; w++) {
-            const int ng = groups(walkers[w].n_r);
-            if (ng == 2 && (g & 1)) g++;
-            goff[w] = g;
-            g += ng;
-        }
         goff[n_walkers] = g;
         *ncols = g * kGroup;
     }
