@@ -50,3 +50,21 @@ def test_traffic_record_used_only_for_its_sources(bench):
             assert got is None
     assert bench.ncu_launch_traffic("no_such_class", 1.0) is None
     assert bench.ncu_launch_traffic("ps_plane", 1.0, 2) is None   # another tiling's kernels
+
+
+def test_f16_column_chunks_follows_the_placement_rule(bench):
+    # the executed-FLOP figure counts 256-column chunks of the flag contraction: walkers'
+    # radii above R_cell in groups of 32 (one group at least), a two-group walker starting on
+    # an even group; checked here against the columns laid out one by one
+    def layout(ladders):
+        cols = []
+        for w, nr in enumerate(ladders):
+            width = max(nr - 1, 0)
+            ng = max(1, -(-width // 32))
+            if ng == 2 and (len(cols) // 32) % 2:
+                cols += [None] * 32
+            cols += [w] * width + [None] * (ng * 32 - width)
+        return -(-len(cols) // 256)
+    assert bench.f16_column_chunks([]) == 0 == layout([])
+    for ladders in ([1], [2] * 8, [33] * 8, [17, 31, 40, 2, 64, 33, 1], [40, 9] * 11, list(range(1, 65))):
+        assert bench.f16_column_chunks(ladders) == layout(ladders), ladders
