@@ -853,13 +853,6 @@ int eor_set_method(eor_ctx* c, int method) {
                          : method == EOR_METHOD_DIRECT     ? eor::kMethodDirect
                          : method == EOR_METHOD_BASIS_SIMT ? eor::kMethodBasisSimt
                                                            : eor::kMethodBasisTf32;
-    const size_t slots = inter_slots(internal, c->tune.pairs, c->tune.group);
-    if (slots != inter_slots(c->tune.method, c->tune.pairs, c->tune.group)) {
-        float2* inter = nullptr;
-        if (!alloc_n(c, &inter, slots * c->nspec)) return fail(c, EOR_ENOMEM, "direct-method scratch");
-        dev_free(c, c->d_inter);
-        c->d_inter = inter;
-    }
     if (method == EOR_METHOD_BASIS_TF32 && !c->d_tcA && eor::basis_tc_fits(c->basis_rank)) {
         // the TF32 contraction's operands, formatted now if the boxes are already in place
         if (!alloc_n(c, &c->d_tcA, eor::basis_tc_a_bytes((long long)c->n3, c->cfg.n_z)) ||
@@ -876,6 +869,15 @@ int eor_set_method(eor_ctx* c, int method) {
               alloc_n(c, &c->d_goff, (size_t)c->cfg.max_walkers + 1)))
             return fail(c, EOR_ENOMEM, "TF32 contraction columns");
         if (c->stage >= 1) CK(eor::format_basis_tc(c), "TF32 contraction operands");
+    }
+    // the direct method's scratch, resized last: every failure above leaves the method and its
+    // buffers as they were
+    const size_t slots = inter_slots(internal, c->tune.pairs, c->tune.group);
+    if (slots != inter_slots(c->tune.method, c->tune.pairs, c->tune.group)) {
+        float2* inter = nullptr;
+        if (!alloc_n(c, &inter, slots * c->nspec)) return fail(c, EOR_ENOMEM, "direct-method scratch");
+        dev_free(c, c->d_inter);
+        c->d_inter = inter;
     }
     c->tune.method = internal;
     if (c->graph_exec) {
