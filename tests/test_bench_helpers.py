@@ -68,3 +68,22 @@ def test_f16_column_chunks_follows_the_placement_rule(bench):
     assert bench.f16_column_chunks([]) == 0 == layout([])
     for ladders in ([1], [2] * 8, [33] * 8, [17, 31, 40, 2, 64, 33, 1], [40, 9] * 11, list(range(1, 65))):
         assert bench.f16_column_chunks(ladders) == layout(ladders), ladders
+
+
+def test_reference_arm_prints_the_contract_line():
+    # `bench.py --impl reference` times the FP64 oracle on the host cores (one realization here)
+    # and prints one JSON line with the fields the driver reads; it needs no GPU
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["n"] == 128 and d["config"]["z"] == [8.0, 9.0, 10.0]
