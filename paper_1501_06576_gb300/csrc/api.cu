@@ -311,7 +311,6 @@ int eor_create(const eor_config* cfg, void* cuda_stream, eor_ctx** out) {
               alloc_n(c, &c->d_cosmo_amp, 1) && alloc_n(c, &c->d_bin_of_m2, c->n_m2) &&
               alloc_n(c, &c->d_nmodes, B) && alloc_n(c, &c->d_ksum, B) && alloc_n(c, &c->d_params, 3 * W) &&
               alloc_n(c, &c->d_walkers, W) && alloc_n(c, &c->d_pairs, pairs) &&
-              alloc_n(c, &c->d_wtab, (size_t)W * c->max_radii * c->n_m2) &&
               alloc_n(c, &c->d_inter, inter_slots(c->tune.method, P, G) * c->nspec) &&
               alloc_n(c, &c->d_flags, (size_t)P * c->flag_words) && alloc_n(c, &c->d_psinter, 2 * (size_t)P * c->nspec) &&
               alloc_n(c, &c->d_ps_sum, pairs * B) && alloc_n(c, &c->d_xhi_sum, pairs) &&
@@ -870,6 +869,10 @@ int eor_set_method(eor_ctx* c, int method) {
             return fail(c, EOR_ENOMEM, "TF32 contraction columns");
         if (c->stage >= 1) CK(eor::format_basis_tc(c), "TF32 contraction operands");
     }
+    // the direct method's per-radius window tables, allocated on its first choice and kept
+    if (internal == eor::kMethodDirect && !c->d_wtab &&
+        !alloc_n(c, &c->d_wtab, (size_t)c->cfg.max_walkers * c->max_radii * c->n_m2))
+        return fail(c, EOR_ENOMEM, "direct-method window tables");
     // the direct method's scratch, resized last: every failure above leaves the method and its
     // buffers as they were
     const size_t slots = inter_slots(internal, c->tune.pairs, c->tune.group);
