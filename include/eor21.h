@@ -262,7 +262,8 @@ int eor_autotune(eor_ctx* ctx, const double* params, int n_walkers, const double
  * EOR_METHOD_BASIS_SIMT: the same contraction on the FP32 units only.
  * EOR_METHOD_DIRECT: a filter and inverse FFT of the density spectrum for every radius
  *   (its group x pairs half spectra of scratch are allocated when it is chosen and released
- *   when another method is; EOR_ENOMEM leaves the method unchanged).
+ *   when another method is, its per-radius window tables on its first choice; EOR_ENOMEM
+ *   leaves the method unchanged).
  * eor_basis_info gives the basis size and its largest residual |W - sum c phi|. A bounded
  * tensor-core wait that runs out makes the call return EOR_ETIMEOUT. */
 enum { EOR_METHOD_BASIS = 0, EOR_METHOD_DIRECT = 1, EOR_METHOD_BASIS_SIMT = 2, EOR_METHOD_BASIS_TF32 = 3 };
